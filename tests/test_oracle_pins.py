@@ -1,0 +1,306 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test names the passage it pins.  None of them retypes the oracle's own
+formula: they use closed forms (Prop. 1, 1-D W1, separable costs), brute force
+(Birkhoff), library solvers (scipy's assignment and HiGHS LP), the explicit
+Kronecker matrix of Eq. (4) with the generic Algorithm 1, and invariants
+(fixed point at an optimum, scaling by the data precision, Lemma 2).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2407_19689_gb300 import instances as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ot_closed_forms.txt")
+
+
+def _rand_instance(m, n, seed, marg="uniform"):
+    return I.points_instance(m, n, seed, marginals=marg)
+
+
+# --------------------------------------------------------------------------
+# Eq. (4) and Prop. 1: the implicit operator pair
+# --------------------------------------------------------------------------
+
+def _kron_A(m, n):
+    """A = [1_n^T (x) I_m ; I_n (x) 1_m^T] of Eq. (4) (vec stacks columns)."""
+    return np.vstack([np.kron(np.ones((1, n)), np.eye(m)), np.kron(np.eye(n), np.ones((1, m)))])
+
+
+def test_operators_match_kronecker_matrix(ora):
+    """Eq. (4): A vec(X) = [X1; X^T1] and A^T[p;q] = p1^T + 1q^T, against np.kron."""
+    rng = np.random.default_rng(1)
+    m, n = 5, 7
+    A = _kron_A(m, n)
+    X = rng.standard_normal((m, n))
+    p, q = rng.standard_normal(m), rng.standard_normal(n)
+    r, c = ora.apply_A(X)
+    ax = A @ X.reshape(-1, order="F")
+    np.testing.assert_allclose(np.concatenate([r, c]), ax, rtol=0, atol=1e-13)
+    aty = A.T @ np.concatenate([p, q])
+    np.testing.assert_allclose(ora.apply_At(p, q).reshape(-1, order="F"), aty, rtol=0, atol=1e-13)
+
+
+def test_operator_adjointness(ora):
+    rng = np.random.default_rng(2)
+    m, n = 33, 17
+    X = rng.standard_normal((m, n))
+    p, q = rng.standard_normal(m), rng.standard_normal(n)
+    r, c = ora.apply_A(X)
+    lhs = r @ p + c @ q
+    rhs = np.sum(X * ora.apply_At(p, q))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("m,n", [(3, 4), (16, 9), (40, 40)])
+def test_operator_norm_is_sqrt_m_plus_n(ora, m, n):
+    """Prop. 1: ||A||_2 = sqrt(m+n), attained at X = 1/sqrt(mn)."""
+    rng = np.random.default_rng(3)
+    X = rng.random((m, n))
+    for _ in range(200):
+        r, c = ora.apply_A(X)
+        X = ora.apply_At(r, c)
+        X /= np.linalg.norm(X)
+    r, c = ora.apply_A(X)
+    est = math.sqrt(r @ r + c @ c)
+    assert abs(est - math.sqrt(m + n)) < 1e-9
+    U = np.full((m, n), 1.0 / math.sqrt(m * n))
+    r, c = ora.apply_A(U)
+    assert abs(math.sqrt(r @ r + c @ c) - math.sqrt(m + n)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 step
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n", [(2, 3), (4, 4), (6, 5)])
+def test_alg2_step_equals_alg1_with_explicit_A(ora, m, n):
+    """Sec. 3 (vectorisation): Algorithm 2's iterates equal Algorithm 1's on
+    c = vec(C), b = [f; g] and the explicit Kronecker A."""
+    ins = _rand_instance(m, n, 10 + m)
+    rng = np.random.default_rng(4)
+    X = rng.random((m, n)) * 0.1
+    p, q = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
+    eta = 0.5 / math.sqrt(m + n)
+    A = _kron_A(m, n)
+    for _ in range(5):
+        Xn, pn, qn = ora.pdhg_step(ins.C, ins.f, ins.g, X, p, q, eta, eta)
+        xn, yn = ora.lp_pdhg_step(A, np.concatenate([ins.f, ins.g]), ins.C.reshape(-1, order="F"),
+                                  X.reshape(-1, order="F"), np.concatenate([p, q]), eta, eta)
+        np.testing.assert_allclose(Xn.reshape(-1, order="F"), xn, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(np.concatenate([pn, qn]), yn, rtol=0, atol=1e-14)
+        X, p, q = Xn, pn, qn
+
+
+def test_optimum_is_fixed_point_of_step(ora):
+    """An optimal (X*, p*, q*) solves the minimax, so one PDHG step leaves it in place."""
+    ins = _rand_instance(9, 11, 21)
+    obj, X, p, q = ora.exact_transport(ins.C, ins.f, ins.g)
+    for tau, sigma in [(0.1, 0.1), (0.01, 3.0)]:
+        Xn, pn, qn = ora.pdhg_step(ins.C, ins.f, ins.g, X, p, q, tau, sigma)
+        np.testing.assert_allclose(Xn, X, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(pn, p, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(qn, q, rtol=0, atol=1e-13)
+
+
+def test_scaling_by_data_precision_is_exact(ora):
+    """Sec. 4.2: iterates on (C, f, g)/Delta are the iterates on (C, f, g) divided by
+    Delta at the same steps; with Delta a power of two this holds bit for bit."""
+    ins = _rand_instance(7, 6, 31)
+    z0 = (np.zeros((7, 6)), np.zeros(7), np.zeros(6))
+    a = ora.pdhg_steps(ins.C, ins.f, ins.g, *z0, k=25, eta=0.2)
+    s = 2.0 ** -7
+    b = ora.pdhg_steps(ins.C * s, ins.f * s, ins.g * s, *z0, k=25, eta=0.2)
+    for u, v in zip(a, b):
+        assert np.array_equal(u * s, v)
+    # The whole adaptive solve (restarts, steps, primal weight) is scale-equivariant
+    # too, once the two absolute constants scale with the data: R (a bound on
+    # ||z||; <C,X> - f^T p - g^T q is quadratic in the scaling, so gap/R stays
+    # linear) and eps_zero of the primal-weight update.  Every decision then
+    # compares ratios of homogeneous quantities.
+    ra = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=0.0, max_passes=640, R=1.0, eps_zero=1e-10))
+    rb = ora.solve(ins.C * s, ins.f * s, ins.g * s, ora.Options(tol=0.0, max_passes=640, R=s, eps_zero=1e-10 * s))
+    assert ra.restarts >= 3
+    assert (ra.restarts, ra.rejected, ra.iters) == (rb.restarts, rb.rejected, rb.iters)
+    assert np.array_equal(ra.X * s, rb.X) and np.array_equal(ra.p * s, rb.p)
+
+
+# --------------------------------------------------------------------------
+# KKT error (Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def test_kkt_closed_forms(ora):
+    ins = _rand_instance(8, 5, 41)
+    C, f, g = ins.C, ins.f, ins.g
+    # At the origin only the primal residual is left (C >= 0 so [-C]^+ = 0).
+    k0 = ora.kkt(C, f, g, np.zeros((8, 5)), np.zeros(8), np.zeros(5))
+    assert abs(k0.kkt - math.sqrt(np.sum(f ** 2) + np.sum(g ** 2))) < 1e-15
+    # The product plan f g^T is feasible; with zero duals only the gap <C, f g^T> is left.
+    kp = ora.kkt(C, f, g, np.outer(f, g), np.zeros(8), np.zeros(5), R=2.0)
+    assert abs(kp.kkt - abs(f @ C @ g) / 2.0) < 1e-14
+    # Constant duals p = t 1: dual infeasibility sum_ij ([t - C_ij]^+)^2.
+    t = 0.4
+    kd = ora.kkt(C, f, g, np.outer(f, g), np.full(8, t), np.zeros(5))
+    assert abs(kd.rd2 - np.sum(np.maximum(t - C, 0.0) ** 2)) < 1e-14
+    assert abs(kd.dual - t) < 1e-15
+    # At an exact optimum every part vanishes.
+    obj, X, p, q = ora.exact_transport(C, f, g)
+    ks = ora.kkt(C, f, g, X, p, q)
+    assert ks.kkt < 1e-14 and ks.rel_kkt < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Exact optimum of Eq. (1)
+# --------------------------------------------------------------------------
+
+def _golden():
+    out = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, mn, C, f, g, opt = [s.strip() for s in line.split("|")]
+        m, n = map(int, mn.split())
+        out.append((name, np.array(C.split(), float).reshape(m, n), np.array(f.split(), float),
+                    np.array(g.split(), float), float(opt)))
+    return out
+
+
+@pytest.mark.parametrize("case", _golden(), ids=lambda c: c[0])
+def test_exact_transport_golden(ora, case):
+    name, C, f, g, opt = case
+    obj, X, p, q = ora.exact_transport(C, f, g)
+    assert abs(obj - opt) < 1e-14
+    res = ora.solve(C, f, g, ora.Options(tol=1e-10))
+    assert res.status == 0 and abs(res.primal_obj - opt) < 1e-8
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7])
+def test_exact_transport_vs_brute_force(ora, n):
+    """Birkhoff: with f = g = 1/n the optimum is a permutation / n."""
+    ins = I.points_instance(n, n, 50 + n, marginals="equal")
+    best = min(sum(ins.C[i, s[i]] for i in range(n)) for s in itertools.permutations(range(n))) / n
+    obj, *_ = ora.exact_transport(ins.C, ins.f, ins.g)
+    assert abs(obj - best) < 1e-14
+
+
+def test_exact_transport_vs_hungarian(ora):
+    sp = pytest.importorskip("scipy.optimize")
+    n = 60
+    ins = I.points_instance(n, n, 61, marginals="equal")
+    ri, ci = sp.linear_sum_assignment(ins.C)
+    obj, *_ = ora.exact_transport(ins.C, ins.f, ins.g)
+    assert abs(obj - ins.C[ri, ci].sum() / n) < 1e-13
+
+
+@pytest.mark.parametrize("m,n,seed", [(9, 13, 71), (20, 7, 72), (25, 25, 73)])
+def test_exact_transport_vs_highs(ora, m, n, seed):
+    sp = pytest.importorskip("scipy.optimize")
+    ins = I.points_instance(m, n, seed, marginals="dirichlet", alpha=1.0)
+    A = _kron_A(m, n)
+    lp = sp.linprog(ins.C.reshape(-1, order="F"), A_eq=A, b_eq=np.concatenate([ins.f, ins.g]),
+                    bounds=(0, None), method="highs")
+    obj, *_ = ora.exact_transport(ins.C, ins.f, ins.g)
+    assert abs(obj - lp.fun) < 1e-9
+
+
+def test_exact_transport_one_dimensional_w1(ora):
+    """1-D closed form: with cost |x - y|, OPT = integral |F(t) - G(t)| dt."""
+    rng = np.random.default_rng(81)
+    x, y = rng.random(23), rng.random(31)
+    f, g = rng.dirichlet(np.ones(23)), rng.dirichlet(np.ones(31))
+    C = np.abs(x[:, None] - y[None, :])
+    pts = np.sort(np.concatenate([x, y]))
+    F = np.array([f[x <= t].sum() for t in pts[:-1]])
+    G = np.array([g[y <= t].sum() for t in pts[:-1]])
+    w1 = np.sum(np.abs(F - G) * np.diff(pts))
+    obj, *_ = ora.exact_transport(C, f, g)
+    assert abs(obj - w1) < 1e-13
+
+
+def test_exact_transport_certificates(ora):
+    """Primal feasibility, dual feasibility, zero gap, complementary slackness."""
+    ins = I.points_instance(40, 30, 91, marginals="dirichlet", alpha=0.5)
+    obj, X, p, q = ora.exact_transport(ins.C, ins.f, ins.g)
+    assert X.min() >= 0.0
+    np.testing.assert_allclose(X.sum(1), ins.f, atol=1e-15)
+    np.testing.assert_allclose(X.sum(0), ins.g, atol=1e-15)
+    red = ins.C - p[:, None] - q[None, :]
+    assert red.min() > -1e-14
+    assert abs(obj - (ins.f @ p + ins.g @ q)) < 1e-14
+    assert np.all(np.abs(red[X > 0]) < 1e-14)
+
+
+# --------------------------------------------------------------------------
+# The solve (Algorithm 2 + Sec. 5)
+# --------------------------------------------------------------------------
+
+def _certified_interval(C, f, g, X, p, q):
+    """OPT lies in [dual bound, primal bound]: a feasible dual by lowering q
+    (q_j <- min_i C_ij - p_i) and a feasible plan by Algorithm 3 (Lemma 2)."""
+    qf = np.minimum(q, (C - p[:, None]).min(axis=0))
+    return f @ p + g @ qf
+
+
+@pytest.mark.parametrize("m,n,seed", [(64, 64, I.seed_for(0)), (37, 51, 101), (80, 20, 102)])
+def test_solve_reaches_exact_optimum(ora, m, n, seed):
+    ins = I.points_instance(m, n, seed)
+    opt, *_ = ora.exact_transport(ins.C, ins.f, ins.g)
+    for tol, bound in [(1e-4, 5e-3), (1e-6, 1e-5), (1e-8, 1e-7)]:
+        res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=tol))
+        assert res.status == 0 and res.rel_kkt <= tol
+        assert abs(res.primal_obj - opt) / opt < bound
+        lb = _certified_interval(ins.C, ins.f, ins.g, res.X, res.p, res.q)
+        ub = ins.C.reshape(-1) @ ora.round_plan(res.X, ins.f, ins.g).reshape(-1)
+        assert lb <= opt + 1e-15 and opt <= ub + 1e-15
+
+
+def test_solve_theory_mode_identifies_support(ora):
+    """Constant eta = 1/(2 sqrt(m+n)), fixed-beta restarts to the average
+    (Eq. 6): converges; after identification X_ij is exactly 0 on N (Thm. 1)."""
+    ins = I.points_instance(12, 10, 111)
+    opt, Xs, ps, qs = ora.exact_transport(ins.C, ins.f, ins.g)
+    opts = ora.Options(tol=1e-9, adaptive_step=0, adaptive_restart=0, primal_weight_update=0, beta=0.2,
+                       max_passes=2_000_000)
+    res = ora.solve(ins.C, ins.f, ins.g, opts)
+    assert res.status == 0
+    assert abs(res.primal_obj - opt) / opt < 1e-7
+    N = (ins.C - ps[:, None] - qs[None, :]) > 1e-6
+    assert np.all(res.X[N] == 0.0)
+
+
+def test_solve_rel_mode_one_plus(ora):
+    """Reading C5, option 1 (cuPDLP's '1 +' denominators) also terminates correctly."""
+    ins = I.points_instance(30, 30, 121)
+    res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=1e-6, rel_mode=1))
+    k = ora.kkt(ins.C, ins.f, ins.g, res.X, res.p, res.q, rel_mode=1)
+    assert res.status == 0 and k.rel_kkt <= 1e-6
+    assert abs(k.rel_kkt - res.rel_kkt) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Algorithm 3 and Lemma 2
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [131, 132, 133])
+def test_rounding_feasible_and_lemma2(ora, seed):
+    rng = np.random.default_rng(seed)
+    m, n = 13, 17
+    f, g = rng.dirichlet(np.ones(m)), rng.dirichlet(np.ones(n))
+    X = np.outer(f, g) * rng.uniform(0.5, 1.5, (m, n))
+    Xf = ora.round_plan(X, f, g)
+    assert Xf.min() >= 0.0
+    np.testing.assert_allclose(Xf.sum(1), f, atol=1e-15)
+    np.testing.assert_allclose(Xf.sum(0), g, atol=1e-15)
+    viol = np.abs(f - X.sum(1)).sum() + np.abs(g - X.sum(0)).sum()
+    assert np.abs(Xf - X).sum() <= 2.0 * viol + 1e-15
+
+
+def test_rounding_keeps_feasible_plan(ora):
+    ins = I.points_instance(6, 9, 141)
+    obj, X, p, q = ora.exact_transport(ins.C, ins.f, ins.g)
+    np.testing.assert_allclose(ora.round_plan(X, ins.f, ins.g), X, atol=1e-16)
