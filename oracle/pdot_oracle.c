@@ -303,7 +303,9 @@ int ora_solve(int64_t m, int64_t n, const double *C, const double *f, const doub
         if (opt->adaptive_step) {
             /* Step-size test of Sec. 5 in the PDLP form (reading C6):
              *   eta_bar = (omega ||dX||^2 + ||(dp,dq)||^2 / omega) / (2 |dp^T dX 1 + dq^T dX^T 1|)
-             *   eta'    = min((1 - (t+1)^-0.3) eta_bar, (1 + (t+1)^-0.6) eta),  t = accepted so far
+             *   eta'    = min((1 - (t+1)^-0.3) eta_bar, (1 + (t+1)^-0.6) eta),
+             * t = 1-based index of the iteration being attempted (accepted so far + 1),
+             * so the first factor is never 0.  eta_bar = +inf when the denominator is 0.
              * The step is accepted when eta <= eta_bar; eta' is used next either way. */
             for (int64_t e = 0; e < mn; ++e) D[e] = Xn[e] - X[e];
             ora_apply_A(m, n, D, rd, cd);
@@ -312,7 +314,7 @@ int ora_solve(int64_t m, int64_t n, const double *C, const double *f, const doub
             for (int64_t i = 0; i < m; ++i) { dy2 += (pn[i] - p[i]) * (pn[i] - p[i]); inter += (pn[i] - p[i]) * rd[i]; }
             for (int64_t j = 0; j < n; ++j) { dy2 += (qn[j] - q[j]) * (qn[j] - q[j]); inter += (qn[j] - q[j]) * cd[j]; }
             double eta_bar = inter != 0.0 ? (omega * dX2 + dy2 / omega) / (2.0 * fabs(inter)) : INFINITY;
-            double t1 = (double)(total + 1);
+            double t1 = (double)(total + 2);
             double a = (1.0 - pow(t1, -0.3)) * eta_bar;
             double b = (1.0 + pow(t1, -0.6)) * eta;
             double eta_next = a < b ? a : b;
