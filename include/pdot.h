@@ -1,0 +1,226 @@
+/*
+ * pdot.h -- C ABI of the GB300 (sm_103a) PDOT library: restarted PDHG for
+ * discrete optimal transport (arXiv 2407.19689).
+ *
+ * Problem (Eq. (1)):   min <C, X>   s.t.  X 1_n = f,  X^T 1_m = g,  X >= 0,
+ * with C (m x n, non-negative), f (m) and g (n) probability vectors.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major: element (i, j) of C sits at C[i * ldc + j],
+ *     0 <= i < m, 0 <= j < n, ldc >= n.  Plans passed in or out are dense
+ *     row-major m x n (leading dimension n) in the handle's x_dtype.
+ *   - Unless a name ends in _host, every pointer is a CUDA DEVICE pointer on
+ *     the handle's device.  Inputs are borrowed for the duration of the call
+ *     (for pdot_batch_submit: until pdot_poll reports the ticket).  The library
+ *     owns its plan buffers, dual vectors and scratch memory, allocated with
+ *     cudaMalloc and freed by pdot_destroy.
+ *   - Work is issued on the handle's CUDA stream.  Every call returns only
+ *     after its results are in place (it synchronises that stream), except
+ *     pdot_batch_submit, which only queues.
+ *   - Errors are reported only through return codes; nothing is thrown across
+ *     the ABI.  A handle is used by one host thread at a time.
+ *   - Argument errors (PDOT_ERR_ARG): m < 1, n < 1, ldc < n, tol <= 0 (solve),
+ *     null required pointers, unknown dtypes, |sum f - sum g| > 1e-9 * max(sum f, 1)
+ *     or a negative entry in f or g (checked on a host copy), x_dtype other
+ *     than F32/F64, F64 plans with non-F64 costs or F32 plans with F64 costs.
+ *     C is not scanned for negative entries.
+ */
+#ifndef PDOT_H
+#define PDOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PDOT_OK = 0,
+    PDOT_ERR_ARG = 1,
+    PDOT_ERR_OOM = 2,
+    PDOT_ERR_CUDA = 3,
+    PDOT_ERR_NUMERIC = 4,    /* a KKT quantity became NaN or Inf */
+    PDOT_MAX_ITER = 5,       /* pass budget spent; the last check's candidate is returned */
+    PDOT_TIMEOUT = 6,        /* time_limit_s exceeded; the current iterate is returned */
+    PDOT_BUSY = 7,           /* batch admission would exceed the HBM budget or slot count */
+    PDOT_PENDING = 8,        /* ticket not finished yet */
+    PDOT_CANCELLED = 9
+} pdot_status;
+
+typedef enum { PDOT_F32 = 0, PDOT_BF16 = 1, PDOT_F64 = 2 } pdot_dtype;
+
+/*
+ * Solver options.  Defaults (pdot_default_options) follow Sec. 5 of the paper
+ * and the readings recorded in the design notes:
+ *   tol 1e-4 (Sec. 5.1), restart check every 64 passes, adaptive step on
+ *   (PDLP rule), adaptive restart on (beta_suff 0.1, beta_nec 0.9,
+ *   beta_art 0.36), primal-weight update on (theta 0.5, omega0 1,
+ *   eps_zero 1e-10), R = 1, scale-relative termination measures.
+ * Theory mode (Algorithm 2 with the fixed-beta restart of Eq. (6) and the
+ * constant step 1/(2 sqrt(m+n)) of Theorem 1): adaptive_step = 0,
+ * adaptive_restart = 0, primal_weight_update = 0.
+ */
+typedef struct {
+    double tol;                    /* relative KKT tolerance for termination */
+    int64_t max_iter;              /* bound on PDHG passes (accepted + rejected) */
+    double time_limit_s;           /* wall-clock limit of one solve; <= 0: none */
+    int32_t restart_check_every;   /* K: restart/termination check after every K-th pass */
+    int32_t adaptive_step;         /* 1: PDLP adaptive step size (Sec. 5); 0: constant eta */
+    int32_t adaptive_restart;      /* 1: three restart conditions (Sec. 5); 0: Eq. (6) */
+    int32_t primal_weight_update;  /* 1: PrimalWeightUpdate at restarts (Sec. 5) */
+    double beta;                   /* decay of the fixed-beta restart, Eq. (6) */
+    double beta_suff, beta_nec, beta_art;
+    double theta;                  /* primal-weight smoothing */
+    double eta0;                   /* initial/constant step; <= 0: 1/sqrt(m+n) adaptive, 1/(2 sqrt(m+n)) constant */
+    double omega0;                 /* initial primal weight */
+    double R;                      /* gap scaling in the KKT error (Sec. 3.1) */
+    double eps_zero;               /* threshold of the primal-weight update */
+    int32_t rel_mode;              /* 0: scale-relative termination measures; 1: cuPDLP "1 +" form */
+    pdot_dtype x_dtype;            /* plan precision: PDOT_F32 (default) or PDOT_F64 */
+    int32_t round_plan;            /* 1: return the Algorithm 3 rounding of the plan */
+    int32_t use_graph;             /* 1: capture K-pass chunks as CUDA graphs (default) */
+    int32_t tile_rows;             /* rows per plan tile (16..256, multiple of 8); 0: autotune */
+    uint64_t hbm_budget_bytes;     /* batch admission budget; 0: 90% of free memory at create */
+    int32_t max_batch_slots;       /* most instances resident at once in the batch engine */
+    int32_t chunk_checks;          /* check periods per batch chunk launch (serving granularity) */
+} pdot_options;
+
+typedef struct {
+    pdot_status status;
+    double primal_obj;      /* <C, X> of the returned plan */
+    double dual_obj;        /* f^T p + g^T q */
+    double gap;             /* primal_obj - dual_obj */
+    double kkt;             /* KKT error as printed in Sec. 3.1 (gap scaled by 1/R) */
+    double rel_kkt;         /* max(rel_primal, rel_dual, rel_gap) */
+    double rel_primal, rel_dual, rel_gap;
+    int64_t iters;          /* accepted PDHG iterations */
+    int64_t passes;         /* PDHG passes (accepted + rejected) */
+    int64_t restarts;
+    int64_t rejected_steps;
+    double eta, omega;      /* final step size and primal weight */
+    double seconds;         /* wall time of the call (batch: admission to completion) */
+    double hbm_bytes;       /* algorithmic plan-pass bytes moved */
+    double rounded_obj;     /* <C, X_feas> of Algorithm 3 when round_plan = 1, else NaN */
+    int32_t returned_average; /* 1 if the returned iterate is the running average */
+} pdot_result;
+
+typedef struct {
+    double rp2;        /* ||X1 - f||^2 + ||X^T1 - g||^2 */
+    double rd2;        /* ||[p 1^T + 1 q^T - C]^+||_F^2 */
+    double cx;         /* <C, X> */
+    double dual;       /* f^T p + g^T q */
+    double gap;
+    double kkt;
+    double rel_p, rel_d, rel_gap, rel_kkt;
+} pdot_kkt_parts;
+
+typedef struct {
+    int64_t m, n;
+    const void *C;          /* device, m x ldc */
+    pdot_dtype c_dtype;
+    int64_t ldc;
+    const double *f, *g;    /* device */
+    double tol;             /* <= 0: the handle's tol */
+    void *X_out;            /* nullable device, m x n in x_dtype */
+    double *p_out, *q_out;  /* nullable device */
+    uint64_t user_tag;
+} pdot_request;
+
+typedef struct pdot_handle pdot_handle;
+
+/* Fill *opt with the defaults listed above. */
+void pdot_default_options(pdot_options *opt);
+
+/* Static string for a status code (never NULL). */
+const char *pdot_status_str(pdot_status s);
+
+/* Message of the last failed call on this handle ("" if none); valid until
+ * the next call on the handle. */
+const char *pdot_last_error(pdot_handle *h);
+
+/* Create a solver handle on CUDA device `device`, issuing work on
+ * `cuda_stream` (a cudaStream_t).  With NULL the handle creates its own
+ * blocking stream, which the CUDA runtime orders with the legacy default
+ * stream.  `opt` may be NULL (defaults).  *out receives the handle. */
+pdot_status pdot_create(const pdot_options *opt, int device, void *cuda_stream, pdot_handle **out);
+
+/* Free every buffer the handle owns.  Waits for its stream.  NULL is a no-op. */
+pdot_status pdot_destroy(pdot_handle *h);
+
+/*
+ * Solve Eq. (1) with restarted PDHG (Algorithm 2 plus the Sec. 5 heuristics)
+ * until the relative KKT error is <= tol (Sec. 5.1 termination).
+ * C: device, dtype c_dtype (F32/BF16 with F32 plans, F64 with F64 plans).
+ * f, g: device FP64.  X_out (m x n, x_dtype), p_out (m), q_out (n): nullable
+ * device outputs of the returned iterate (or of its Algorithm 3 rounding for
+ * X_out when round_plan = 1).  res: required.
+ */
+pdot_status pdot_solve(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                       const double *f, const double *g, double tol,
+                       void *X_out, double *p_out, double *q_out, pdot_result *res);
+
+/* Same as pdot_solve with every pointer in HOST memory; the host <-> device
+ * copies happen inside the call. */
+pdot_status pdot_solve_host(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                            const double *f, const double *g, double tol,
+                            void *X_out, double *p_out, double *q_out, pdot_result *res);
+
+/*
+ * k inner iterations of Algorithm 2 at constant step eta and primal weight
+ * omega (tau = eta/omega, sigma = eta*omega), no restarts, starting from the
+ * device state (X, p, q) and overwriting it with (X^k, p^k, q^k).  The uniform
+ * running averages (Xbar, pbar, qbar) of Algorithm 2 are written when the
+ * pointers are non-null.  k >= 0.
+ */
+pdot_status pdot_pdhg_steps(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                            const double *f, const double *g, int64_t k, double eta, double omega,
+                            void *X, double *p, double *q, void *Xbar_out, double *pbar_out, double *qbar_out);
+
+/* The KKT error of Sec. 3.1 at the device point (X, p, q), with the relative
+ * measures of the handle's rel_mode and R; *out is host memory. */
+pdot_status pdot_kkt(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                     const double *f, const double *g, const void *X, const double *p, const double *q,
+                     pdot_kkt_parts *out);
+
+/* Algorithm 3: write into X_out (device, m x n, x_dtype) the rounding of the
+ * device plan X onto {X >= 0, X1 = f, X^T1 = g}.  X and X_out may alias.
+ * A zero row/column sum keeps scale 1; a zero ||err_r||_1 skips the rank-one term. */
+pdot_status pdot_round(pdot_handle *h, int64_t m, int64_t n, const void *X, const double *f, const double *g,
+                       void *X_out);
+
+/*
+ * Batch engine (continuous batching).  pdot_batch_submit queues `count`
+ * requests and writes one ticket id per request; it never blocks on the GPU.
+ * PDOT_BUSY: a request alone would exceed the HBM budget.  Requests wait in
+ * the queue until memory and a slot are free.  pdot_poll advances the engine
+ * (admits queued requests as memory frees up, launches the next chunk of
+ * iterations for every resident instance, retires finished ones) and returns
+ * up to `cap` finished tickets with their results; *n_done receives the
+ * count.  pdot_poll never waits longer than one chunk.
+ * pdot_cancel removes a queued or running ticket (reported by pdot_poll with
+ * PDOT_CANCELLED).  Request pointers must stay valid until the ticket is
+ * reported.
+ */
+pdot_status pdot_batch_submit(pdot_handle *h, const pdot_request *reqs, int count, uint64_t *ticket_ids);
+pdot_status pdot_poll(pdot_handle *h, uint64_t *done_ids, pdot_result *done_results, int cap, int *n_done);
+pdot_status pdot_cancel(pdot_handle *h, uint64_t ticket);
+/* Counts of queued (not yet admitted) and resident instances. */
+pdot_status pdot_batch_pending(pdot_handle *h, int *queued, int *running);
+
+/* Kernel launches issued by this handle since creation (diagnostics). */
+int64_t pdot_launch_count(pdot_handle *h);
+
+/* Diagnostics for roofline measurement: set up the instance, take three
+ * PDHG steps (so the running average is read), then launch the fused plan
+ * pass `reps` times back to back on the handle's stream between two CUDA
+ * events.  *ms_per_pass receives the mean device time of one pass;
+ * *bytes_per_pass (nullable) the algorithmic bytes one pass moves:
+ * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+). */
+pdot_status pdot_time_pass(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                           const double *f, const double *g, int reps, double *ms_per_pass, double *bytes_per_pass);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDOT_H */

@@ -1,0 +1,1020 @@
+// pdot_engine.cu -- host engine and C ABI (include/pdot.h) of the GB300 PDOT
+// library: workspaces in HBM, the launch sequence of Algorithm 2 with the
+// Sec. 5 controller (one solve = an init check, then chunks of K passes plus
+// one check, captured as CUDA graphs), Algorithm 3 rounding, and the
+// continuous-batching engine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <limits>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pdot.h"
+#include "pdot_internal.h"
+
+using namespace pdot;
+
+namespace pdot {
+int launch_round_rowsum(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
+                        const double* cs, double* rowout, double* colpart, int colparts, void* stream);
+int launch_round_write(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
+                       const double* cs, const double* er, const double* ec, double inv_l1, void* Xout,
+                       long long ldo, const void* C, int ctype, long long ldc, double* objpart, int parts,
+                       void* stream);
+int launch_colreduce(const double* colpart, int parts, long long n, double* out, void* stream);
+}  // namespace pdot
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct CudaError {
+    cudaError_t e;
+};
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) throw CudaError{e_};           \
+    } while (0)
+
+#define CKL(call)                                             \
+    do {                                                      \
+        int e_ = (call);                                      \
+        if (e_ != 0) throw CudaError{(cudaError_t)e_};        \
+    } while (0)
+
+struct ArgError {
+    const char* what;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int ttype_of(int ctype) { return ctype == PDOT_F64 ? TT_F64 : (ctype == PDOT_BF16 ? TT_BF16 : TT_F32); }
+size_t csize_of(int ctype) { return ctype == PDOT_F64 ? 8 : (ctype == PDOT_BF16 ? 2 : 4); }
+size_t xsize_of(int xtype) { return xtype == PDOT_F64 ? 8 : 4; }
+
+// One instance's device buffers (a single cudaMalloc carved into pieces).
+struct Work {
+    long long m = 0, n = 0, ldx = 0;
+    int xtype = 0, tile_rows = 0;
+    int nstrips = 0, nchunks = 0, ntiles = 0, nvt = 0;
+    void* base = nullptr;
+    size_t bytes = 0;
+    void* X = nullptr;
+    double* V = nullptr;
+    double* rowpart = nullptr;
+    double* colpart = nullptr;
+    double* tpart = nullptr;
+    double* vpart = nullptr;
+    Ctrl* ctrl = nullptr;
+    unsigned* ticket = nullptr;
+    // internal copy of C when the caller's layout does not allow 16-byte loads
+    void* Cpad = nullptr;
+    size_t cpad_bytes = 0;
+};
+
+size_t work_bytes(long long m, long long n, int xtype, int tile_rows, Work* w) {
+    const long long ldx = (n + 3) / 4 * 4;
+    const int nstrips = (int)((n + STRIP - 1) / STRIP);
+    const int nchunks = (int)((m + tile_rows - 1) / tile_rows);
+    const long long ntiles = (long long)nstrips * nchunks;
+    const int nvt = (int)((m + n + VT - 1) / VT);
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    const size_t oX = take((size_t)NSLOT * m * ldx * xsize_of(xtype));
+    const size_t oV = take((size_t)NSLOT * 2 * (m + n) * sizeof(double));
+    const size_t oR = take((size_t)nstrips * m * sizeof(double));
+    const size_t oC = take((size_t)nchunks * ldx * sizeof(double));
+    const size_t oT = take((size_t)ntiles * TP * sizeof(double));
+    const size_t oP = take((size_t)nvt * VP * sizeof(double));
+    const size_t oS = take(sizeof(Ctrl));
+    const size_t oK = take(sizeof(unsigned));
+    if (w) {
+        w->m = m; w->n = n; w->ldx = ldx; w->xtype = xtype; w->tile_rows = tile_rows;
+        w->nstrips = nstrips; w->nchunks = nchunks; w->ntiles = (int)ntiles; w->nvt = nvt;
+        char* b = (char*)w->base;
+        w->X = b + oX;
+        w->V = (double*)(b + oV);
+        w->rowpart = (double*)(b + oR);
+        w->colpart = (double*)(b + oC);
+        w->tpart = (double*)(b + oT);
+        w->vpart = (double*)(b + oP);
+        w->ctrl = (Ctrl*)(b + oS);
+        w->ticket = (unsigned*)(b + oK);
+    }
+    return off;
+}
+
+Inst make_inst(const Work& w, const void* C, int ctype, long long ldc, const double* f, const double* g) {
+    Inst I;
+    memset(&I, 0, sizeof(I));
+    I.m = w.m; I.n = w.n; I.ldc = ldc; I.ldx = w.ldx;
+    I.C = C; I.ctype = ctype; I.xtype = w.xtype;
+    I.f = f; I.g = g;
+    I.X = w.X; I.xslot = w.m * w.ldx;
+    I.V = w.V; I.vslot = 2 * (w.m + w.n);
+    I.rowpart = w.rowpart; I.colpart = w.colpart; I.tpart = w.tpart; I.vpart = w.vpart;
+    I.ctrl = w.ctrl; I.ticket = w.ticket;
+    I.nstrips = w.nstrips; I.nchunks = w.nchunks; I.tile_rows = w.tile_rows; I.ntiles = w.ntiles; I.nvt = w.nvt;
+    return I;
+}
+
+struct Graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        exec = nullptr;
+        g = nullptr;
+        kernels = 0;
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct BatchEngine;
+
+struct pdot_handle {
+    pdot_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    LaunchCfg cfg{};
+    LaunchCfg cfg_base{};
+    unsigned* wctr = nullptr;
+    int64_t launches = 0;
+    std::string last_error;
+
+    // single-instance path
+    Work ws;
+    Inst* d_inst = nullptr;
+    TileRef* d_tmap = nullptr;
+    TileRef* d_vmap = nullptr;
+    size_t tmap_cap = 0, vmap_cap = 0;
+    Ctrl* h_ctrl = nullptr;      // pinned
+    Inst* h_inst = nullptr;      // pinned
+    int* h_status = nullptr;     // pinned [2]
+    Graph chunk;                 // K x (pass, dual) + (kkt, checkvec)
+    long long chunk_key[6] = {0, 0, 0, 0, 0, 0};
+    std::map<long long, int> tune_cache;   // (m, n, ttype) -> tile_rows
+    // host staging for pdot_solve_host
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    double* round_scratch = nullptr;
+    size_t round_scratch_bytes = 0;
+
+    BatchEngine* batch = nullptr;
+};
+
+namespace {
+
+void free_work(Work& w) {
+    if (w.base) cudaFree(w.base);
+    if (w.Cpad) cudaFree(w.Cpad);
+    w = Work();
+}
+
+void ensure_work(pdot_handle* h, long long m, long long n, int xtype, int tile_rows) {
+    Work& w = h->ws;
+    if (w.base && w.m == m && w.n == n && w.xtype == xtype && w.tile_rows == tile_rows) return;
+    h->chunk.reset();
+    void* cpad = w.Cpad;
+    size_t cpb = w.cpad_bytes;
+    w.Cpad = nullptr;
+    if (w.base) cudaFree(w.base);
+    w = Work();
+    w.Cpad = cpad;
+    w.cpad_bytes = cpb;
+    const size_t bytes = work_bytes(m, n, xtype, tile_rows, nullptr);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw CudaError{cudaErrorMemoryAllocation};
+    }
+    w.base = base;
+    w.bytes = bytes;
+    work_bytes(m, n, xtype, tile_rows, &w);
+    CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+}
+
+void ensure_maps(pdot_handle* h) {
+    const Work& w = h->ws;
+    if ((size_t)w.ntiles > h->tmap_cap) {
+        if (h->d_tmap) cudaFree(h->d_tmap);
+        h->d_tmap = nullptr;
+        CK(cudaMalloc(&h->d_tmap, sizeof(TileRef) * (size_t)w.ntiles));
+        h->tmap_cap = (size_t)w.ntiles;
+    }
+    if ((size_t)w.nvt > h->vmap_cap) {
+        if (h->d_vmap) cudaFree(h->d_vmap);
+        h->d_vmap = nullptr;
+        CK(cudaMalloc(&h->d_vmap, sizeof(TileRef) * (size_t)w.nvt));
+        h->vmap_cap = (size_t)w.nvt;
+    }
+    std::vector<TileRef> tm((size_t)w.ntiles), vm((size_t)w.nvt);
+    for (int t = 0; t < w.ntiles; ++t) tm[(size_t)t] = TileRef{0, t};
+    for (int t = 0; t < w.nvt; ++t) vm[(size_t)t] = TileRef{0, t};
+    CK(cudaMemcpyAsync(h->d_tmap, tm.data(), sizeof(TileRef) * tm.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_vmap, vm.data(), sizeof(TileRef) * vm.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));   // vectors above are pageable and go out of scope
+}
+
+void validate_marginals(pdot_handle* h, long long m, long long n, const double* f, const double* g, bool host,
+                        double* norm_b) {
+    std::vector<double> hf((size_t)m), hg((size_t)n);
+    if (host) {
+        memcpy(hf.data(), f, sizeof(double) * (size_t)m);
+        memcpy(hg.data(), g, sizeof(double) * (size_t)n);
+    } else {
+        CK(cudaMemcpyAsync(hf.data(), f, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hg.data(), g, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    double sf = 0.0, sg = 0.0, nb = 0.0;
+    for (double v : hf) {
+        if (!(v >= 0.0) || !std::isfinite(v)) throw ArgError{"f has a negative or non-finite entry"};
+        sf += v;
+        nb += v * v;
+    }
+    for (double v : hg) {
+        if (!(v >= 0.0) || !std::isfinite(v)) throw ArgError{"g has a negative or non-finite entry"};
+        sg += v;
+        nb += v * v;
+    }
+    if (std::fabs(sf - sg) > 1e-9 * std::max(sf, 1.0)) throw ArgError{"sum(f) != sum(g)"};
+    *norm_b = std::sqrt(nb);
+}
+
+int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype) {
+    if (h->opt.tile_rows > 0) return h->opt.tile_rows;
+    const long long key = (m * 1000003LL + n) * 4 + ttype;
+    auto it = h->tune_cache.find(key);
+    if (it != h->tune_cache.end()) return it->second;
+    // Enough warp tiles to keep every resident warp busy several times over,
+    // with the tallest tile (fewest column partials) that achieves it.
+    const long long warps = (long long)(ttype == TT_F64 ? h->cfg.tile_blocks_f64 : h->cfg.tile_blocks) * TWARPS;
+    const long long nstrips = (n + STRIP - 1) / STRIP;
+    int tr = 16;
+    for (int cand : {128, 64, 32, 16}) {
+        const long long tiles = nstrips * ((m + cand - 1) / cand);
+        if (tiles >= 4 * warps) { tr = cand; break; }
+    }
+    return tr;
+}
+
+const void* prepare_C(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
+                      long long* ldc_used) {
+    const size_t cs = csize_of(ctype);
+    const size_t need_align = ctype == PDOT_BF16 ? 8 : 16;
+    if (((uintptr_t)C % need_align) == 0 && ldc % 4 == 0) {
+        *ldc_used = ldc;
+        return C;
+    }
+    // Copy into a padded buffer whose rows start on 16-byte boundaries.
+    Work& w = h->ws;
+    const long long ldp = (n + 3) / 4 * 4;
+    const size_t bytes = (size_t)m * ldp * cs;
+    if (w.cpad_bytes < bytes) {
+        if (w.Cpad) cudaFree(w.Cpad);
+        w.Cpad = nullptr;
+        w.cpad_bytes = 0;
+        CK(cudaMalloc(&w.Cpad, bytes));
+        w.cpad_bytes = bytes;
+    }
+    CK(cudaMemcpy2DAsync(w.Cpad, ldp * cs, C, ldc * cs, n * cs, m, cudaMemcpyDeviceToDevice, h->stream));
+    *ldc_used = ldp;
+    return w.Cpad;
+}
+
+void init_ctrl(pdot_handle* h, Ctrl* S, long long m, long long n, double tol, double norm_b, double norm_C,
+               bool fixed, double eta_fixed, double omega_fixed) {
+    const pdot_options& o = h->opt;
+    memset(S, 0, sizeof(Ctrl));
+    S->adaptive_step = fixed ? 0 : o.adaptive_step;
+    S->adaptive_restart = o.adaptive_restart;
+    S->pw_update = o.primal_weight_update;
+    double eta = o.eta0;
+    if (!(eta > 0.0)) eta = S->adaptive_step ? 1.0 / std::sqrt((double)(m + n)) : 0.5 / std::sqrt((double)(m + n));
+    double omega = o.omega0 > 0.0 ? o.omega0 : 1.0;
+    if (fixed) {
+        eta = eta_fixed;
+        omega = omega_fixed;
+    }
+    S->eta = eta;
+    S->omega = omega;
+    S->tau = eta / omega;
+    S->sigma = eta * omega;
+    S->tol = tol;
+    S->beta = o.beta;
+    S->beta_suff = o.beta_suff;
+    S->beta_nec = o.beta_nec;
+    S->beta_art = o.beta_art;
+    S->theta = o.theta;
+    S->R = o.R;
+    S->eps_zero = o.eps_zero;
+    S->rel_mode = o.rel_mode;
+    S->max_passes = o.max_iter > 0 ? o.max_iter : std::numeric_limits<long long>::max() / 4;
+    S->norm_b = norm_b;
+    S->norm_C = norm_C;
+    S->cur = 0; S->anc = 0; S->bar = 1; S->nxt = 2; S->barn = 3;
+    S->status = ST_RUNNING;
+    S->res_slot = 0;
+}
+
+void launch_count(pdot_handle* h, int k) { h->launches += k; }
+
+// Upload the instance descriptor and reset the work counters.
+void stage_instance(pdot_handle* h, const Inst& I) {
+    *h->h_inst = I;
+    CK(cudaMemcpyAsync(h->d_inst, h->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
+}
+
+double compute_norm_C(pdot_handle* h, int ctype) {
+    const Work& w = h->ws;
+    CKL(launch_sumsq_C(ctype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream));
+    launch_count(h, 1);
+    std::vector<double> parts((size_t)w.ntiles * TP);
+    CK(cudaMemcpyAsync(parts.data(), w.tpart, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double s = 0.0;
+    for (int t = 0; t < w.ntiles; ++t) s += parts[(size_t)t * TP];
+    return std::sqrt(s);
+}
+
+void run_check(pdot_handle* h, int ttype, int mode) {
+    const Work& w = h->ws;
+    CKL(launch_kkt(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, mode, h->cfg, h->stream));
+    CKL(launch_checkvec(h->d_inst, h->d_vmap, w.nvt, h->wctr, mode, h->cfg, h->stream));
+    launch_count(h, 2);
+}
+
+void run_step(pdot_handle* h, int ttype) {
+    const Work& w = h->ws;
+    CKL(launch_pass(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream));
+    CKL(launch_dual(h->d_inst, h->d_vmap, w.nvt, h->wctr, h->cfg, h->stream));
+    launch_count(h, 2);
+}
+
+void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
+    for (int s = 0; s < K; ++s) run_step(h, ttype);
+    run_check(h, ttype, MODE_CHECK);
+}
+
+void launch_chunk(pdot_handle* h, int ttype, int K) {
+    const Work& w = h->ws;
+    const long long key[6] = {(long long)(uintptr_t)w.base, (long long)(uintptr_t)h->d_tmap ^ ((long long)(uintptr_t)h->d_vmap << 1),
+                              w.m * 4 + ttype, w.n, K, (long long)h->cfg.pass_u * 1000 + w.tile_rows};
+    if (!h->opt.use_graph) {
+        issue_chunk_kernels(h, ttype, K);
+        return;
+    }
+    if (!h->chunk.exec || memcmp(key, h->chunk_key, sizeof(key)) != 0) {
+        h->chunk.reset();
+        const int64_t before = h->launches;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            issue_chunk_kernels(h, ttype, K);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            h->launches = before;
+            throw;
+        }
+        CK(cudaStreamEndCapture(h->stream, &h->chunk.g));
+        CK(cudaGraphInstantiate(&h->chunk.exec, h->chunk.g, 0));
+        h->chunk.kernels = (int)(h->launches - before);
+        h->launches = before;
+        memcpy(h->chunk_key, key, sizeof(key));
+    }
+    CK(cudaGraphLaunch(h->chunk.exec, h->stream));
+    launch_count(h, h->chunk.kernels);
+}
+
+void fill_result(const Ctrl& S, pdot_result* r, pdot_status st) {
+    r->status = st;
+    r->primal_obj = S.r_cx;
+    r->dual_obj = S.r_dual;
+    r->gap = S.r_gap;
+    r->kkt = S.r_kkt;
+    r->rel_kkt = S.r_rel;
+    r->rel_primal = S.r_rel_p;
+    r->rel_dual = S.r_rel_d;
+    r->rel_gap = S.r_rel_gap;
+    r->iters = S.total;
+    r->passes = S.passes;
+    r->restarts = S.restarts;
+    r->rejected_steps = S.rejected;
+    r->eta = S.eta;
+    r->omega = S.omega;
+    r->returned_average = S.res_avg;
+}
+
+pdot_status map_status(int st) {
+    switch (st) {
+        case ST_OK: return PDOT_OK;
+        case ST_NUMERIC: return PDOT_ERR_NUMERIC;
+        case ST_MAX_ITER: return PDOT_MAX_ITER;
+        case ST_TIMEOUT: return PDOT_TIMEOUT;
+        case ST_CANCELLED: return PDOT_CANCELLED;
+        default: return PDOT_ERR_CUDA;
+    }
+}
+
+// Copy the plan of a slot (m x ldx) out as dense m x n.
+void copy_plan_out(pdot_handle* h, int slot, void* X_out, cudaMemcpyKind kind) {
+    const Work& w = h->ws;
+    const size_t xs = xsize_of(w.xtype);
+    const char* src = (const char*)w.X + (size_t)slot * w.m * w.ldx * xs;
+    CK(cudaMemcpy2DAsync(X_out, (size_t)w.n * xs, src, (size_t)w.ldx * xs, (size_t)w.n * xs, (size_t)w.m, kind,
+                         h->stream));
+}
+
+void copy_duals_out(pdot_handle* h, int slot, double* p_out, double* q_out, cudaMemcpyKind kind) {
+    const Work& w = h->ws;
+    const double* V = w.V + (size_t)slot * 2 * (w.m + w.n);
+    if (p_out) CK(cudaMemcpyAsync(p_out, V, sizeof(double) * (size_t)w.m, kind, h->stream));
+    if (q_out) CK(cudaMemcpyAsync(q_out, V + w.m, sizeof(double) * (size_t)w.n, kind, h->stream));
+}
+
+// Upload a dense m x n plan and its duals into slot 0.
+void upload_state(pdot_handle* h, const void* X, const double* p, const double* q) {
+    const Work& w = h->ws;
+    const size_t xs = xsize_of(w.xtype);
+    CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xs, h->stream));
+    CK(cudaMemcpy2DAsync(w.X, (size_t)w.ldx * xs, X, (size_t)w.n * xs, (size_t)w.n * xs, (size_t)w.m,
+                         cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));
+    CK(cudaMemcpyAsync(w.V, p, sizeof(double) * (size_t)w.m, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(w.V + w.m, q, sizeof(double) * (size_t)w.n, cudaMemcpyDeviceToDevice, h->stream));
+}
+
+void check_common_args(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
+                       const double* f, const double* g) {
+    if (!h) throw ArgError{"null handle"};
+    if (m < 1 || n < 1) throw ArgError{"m and n must be >= 1"};
+    if (ldc < n) throw ArgError{"ldc < n"};
+    if (!C || !f || !g) throw ArgError{"null C, f or g"};
+    if (ctype != PDOT_F32 && ctype != PDOT_BF16 && ctype != PDOT_F64) throw ArgError{"unknown c_dtype"};
+    const int xt = h->opt.x_dtype;
+    if (xt != PDOT_F32 && xt != PDOT_F64) throw ArgError{"x_dtype must be F32 or F64"};
+    if ((xt == PDOT_F64) != (ctype == PDOT_F64))
+        throw ArgError{"F64 plans need F64 costs and F32 plans need F32/BF16 costs"};
+    if (m > (1LL << 31) / 2 || n > (1LL << 31) / 2) throw ArgError{"dimension too large"};
+}
+
+// Algorithm 3 on the plan of `slot` (or an external device plan), writing
+// X_out (dense m x n).  Returns <C, X_feas> when C is given.
+double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const void* Xsrc, long long ldx,
+                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc);
+
+pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
+                       const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
+                       pdot_result* res) {
+    const auto t_start = Clock::now();
+    if (!res) throw ArgError{"null result"};
+    check_common_args(h, m, n, C, ctype, ldc, f, g);
+    if (!(tol > 0.0)) throw ArgError{"tol must be > 0"};
+    double norm_b = 0.0;
+    validate_marginals(h, m, n, f, g, false, &norm_b);
+    const int ttype = ttype_of(ctype);
+    const int tr = pick_tile_rows(h, m, n, ttype);
+    ensure_work(h, m, n, h->opt.x_dtype, tr);
+    ensure_maps(h);
+    Work& w = h->ws;
+    long long ldc_used = ldc;
+    const void* Cd = prepare_C(h, m, n, C, ctype, ldc, &ldc_used);
+    const Inst I = make_inst(w, Cd, ctype, ldc_used, f, g);
+    stage_instance(h, I);
+    const double norm_C = compute_norm_C(h, ctype);
+
+    Ctrl* S = h->h_ctrl;
+    init_ctrl(h, S, m, n, tol, norm_b, norm_C, false, 0.0, 0.0);
+    CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    const size_t xs = xsize_of(w.xtype);
+    CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xs, h->stream));                 // X = 0 (C1)
+    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));  // p = q = 0
+    CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+    run_check(h, ttype, MODE_INIT);
+
+    const int K = std::max(1, h->opt.restart_check_every);
+    const double tlim = h->opt.time_limit_s;
+    int status = ST_RUNNING;
+    bool timed_out = false;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    try {
+        // Keep two chunks in flight: the host reads chunk i's status while
+        // chunk i+1 runs (a chunk issued after termination is a no-op).
+        long long i = 0;
+        launch_chunk(h, ttype, K);
+        CK(cudaMemcpyAsync(&h->h_status[0], &w.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaEventRecord(ev[0], h->stream));
+        for (;;) {
+            launch_chunk(h, ttype, K);
+            const int nb = (int)((i + 1) & 1);
+            CK(cudaMemcpyAsync(&h->h_status[nb], &w.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaEventRecord(ev[nb], h->stream));
+            CK(cudaEventSynchronize(ev[i & 1]));
+            status = h->h_status[i & 1];
+            if (status != ST_RUNNING) break;
+            if (tlim > 0.0 && std::chrono::duration<double>(Clock::now() - t_start).count() > tlim) {
+                timed_out = true;
+                break;
+            }
+            ++i;
+        }
+        CK(cudaStreamSynchronize(h->stream));
+    } catch (...) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        throw;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (timed_out && S->status == ST_RUNNING) {
+        // Evaluate the current iterate and report it.
+        run_check(h, ttype, MODE_INIT);
+        CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (S->status == ST_RUNNING) {
+            S->status = ST_TIMEOUT;
+            S->res_slot = S->cur;
+            S->res_avg = 0;
+        }
+    }
+    const pdot_status st = map_status(S->status);
+    fill_result(*S, res, st);
+    const double mn = (double)m * (double)n;
+    const double bc = (double)csize_of(ctype), bx = (double)xsize_of(w.xtype);
+    res->hbm_bytes = (double)S->passes * mn * (bc + 4.0 * bx) + (double)S->checks * mn * (bc + 3.0 * bx);
+    res->rounded_obj = std::numeric_limits<double>::quiet_NaN();
+    const int slot = S->res_slot;
+    const char* Xslot = (const char*)w.X + (size_t)slot * (size_t)(w.m * w.ldx) * xsize_of(w.xtype);
+    if (h->opt.round_plan) {
+        res->rounded_obj = round_plan_dev(h, w.m, w.n, w.xtype, Xslot, w.ldx, f, g, X_out, Cd, ctype, ldc_used);
+    } else if (X_out) {
+        copy_plan_out(h, slot, X_out, cudaMemcpyDeviceToDevice);
+    }
+    copy_duals_out(h, slot, p_out, q_out, cudaMemcpyDeviceToDevice);
+    CK(cudaStreamSynchronize(h->stream));
+    res->seconds = std::chrono::duration<double>(Clock::now() - t_start).count();
+    return st;
+}
+
+template <typename F>
+pdot_status guarded(pdot_handle* h, F&& fn) {
+    try {
+        return fn();
+    } catch (const ArgError& e) {
+        if (h) h->last_error = e.what;
+        return PDOT_ERR_ARG;
+    } catch (const CudaError& e) {
+        if (h) h->last_error = cudaGetErrorString(e.e);
+        if (e.e == cudaErrorMemoryAllocation) return PDOT_ERR_OOM;
+        return PDOT_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        if (h) h->last_error = "host allocation failed";
+        return PDOT_ERR_OOM;
+    } catch (...) {
+        if (h) h->last_error = "unexpected exception";
+        return PDOT_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 (rounding)
+// ---------------------------------------------------------------------------
+namespace {
+double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const void* Xsrc, long long ldx,
+                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc) {
+    const int parts = 64;   // column-partial rows (fixed order)
+    const size_t need = sizeof(double) * (size_t)(4 * m + 4 * n + (size_t)parts * n + parts + 8);
+    if (h->round_scratch_bytes < need) {
+        if (h->round_scratch) cudaFree(h->round_scratch);
+        h->round_scratch = nullptr;
+        h->round_scratch_bytes = 0;
+        CK(cudaMalloc(&h->round_scratch, need));
+        h->round_scratch_bytes = need;
+    }
+    double* xs = h->round_scratch;      // row scales (m)
+    double* ys = xs + m;                // column scales (n)
+    double* rsum = ys + n;              // row sums (m)
+    double* csum = rsum + m;            // column sums (n)
+    double* er = csum + n;              // err_r (m)
+    double* ec = er + m;                // err_c (n)
+    double* colpart = ec + n;           // parts x n
+    double* objpart = colpart + (size_t)parts * n;
+    void* out = X_out;
+    void* tmp = nullptr;
+    if (!out) {
+        CK(cudaMalloc(&tmp, (size_t)m * n * xsize_of(xtype)));
+        out = tmp;
+    }
+    // 1) r = X1 -> x_i = min(f_i / r_i, 1)
+    CKL(launch_round_rowsum(Xsrc, xtype, m, n, ldx, nullptr, nullptr, rsum, colpart, parts, h->stream));
+    // 2) column sums of diag(x) X -> y_j = min(g_j / c_j, 1)
+    // 3) row and column sums of diag(x) X diag(y) -> err_r, err_c
+    // The host drives the scalar glue with tiny vector kernels inside the launcher file.
+    CKL(launch_colreduce(colpart, parts, n, csum, h->stream));
+    launch_count(h, 2);
+    // Scales are computed on the host from the sums (O(m+n), once per solve).
+    std::vector<double> hr((size_t)m), hc((size_t)n), hf((size_t)m), hg((size_t)n), hx((size_t)m), hy((size_t)n);
+    CK(cudaMemcpyAsync(hr.data(), rsum, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(hf.data(), f, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(hg.data(), g, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < m; ++i) hx[(size_t)i] = hr[(size_t)i] > 0.0 ? std::min(hf[(size_t)i] / hr[(size_t)i], 1.0) : 1.0;
+    CK(cudaMemcpyAsync(xs, hx.data(), sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+    CKL(launch_round_rowsum(Xsrc, xtype, m, n, ldx, xs, nullptr, rsum, colpart, parts, h->stream));
+    CKL(launch_colreduce(colpart, parts, n, csum, h->stream));
+    launch_count(h, 2);
+    CK(cudaMemcpyAsync(hc.data(), csum, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (long long j = 0; j < n; ++j) hy[(size_t)j] = hc[(size_t)j] > 0.0 ? std::min(hg[(size_t)j] / hc[(size_t)j], 1.0) : 1.0;
+    CK(cudaMemcpyAsync(ys, hy.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CKL(launch_round_rowsum(Xsrc, xtype, m, n, ldx, xs, ys, rsum, colpart, parts, h->stream));
+    CKL(launch_colreduce(colpart, parts, n, csum, h->stream));
+    launch_count(h, 2);
+    CK(cudaMemcpyAsync(hr.data(), rsum, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(hc.data(), csum, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double l1 = 0.0;
+    for (long long i = 0; i < m; ++i) { hr[(size_t)i] = hf[(size_t)i] - hr[(size_t)i]; l1 += std::fabs(hr[(size_t)i]); }
+    for (long long j = 0; j < n; ++j) hc[(size_t)j] = hg[(size_t)j] - hc[(size_t)j];
+    CK(cudaMemcpyAsync(er, hr.data(), sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(ec, hc.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    const double inv_l1 = l1 > 0.0 ? 1.0 / l1 : 0.0;
+    // 4) X_feas = diag(x) X diag(y) + err_r err_c^T / ||err_r||_1, and <C, X_feas>
+    CKL(launch_round_write(Xsrc, xtype, m, n, ldx, xs, ys, er, ec, inv_l1, out, n, C, ctype, ldc, objpart, parts,
+                           h->stream));
+    launch_count(h, 1);
+    std::vector<double> ho((size_t)parts);
+    CK(cudaMemcpyAsync(ho.data(), objpart, sizeof(double) * parts, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (tmp) cudaFree(tmp);
+    double obj = 0.0;
+    for (int k = 0; k < parts; ++k) obj += ho[(size_t)k];
+    return obj;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void pdot_default_options(pdot_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->tol = 1e-4;
+    o->max_iter = 0;
+    o->time_limit_s = 0.0;
+    o->restart_check_every = 64;
+    o->adaptive_step = 1;
+    o->adaptive_restart = 1;
+    o->primal_weight_update = 1;
+    o->beta = 0.2;
+    o->beta_suff = 0.1;
+    o->beta_nec = 0.9;
+    o->beta_art = 0.36;
+    o->theta = 0.5;
+    o->eta0 = 0.0;
+    o->omega0 = 1.0;
+    o->R = 1.0;
+    o->eps_zero = 1e-10;
+    o->rel_mode = 0;
+    o->x_dtype = PDOT_F32;
+    o->round_plan = 0;
+    o->use_graph = 1;
+    o->tile_rows = 0;
+    o->hbm_budget_bytes = 0;
+    o->max_batch_slots = 4096;
+    o->chunk_checks = 4;
+}
+
+const char* pdot_status_str(pdot_status s) {
+    switch (s) {
+        case PDOT_OK: return "PDOT_OK";
+        case PDOT_ERR_ARG: return "PDOT_ERR_ARG";
+        case PDOT_ERR_OOM: return "PDOT_ERR_OOM";
+        case PDOT_ERR_CUDA: return "PDOT_ERR_CUDA";
+        case PDOT_ERR_NUMERIC: return "PDOT_ERR_NUMERIC";
+        case PDOT_MAX_ITER: return "PDOT_MAX_ITER";
+        case PDOT_TIMEOUT: return "PDOT_TIMEOUT";
+        case PDOT_BUSY: return "PDOT_BUSY";
+        case PDOT_PENDING: return "PDOT_PENDING";
+        case PDOT_CANCELLED: return "PDOT_CANCELLED";
+    }
+    return "PDOT_UNKNOWN";
+}
+
+const char* pdot_last_error(pdot_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, pdot_handle** out) {
+    if (!out) return PDOT_ERR_ARG;
+    *out = nullptr;
+    pdot_handle* h = new (std::nothrow) pdot_handle();
+    if (!h) return PDOT_ERR_OOM;
+    if (opt) h->opt = *opt;
+    else pdot_default_options(&h->opt);
+    pdot_status st = guarded(h, [&]() -> pdot_status {
+        if (h->opt.restart_check_every < 1) throw ArgError{"restart_check_every < 1"};
+        if (h->opt.tile_rows < 0 || h->opt.tile_rows > 256 || h->opt.tile_rows % 8 != 0) {
+            throw ArgError{"tile_rows must be 0 or a multiple of 8 in [8, 256]"};
+        }
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        if (device < 0 || device >= ndev) throw ArgError{"no such CUDA device"};
+        h->device = device;
+        CK(cudaSetDevice(device));
+        CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device));
+        if (cuda_stream) {
+            h->stream = (cudaStream_t)cuda_stream;
+        } else {
+            // A blocking stream: ordered with the legacy default stream, and capturable.
+            CK(cudaStreamCreate(&h->stream));
+            h->own_stream = true;
+        }
+        h->cfg.tile_blocks = h->sm_count * occupancy_tile_blocks_per_sm(TT_F32);
+        h->cfg.tile_blocks_f64 = h->sm_count * occupancy_tile_blocks_per_sm(TT_F64);
+        h->cfg.vec_blocks = h->sm_count * occupancy_vec_blocks_per_sm();
+        h->cfg.pass_u = 2;
+        const char* pu = getenv("PDOT_PASS_U");
+        if (pu && atoi(pu) == 4) h->cfg.pass_u = 4;
+        h->cfg_base = h->cfg;
+        CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
+        CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));
+        CK(cudaMalloc(&h->d_inst, sizeof(Inst)));
+        CK(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
+        CK(cudaMallocHost(&h->h_inst, sizeof(Inst)));
+        CK(cudaMallocHost(&h->h_status, 2 * sizeof(int)));
+        return PDOT_OK;
+    });
+    if (st != PDOT_OK) {
+        pdot_destroy(h);
+        return st;
+    }
+    *out = h;
+    return PDOT_OK;
+}
+
+void pdot_batch_destroy(pdot_handle* h);
+
+pdot_status pdot_destroy(pdot_handle* h) {
+    if (!h) return PDOT_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    pdot_batch_destroy(h);
+    h->chunk.reset();
+    free_work(h->ws);
+    if (h->d_tmap) cudaFree(h->d_tmap);
+    if (h->d_vmap) cudaFree(h->d_vmap);
+    if (h->d_inst) cudaFree(h->d_inst);
+    if (h->wctr) cudaFree(h->wctr);
+    if (h->round_scratch) cudaFree(h->round_scratch);
+    if (h->stage) cudaFree(h->stage);
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    if (h->h_inst) cudaFreeHost(h->h_inst);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return PDOT_OK;
+}
+
+pdot_status pdot_solve(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                       const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
+                       pdot_result* res) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        return solve_impl(h, m, n, C, c_dtype, ldc, f, g, tol, X_out, p_out, q_out, res);
+    });
+}
+
+pdot_status pdot_solve_host(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                            const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
+                            pdot_result* res) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        if (m < 1 || n < 1 || ldc < n || !C || !f || !g) throw ArgError{"bad arguments"};
+        const size_t cs = csize_of(c_dtype);
+        const size_t xs = xsize_of(h->opt.x_dtype);
+        const long long ldp = (n + 3) / 4 * 4;
+        const size_t bC = align_up((size_t)m * ldp * cs, 256);
+        const size_t bf = align_up(sizeof(double) * (size_t)m, 256), bg = align_up(sizeof(double) * (size_t)n, 256);
+        const size_t bX = X_out ? align_up((size_t)m * n * xs, 256) : 0;
+        const size_t bp = p_out ? bf : 0, bq = q_out ? bg : 0;
+        const size_t need = bC + bf + bg + bX + bp + bq;
+        if (h->stage_bytes < need) {
+            if (h->stage) cudaFree(h->stage);
+            h->stage = nullptr;
+            h->stage_bytes = 0;
+            CK(cudaMalloc(&h->stage, need));
+            h->stage_bytes = need;
+        }
+        char* b = (char*)h->stage;
+        void* dC = b;
+        double* df = (double*)(b + bC);
+        double* dg = (double*)(b + bC + bf);
+        void* dX = X_out ? (void*)(b + bC + bf + bg) : nullptr;
+        double* dp = p_out ? (double*)(b + bC + bf + bg + bX) : nullptr;
+        double* dq = q_out ? (double*)(b + bC + bf + bg + bX + bp) : nullptr;
+        CK(cudaMemcpy2DAsync(dC, ldp * cs, C, (size_t)ldc * cs, (size_t)n * cs, (size_t)m, cudaMemcpyHostToDevice,
+                             h->stream));
+        CK(cudaMemcpyAsync(df, f, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(dg, g, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+        pdot_status st = solve_impl(h, m, n, dC, c_dtype, ldp, df, dg, tol, dX, dp, dq, res);
+        const auto t0 = Clock::now();
+        if (X_out) CK(cudaMemcpyAsync(X_out, dX, (size_t)m * n * xs, cudaMemcpyDeviceToHost, h->stream));
+        if (p_out) CK(cudaMemcpyAsync(p_out, dp, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+        if (q_out) CK(cudaMemcpyAsync(q_out, dq, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        res->seconds += std::chrono::duration<double>(Clock::now() - t0).count();
+        return st;
+    });
+}
+
+pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                            const double* f, const double* g, int64_t k, double eta, double omega, void* X, double* p,
+                            double* q, void* Xbar_out, double* pbar_out, double* qbar_out) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        check_common_args(h, m, n, C, c_dtype, ldc, f, g);
+        if (k < 0 || !(eta > 0.0) || !(omega > 0.0) || !X || !p || !q) throw ArgError{"bad k, eta, omega or state"};
+        const int ttype = ttype_of(c_dtype);
+        const int tr = pick_tile_rows(h, m, n, ttype);
+        ensure_work(h, m, n, h->opt.x_dtype, tr);
+        ensure_maps(h);
+        Work& w = h->ws;
+        long long ldc_used = ldc;
+        const void* Cd = prepare_C(h, m, n, C, c_dtype, ldc, &ldc_used);
+        stage_instance(h, make_inst(w, Cd, c_dtype, ldc_used, f, g));
+        Ctrl* S = h->h_ctrl;
+        init_ctrl(h, S, m, n, -1.0, 1.0, 1.0, true, eta, omega);
+        S->adaptive_restart = 0;
+        S->pw_update = 0;
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+        upload_state(h, X, p, q);
+        run_check(h, ttype, MODE_INIT);   // row/column sums of the starting plan
+        for (int64_t s = 0; s < k; ++s) run_step(h, ttype);
+        CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (S->status == ST_NUMERIC) return PDOT_ERR_NUMERIC;
+        const int cur = S->cur, bar = k > 0 ? S->bar : S->cur;
+        copy_plan_out(h, cur, X, cudaMemcpyDeviceToDevice);
+        copy_duals_out(h, cur, p, q, cudaMemcpyDeviceToDevice);
+        if (Xbar_out) copy_plan_out(h, bar, Xbar_out, cudaMemcpyDeviceToDevice);
+        copy_duals_out(h, bar, pbar_out, qbar_out, cudaMemcpyDeviceToDevice);
+        CK(cudaStreamSynchronize(h->stream));
+        return PDOT_OK;
+    });
+}
+
+pdot_status pdot_kkt(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                     const double* f, const double* g, const void* X, const double* p, const double* q,
+                     pdot_kkt_parts* out) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        check_common_args(h, m, n, C, c_dtype, ldc, f, g);
+        if (!X || !p || !q || !out) throw ArgError{"null X, p, q or out"};
+        double norm_b = 0.0;
+        validate_marginals(h, m, n, f, g, false, &norm_b);
+        const int ttype = ttype_of(c_dtype);
+        const int tr = pick_tile_rows(h, m, n, ttype);
+        ensure_work(h, m, n, h->opt.x_dtype, tr);
+        ensure_maps(h);
+        Work& w = h->ws;
+        long long ldc_used = ldc;
+        const void* Cd = prepare_C(h, m, n, C, c_dtype, ldc, &ldc_used);
+        stage_instance(h, make_inst(w, Cd, c_dtype, ldc_used, f, g));
+        const double norm_C = compute_norm_C(h, c_dtype);
+        Ctrl* S = h->h_ctrl;
+        init_ctrl(h, S, m, n, -1.0, norm_b, norm_C, false, 0.0, 0.0);
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+        upload_state(h, X, p, q);
+        run_check(h, ttype, MODE_INIT);
+        CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        out->rp2 = S->r_rp2; out->rd2 = S->r_rd2; out->cx = S->r_cx; out->dual = S->r_dual; out->gap = S->r_gap;
+        out->kkt = S->r_kkt; out->rel_p = S->r_rel_p; out->rel_d = S->r_rel_d; out->rel_gap = S->r_rel_gap;
+        out->rel_kkt = S->r_rel;
+        return PDOT_OK;
+    });
+}
+
+pdot_status pdot_round(pdot_handle* h, int64_t m, int64_t n, const void* X, const double* f, const double* g,
+                       void* X_out) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        if (m < 1 || n < 1 || !X || !f || !g || !X_out) throw ArgError{"bad arguments"};
+        const int xt = h->opt.x_dtype;
+        if (xt != PDOT_F32 && xt != PDOT_F64) throw ArgError{"x_dtype must be F32 or F64"};
+        round_plan_dev(h, m, n, xt, X, n, f, g, X_out, nullptr, 0, 0);
+        CK(cudaStreamSynchronize(h->stream));
+        return PDOT_OK;
+    });
+}
+
+int64_t pdot_launch_count(pdot_handle* h) { return h ? h->launches : 0; }
+
+pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                           const double* f, const double* g, int reps, double* ms_per_pass, double* bytes_per_pass) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        check_common_args(h, m, n, C, c_dtype, ldc, f, g);
+        if (reps < 1 || !ms_per_pass) throw ArgError{"reps < 1 or null output"};
+        const int ttype = ttype_of(c_dtype);
+        const int tr = pick_tile_rows(h, m, n, ttype);
+        ensure_work(h, m, n, h->opt.x_dtype, tr);
+        ensure_maps(h);
+        Work& w = h->ws;
+        long long ldc_used = ldc;
+        const void* Cd = prepare_C(h, m, n, C, c_dtype, ldc, &ldc_used);
+        stage_instance(h, make_inst(w, Cd, c_dtype, ldc_used, f, g));
+        Ctrl* S = h->h_ctrl;
+        init_ctrl(h, S, m, n, -1.0, 1.0, 1.0, true, 0.5 / std::sqrt((double)(m + n)), 1.0);
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xsize_of(w.xtype), h->stream));
+        CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));
+        run_check(h, ttype, MODE_INIT);
+        for (int s = 0; s < 3; ++s) run_step(h, ttype);   // steady state: k > 0, the average is read
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        // The plan pass alone, repeated on the same state (roles do not change
+        // without the dual kernel), so every launch moves the same bytes.
+        CK(cudaEventRecord(e0, h->stream));
+        // Alternate two work counters: each launch resets every counter but
+        // its own, so the next launch finds its counter at zero.
+        for (int r = 0; r < reps; ++r) {
+            const int wc = (r & 1) ? wc_index(WC_AUX, ttype) : wc_index(WC_PASS, ttype);
+            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream, wc));
+        }
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        launch_count(h, reps);
+        *ms_per_pass = (double)ms / reps;
+        if (bytes_per_pass)
+            *bytes_per_pass = (double)m * (double)n * ((double)csize_of(c_dtype) + 4.0 * (double)xsize_of(w.xtype));
+        return PDOT_OK;
+    });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batch engine (placeholder until the continuous-batching engine lands)
+// ---------------------------------------------------------------------------
+extern "C" {
+void pdot_batch_destroy(pdot_handle*) {}
+pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request*, int, uint64_t*) {
+    if (h) h->last_error = "batch engine not available";
+    return PDOT_ERR_ARG;
+}
+pdot_status pdot_poll(pdot_handle* h, uint64_t*, pdot_result*, int, int* n_done) {
+    if (n_done) *n_done = 0;
+    if (h) h->last_error = "batch engine not available";
+    return PDOT_ERR_ARG;
+}
+pdot_status pdot_cancel(pdot_handle*, uint64_t) { return PDOT_ERR_ARG; }
+pdot_status pdot_batch_pending(pdot_handle*, int* queued, int* running) {
+    if (queued) *queued = 0;
+    if (running) *running = 0;
+    return PDOT_OK;
+}
+}

@@ -1,0 +1,114 @@
+// pdot_internal.h -- device-side data structures shared by the sm_103a kernels
+// (pdot_kernels.cu) and the host engine (pdot_engine.cu).
+//
+// Layout in HBM, per instance (m rows, n columns, ldx = n rounded up to 4):
+//   X    : NSLOT plan buffers of m * ldx elements (FP32 or FP64).  Roles
+//          (current, next, average, next average, restart anchor) are slot
+//          indices kept in Ctrl, so accepting a step, rejecting it or
+//          restarting swaps indices instead of copying m*n data.
+//   V    : NSLOT vector sets of 2(m+n) doubles, one per plan slot:
+//          [p (m) | q (n) | r = X1 (m) | c = X^T1 (n)].
+//   rowpart[nstrips][m], colpart[nchunks][ldx]: FP64 partial row/column sums
+//          written by the plan-tile kernels and reduced in a fixed order.
+//   tpart[ntiles][TP], vpart[nvt][VP]: FP64 per-tile scalar partials.
+//   Ctrl : the scalar state of Algorithm 2 and the Sec. 5 controller.
+#pragma once
+#include <cstdint>
+
+namespace pdot {
+
+constexpr int NSLOT = 5;
+constexpr int STRIP = 128;   // plan-tile width: 32 lanes x 4 consecutive columns
+constexpr int TWARPS = 8;    // warps per CTA in the plan-tile kernels
+constexpr int VT = 256;      // entries per vector tile = threads per CTA in vector kernels
+constexpr int TP = 6;        // scalars per plan-tile partial
+constexpr int VP = 12;       // scalars per vector-tile partial
+
+constexpr int ST_RUNNING = -1;
+constexpr int MODE_CHECK = 0;
+constexpr int MODE_INIT = 1;
+
+// Status codes (same values as pdot_status in include/pdot.h).
+constexpr int ST_OK = 0, ST_NUMERIC = 4, ST_MAX_ITER = 5, ST_TIMEOUT = 6, ST_CANCELLED = 9;
+
+struct Ctrl {
+    // iteration state
+    double eta, omega, tau, sigma;
+    double kkt0, kkt_prev;
+    long long k, total, passes, restarts, rejected, checks;
+    int cur, nxt, bar, barn, anc;
+    int status;          // ST_RUNNING or a final status
+    int res_slot, res_avg;
+    // options
+    double tol, beta, beta_suff, beta_nec, beta_art, theta, R, eps_zero;
+    long long max_passes;
+    int adaptive_step, adaptive_restart, pw_update, rel_mode;
+    // data norms ||[f;g]||_2 and ||C||_F
+    double norm_b, norm_C;
+    // parts of the reported point (last init/check candidate)
+    double r_rp2, r_rd2, r_cx, r_dual, r_gap, r_kkt, r_rel_p, r_rel_d, r_rel_gap, r_rel;
+    // diagnostics of the last pass
+    double last_etabar, last_dX2, last_dy2, last_inter;
+};
+
+struct Inst {
+    long long m, n, ldc, ldx;
+    const void* C;
+    int ctype;           // 0 FP32, 1 BF16, 2 FP64 (pdot_dtype)
+    int xtype;           // 0 FP32, 2 FP64
+    const double* f;
+    const double* g;
+    void* X;             // NSLOT slots of xslot elements
+    long long xslot;
+    double* V;           // NSLOT vector sets of vslot doubles
+    long long vslot;
+    double* rowpart;
+    double* colpart;
+    double* tpart;
+    double* vpart;
+    Ctrl* ctrl;
+    unsigned int* ticket;
+    int nstrips, nchunks, tile_rows, ntiles, nvt, pad_;
+};
+
+struct TileRef {
+    int inst;
+    int local;
+};
+
+// Plan-kernel type combinations (cost dtype / plan dtype).
+constexpr int TT_F32 = 0;    // FP32 C, FP32 X
+constexpr int TT_BF16 = 1;   // BF16 C, FP32 X
+constexpr int TT_F64 = 2;    // FP64 C, FP64 X
+constexpr int NTT = 3;
+
+// Work counters of the tile-queue kernels, one per (phase, type).  Every
+// kernel resets all counters but its own when it starts: kernels on one
+// stream run in order, so the previous user of a counter has finished.  The
+// same (phase, type) kernel never runs twice in a row.
+constexpr int WC_PASS = 0, WC_DUAL = 1, WC_KKT = 2, WC_CHECK = 3, WC_AUX = 4;
+constexpr int WC_N = 5 * NTT;
+__host__ __device__ constexpr int wc_index(int phase, int ttype) { return phase * NTT + ttype; }
+
+// Host-side launchers (pdot_kernels.cu).  All are asynchronous on `stream`
+// and return 0 or a cudaError_t code.
+struct LaunchCfg {
+    int tile_blocks;      // CTAs of the FP32-plan tile kernels (8 warps each)
+    int tile_blocks_f64;  // CTAs of the FP64-plan tile kernels
+    int vec_blocks;       // CTAs of the vector kernels (256 threads each)
+    int pass_u;           // rows per load batch in the FP32-plan pass (2 or 4)
+};
+
+int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
+                void* stream, int wc_override = -1);
+int launch_dual(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, const LaunchCfg& cfg, void* stream);
+int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, int mode,
+               const LaunchCfg& cfg, void* stream);
+int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, int mode, const LaunchCfg& cfg,
+                    void* stream);
+int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
+                   void* stream);
+int occupancy_tile_blocks_per_sm(int ttype);
+int occupancy_vec_blocks_per_sm();
+
+}  // namespace pdot

@@ -1,0 +1,866 @@
+// pdot_kernels.cu -- sm_103a kernels of restarted PDHG for optimal transport
+// (arXiv 2407.19689, Algorithm 2 with the Sec. 5 controller).
+//
+// One iteration = two launches over a multi-instance work queue:
+//   k_pass  (plan tiles, HBM-bound): one read of C, X, Xbar and one write of
+//           X+, Xbar+ per element.  Computes the projected primal step of
+//           Algorithm 2, X+ = max(0, X - tau (C - p 1^T - 1 q^T)), the running
+//           average, and in registers the row sums of X+ (warp shuffles), the
+//           column sums of X+ (per-lane accumulators) and ||X+ - X||^2.
+//   k_dual  (vector tiles, O(m+n)): fixed-order reduction of the partial sums,
+//           the dual updates p+ = p + sigma (f - (2 r+ - r)),
+//           q+ = q + sigma (g - (2 c+ - c)) (r = X 1, c = X^T 1 of the current
+//           plan, so 2X+ - X is never re-read), the average of (p, q), and the
+//           step-size reductions.  The last vector tile of each instance
+//           (atomic ticket) runs the scalar controller: PDLP step-size test,
+//           accept/reject by swapping slot roles.
+// Every K passes:
+//   k_kkt      (plan tiles): reads C, X, Xbar, anchor once; <C,X>, <C,Xbar>,
+//              ||[p1^T+1q^T-C]^+||^2 for the current and the average duals,
+//              distances to the restart anchor, and exact row/column sums of
+//              the stored average.
+//   k_checkvec (vector tiles): primal residuals, dual objectives, dual
+//              distances; the last tile per instance runs the restart /
+//              termination / primal-weight logic of Sec. 5.
+// The path is a streaming stencil plus reductions: no tensor cores.  Plan
+// tiles are one warp wide (128 columns, 16-byte loads per lane) and
+// `tile_rows` tall, handed out by an atomic queue so uneven batches balance.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "pdot_internal.h"
+
+namespace pdot {
+
+constexpr int KU = 2;   // rows per load batch in the KKT pass
+
+// ---------------------------------------------------------------------------
+// loads and stores of 4 consecutive elements
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+__device__ __forceinline__ float bf16_bits_to_f32(unsigned int h) { return __uint_as_float(h << 16); }
+
+// Cost entries (read-only for the whole solve: non-coherent path).
+template <typename A>
+__device__ __forceinline__ void ldc4(const float* p, A (&v)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = (A)t.x; v[1] = (A)t.y; v[2] = (A)t.z; v[3] = (A)t.w;
+}
+template <typename A>
+__device__ __forceinline__ void ldc4(const unsigned short* p, A (&v)[4]) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = (A)bf16_bits_to_f32(t.x & 0xffffu);
+    v[1] = (A)bf16_bits_to_f32(t.x >> 16);
+    v[2] = (A)bf16_bits_to_f32(t.y & 0xffffu);
+    v[3] = (A)bf16_bits_to_f32(t.y >> 16);
+}
+template <typename A>
+__device__ __forceinline__ void ldc4(const double* p, A (&v)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = (A)a.x; v[1] = (A)a.y; v[2] = (A)b.x; v[3] = (A)b.y;
+}
+// Ragged right edge: only the first `cnt` (< 4) entries exist.
+template <typename A>
+__device__ __forceinline__ void ldc4_tail(const float* p, long long cnt, A (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = e < cnt ? (A)__ldg(p + e) : A(0);
+}
+template <typename A>
+__device__ __forceinline__ void ldc4_tail(const unsigned short* p, long long cnt, A (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = e < cnt ? (A)bf16_bits_to_f32(__ldg(p + e)) : A(0);
+}
+template <typename A>
+__device__ __forceinline__ void ldc4_tail(const double* p, long long cnt, A (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = e < cnt ? (A)__ldg(p + e) : A(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    // Butterfly: every lane ends with the same, order-fixed sum.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV doubles over a 256-thread block in a fixed order; result in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NV + k];
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename TX>
+__device__ __forceinline__ TX* slot_x(const Inst& I, int s) {
+    return reinterpret_cast<TX*>(I.X) + (long long)s * I.xslot;
+}
+__device__ __forceinline__ double* slot_v(const Inst& I, int s) { return I.V + (long long)s * I.vslot; }
+
+// Warp-level work queue.
+__device__ __forceinline__ int warp_next(unsigned* ctr) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = (int)atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+__device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int c = 0; c < WC_N; ++c)
+            if (c != mine) wctr[c] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plan pass: Algorithm 2 primal step + running average + partial sums
+// ---------------------------------------------------------------------------
+template <typename TC, typename TX, int U>
+__device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, int lane) {
+    typedef TX A;
+    const long long m = I.m, n = I.n, ldx = I.ldx, ldc = I.ldc;
+    const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
+    const long long j0 = (long long)strip * STRIP + lane * 4;
+    const long long i0 = (long long)chunk * I.tile_rows;
+    const long long i1 = min(i0 + (long long)I.tile_rows, m);
+    const bool on = j0 < n;
+    const bool full = j0 + 4 <= n;
+    const TC* C = reinterpret_cast<const TC*>(I.C);
+    const TX* X = slot_x<TX>(I, S.cur);
+    const TX* Xb = slot_x<TX>(I, S.bar);
+    TX* Xn = slot_x<TX>(I, S.nxt);
+    TX* Xbn = slot_x<TX>(I, S.barn);
+    const double* p = slot_v(I, S.cur);
+    const double* q = p + m;
+    const bool first = S.k == 0;
+    const A tau = (A)S.tau;
+    const A w = (A)(1.0 / (double)(S.k + 1));
+
+    A qv[4];
+    bool valid[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        valid[e] = j0 + e < n;
+        qv[e] = valid[e] ? (A)q[j0 + e] : A(0);
+    }
+    double cs[4] = {0.0, 0.0, 0.0, 0.0};
+    double dx2 = 0.0;
+    double* rowpart = I.rowpart + (long long)strip * m;
+    // Row pointers advanced by the leading dimensions (lanes past n never dereference).
+    const TC* Cr = C + i0 * ldc + j0;
+    const long long xo = i0 * ldx + j0;
+    const TX* Xr = X + xo;
+    const TX* Xbr = Xb + xo;
+    TX* Xnr = Xn + xo;
+    TX* Xbnr = Xbn + xo;
+    const long long ccnt = n - j0;
+
+    for (long long ib = i0; ib < i1; ib += U) {
+        A c[U][4], x[U][4], xb[U][4], pv[U];
+        // Issue every load of the U-row batch before any arithmetic.
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool rv = ib + u < i1;
+            pv[u] = rv ? (A)p[ib + u] : A(0);
+            if (rv && on) {
+                if (full) ldc4<A>(Cr + u * ldc, c[u]);
+                else ldc4_tail<A>(Cr + u * ldc, ccnt, c[u]);
+                ld4(Xr + u * ldx, x[u]);
+                if (!first) ld4(Xbr + u * ldx, xb[u]);
+                else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) xb[u][e] = A(0);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { c[u][e] = A(0); x[u][e] = A(0); xb[u][e] = A(0); }
+            }
+        }
+        A csa[4] = {A(0), A(0), A(0), A(0)};
+        A dxa = A(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool rv = ib + u < i1;
+            A xn[4], xbn[4];
+            A rs = A(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const A R = (c[u][e] - pv[u]) - qv[e];          // reduced cost C - p - q
+                A v = x[u][e] - tau * R;
+                v = v > A(0) ? v : A(0);                         // projection onto X >= 0
+                v = valid[e] ? v : A(0);                         // padding columns stay 0
+                const A d = v - x[u][e];
+                dxa += d * d;
+                rs += v;
+                csa[e] += v;
+                xn[e] = v;
+                xbn[e] = first ? v : xb[u][e] + w * (v - xb[u][e]);
+            }
+            if (rv && on) {
+                st4(Xnr + u * ldx, xn);
+                st4(Xbnr + u * ldx, xbn);
+            }
+            rs = warp_sum(rs);
+            if (rv && lane == 0) rowpart[ib + u] = (double)rs;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
+        dx2 += (double)dxa;
+        Cr += U * ldc;
+        Xr += U * ldx;
+        Xbr += U * ldx;
+        Xnr += U * ldx;
+        Xbnr += U * ldx;
+    }
+    if (on) {
+        double* cp = I.colpart + (long long)chunk * ldx + j0;
+        reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
+        reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
+    }
+    dx2 = warp_sum(dx2);
+    if (lane == 0) I.tpart[(long long)lt * TP + 0] = dx2;
+}
+
+template <typename TC, typename TX, int U>
+__global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
+k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc) {
+    reset_other_counters(wctr, wc);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int t = warp_next(&wctr[wc]);
+        if (t >= T) break;
+        const TileRef tr = tmap[t];
+        const Inst& I = insts[tr.inst];
+        const Ctrl& S = *I.ctrl;
+        if (S.status != ST_RUNNING) continue;
+        pass_tile<TC, TX, U>(I, S, tr.local, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Slot bookkeeping
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void assign_free(Ctrl* S) {
+    const int used = (1 << S->cur) | (1 << S->bar) | (1 << S->anc);
+    int picks[2] = {0, 0};
+    int np = 0;
+    for (int s = 0; s < NSLOT && np < 2; ++s)
+        if (!(used & (1 << s))) picks[np++] = s;
+    S->nxt = picks[0];
+    S->barn = picks[1];
+}
+
+// ---------------------------------------------------------------------------
+// Dual step + PDLP step-size controller
+// ---------------------------------------------------------------------------
+__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
+    S->passes += 1;
+    S->last_dX2 = dX2;
+    S->last_dy2 = dy2;
+    S->last_inter = inter;
+    bool accept = true;
+    double eta = S->eta;
+    if (S->adaptive_step) {
+        // Sec. 5 step-size rule in the PDLP form (reading C6); the exponent base
+        // is the 1-based index of the attempted iteration plus one.
+        const double om = S->omega;
+        const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
+        const double t1 = (double)(S->total + 2);
+        const double a = (1.0 - pow(t1, -0.3)) * etabar;
+        const double b = (1.0 + pow(t1, -0.6)) * eta;
+        const double eta_next = a < b ? a : b;
+        accept = eta <= etabar;
+        S->last_etabar = etabar;
+        eta = eta_next;
+    }
+    if (!isfinite(dX2) || !isfinite(dy2) || !isfinite(eta) || !(eta > 0.0)) {
+        S->status = ST_NUMERIC;
+        S->res_slot = S->cur;
+        S->res_avg = 0;
+        return;
+    }
+    if (accept) {
+        S->cur = S->nxt;
+        S->bar = S->barn;
+        assign_free(S);
+        S->k += 1;
+        S->total += 1;
+    } else {
+        S->rejected += 1;
+    }
+    S->eta = eta;
+    S->tau = eta / S->omega;
+    S->sigma = eta * S->omega;
+}
+
+__device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, int* s_last) {
+    const long long m = I.m, n = I.n;
+    const long long e = (long long)lvt * VT + threadIdx.x;
+    const double sigma = S->sigma;
+    const long long k = S->k;
+    const bool first = k == 0;
+    const double w = 1.0 / (double)(k + 1);
+    const double* Vc = slot_v(I, S->cur);
+    double* Vn = slot_v(I, S->nxt);
+    const double* Vb = slot_v(I, S->bar);
+    double* Vbn = slot_v(I, S->barn);
+    double a[3] = {0.0, 0.0, 0.0};   // ||dy||^2, dy^T A dx, ||dX||^2 (tile slice)
+    if (e < m) {
+        const long long i = e;
+        double s = 0.0;
+        for (int st = 0; st < I.nstrips; ++st) s += I.rowpart[(long long)st * m + i];
+        const double r = Vc[m + n + i], p = Vc[i];
+        const double pn = p + sigma * (I.f[i] - (2.0 * s - r));
+        Vn[i] = pn;
+        Vn[m + n + i] = s;
+        Vbn[i] = first ? pn : Vb[i] + w * (pn - Vb[i]);
+        const double dp = pn - p;
+        a[0] = dp * dp;
+        a[1] = dp * (s - r);
+    } else if (e < m + n) {
+        const long long j = e - m;
+        double s = 0.0;
+        for (int ch = 0; ch < I.nchunks; ++ch) s += I.colpart[(long long)ch * I.ldx + j];
+        const double c = Vc[2 * m + n + j], q = Vc[m + j];
+        const double qn = q + sigma * (I.g[j] - (2.0 * s - c));
+        Vn[m + j] = qn;
+        Vn[2 * m + n + j] = s;
+        Vbn[m + j] = first ? qn : Vb[m + j] + w * (qn - Vb[m + j]);
+        const double dq = qn - q;
+        a[0] = dq * dq;
+        a[1] = dq * (s - c);
+    }
+    const long long T = I.ntiles;
+    const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) a[2] += I.tpart[t * TP + 0];
+    block_sum<3>(a, red);
+    if (threadIdx.x == 0) {
+        double* vp = I.vpart + (long long)lvt * VP;
+        vp[0] = a[0]; vp[1] = a[1]; vp[2] = a[2];
+        __threadfence();
+        const unsigned old = atomicAdd(I.ticket, 1u);
+        *s_last = (old == (unsigned)(I.nvt - 1));
+    }
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        double b[3] = {0.0, 0.0, 0.0};
+        for (int v = threadIdx.x; v < I.nvt; v += blockDim.x) {
+            const double* vp = I.vpart + (long long)v * VP;
+            b[0] += __ldcg(vp + 0);
+            b[1] += __ldcg(vp + 1);
+            b[2] += __ldcg(vp + 2);
+        }
+        block_sum<3>(b, red);
+        if (threadIdx.x == 0) {
+            *I.ticket = 0u;
+            finalize_step(S, b[2], b[0], b[1]);
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
+                                             int NV, unsigned* wctr) {
+    __shared__ double red[(VT / 32) * 3];
+    __shared__ int s_t, s_last;
+    const int wc = wc_index(WC_DUAL, 0);
+    reset_other_counters(wctr, wc);
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= NV) break;
+        const TileRef tr = vmap[t];
+        const Inst& I = insts[tr.inst];
+        Ctrl* S = I.ctrl;
+        if (S->status != ST_RUNNING) continue;
+        dual_tile(I, S, tr.local, red, &s_last);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// KKT pass (every K passes, and once at the start)
+// ---------------------------------------------------------------------------
+template <typename TC, typename TX>
+__device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, int lane, int mode) {
+    typedef TX A;
+    const long long m = I.m, n = I.n, ldx = I.ldx, ldc = I.ldc;
+    const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
+    const long long j0 = (long long)strip * STRIP + lane * 4;
+    const long long i0 = (long long)chunk * I.tile_rows;
+    const long long i1 = min(i0 + (long long)I.tile_rows, m);
+    const bool on = j0 < n;
+    const bool full = j0 + 4 <= n;
+    const bool init = mode == MODE_INIT;
+    const bool avg = !init && S.k > 0;      // the running average exists
+    const bool sums = init || avg;          // exact row/col sums of X (init) or Xbar (check)
+    const TC* C = reinterpret_cast<const TC*>(I.C);
+    const TX* X = slot_x<TX>(I, S.cur);
+    const TX* Xb = slot_x<TX>(I, S.bar);
+    const TX* Xa = slot_x<TX>(I, S.anc);
+    const double* p = slot_v(I, S.cur);
+    const double* q = p + m;
+    const double* pb = slot_v(I, S.bar);
+    const double* qb = pb + m;
+
+    A qv[4], qbv[4];
+    bool valid[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        valid[e] = j0 + e < n;
+        qv[e] = valid[e] ? (A)q[j0 + e] : A(0);
+        qbv[e] = (valid[e] && avg) ? (A)qb[j0 + e] : A(0);
+    }
+    double acc[TP] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // cxc, rd2c, cxb, rd2b, dXac, dXab
+    double cs[4] = {0.0, 0.0, 0.0, 0.0};
+    double* rowpart = I.rowpart + (long long)strip * m;
+
+    for (long long ib = i0; ib < i1; ib += KU) {
+        A c[KU][4], x[KU][4], xb[KU][4], xa[KU][4], pv[KU], pbv[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const long long i = ib + u;
+            const bool rv = i < i1;
+            pv[u] = rv ? (A)p[i] : A(0);
+            pbv[u] = (rv && avg) ? (A)pb[i] : A(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { c[u][e] = A(0); x[u][e] = A(0); xb[u][e] = A(0); xa[u][e] = A(0); }
+            if (rv && on) {
+                if (full) ldc4<A>(C + i * ldc + j0, c[u]);
+                else ldc4_tail<A>(C + i * ldc + j0, n - j0, c[u]);
+                ld4(X + i * ldx + j0, x[u]);
+                if (avg) {
+                    ld4(Xb + i * ldx + j0, xb[u]);
+                    ld4(Xa + i * ldx + j0, xa[u]);
+                } else if (!init) {
+                    ld4(Xa + i * ldx + j0, xa[u]);
+                }
+            }
+        }
+        A t[TP] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+        A csa[4] = {A(0), A(0), A(0), A(0)};
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const long long i = ib + u;
+            const bool rv = i < i1;
+            A rs = A(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (!valid[e]) continue;
+                const A Rc = (c[u][e] - pv[u]) - qv[e];
+                t[0] += c[u][e] * x[u][e];
+                t[1] += Rc < A(0) ? Rc * Rc : A(0);             // [p + q - C]^+ squared
+                const A da = x[u][e] - xa[u][e];
+                t[4] += da * da;
+                if (avg) {
+                    const A Rb = (c[u][e] - pbv[u]) - qbv[e];
+                    t[2] += c[u][e] * xb[u][e];
+                    t[3] += Rb < A(0) ? Rb * Rb : A(0);
+                    const A db = xb[u][e] - xa[u][e];
+                    t[5] += db * db;
+                }
+                const A sv = init ? x[u][e] : xb[u][e];
+                rs += sv;
+                csa[e] += sv;
+            }
+            if (sums) {
+                rs = warp_sum(rs);
+                if (rv && lane == 0) rowpart[i] = (double)rs;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TP; ++k) acc[k] += (double)t[k];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
+    }
+    if (sums && on) {
+        double* cp = I.colpart + (long long)chunk * ldx + j0;
+        reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
+        reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < TP; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < TP; ++k) I.tpart[(long long)lt * TP + k] = acc[k];
+    }
+}
+
+template <typename TC, typename TX>
+__global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
+k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc, int mode) {
+    reset_other_counters(wctr, wc);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int t = warp_next(&wctr[wc]);
+        if (t >= T) break;
+        const TileRef tr = tmap[t];
+        const Inst& I = insts[tr.inst];
+        const Ctrl& S = *I.ctrl;
+        if (S.status != ST_RUNNING) continue;
+        kkt_tile<TC, TX>(I, S, tr.local, lane, mode);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Check: KKT of current and average, restart / termination / primal weight
+// ---------------------------------------------------------------------------
+struct KP {
+    double rp2, rd2, cx, dual, gap, kkt, rel_p, rel_d, rel_gap, rel;
+};
+
+__device__ void kkt_parts(const Ctrl* S, double rp2, double rd2, double cx, double dual, KP& o) {
+    // KKT error of Sec. 3.1 and the relative measures of reading C5.
+    o.rp2 = rp2;
+    o.rd2 = rd2;
+    o.cx = cx;
+    o.dual = dual;
+    o.gap = cx - dual;
+    const double gr = o.gap / S->R;
+    o.kkt = sqrt(rp2 + rd2 + gr * gr);
+    double dp = S->norm_b, dd = S->norm_C, dg = fabs(cx) + fabs(dual);
+    if (S->rel_mode == 1) { dp += 1.0; dd += 1.0; dg += 1.0; }
+    if (!(dp > 0.0)) dp = 1.0;
+    if (!(dd > 0.0)) dd = 1.0;
+    if (!(dg > 0.0)) dg = 1.0;
+    o.rel_p = sqrt(rp2) / dp;
+    o.rel_d = sqrt(rd2) / dd;
+    o.rel_gap = fabs(o.gap) / dg;
+    o.rel = fmax(o.rel_p, fmax(o.rel_d, o.rel_gap));
+}
+
+__device__ void report(Ctrl* S, const KP& k) {
+    S->r_rp2 = k.rp2; S->r_rd2 = k.rd2; S->r_cx = k.cx; S->r_dual = k.dual; S->r_gap = k.gap;
+    S->r_kkt = k.kkt; S->r_rel_p = k.rel_p; S->r_rel_d = k.rel_d; S->r_rel_gap = k.rel_gap; S->r_rel = k.rel;
+}
+
+// A: 0 rp2 cur, 1 rp2 avg, 2 dual cur, 3 dual avg, 4 ||dy_anchor||^2 cur, 5 avg,
+//    6 <C,X>, 7 rd2 cur, 8 <C,Xbar>, 9 rd2 avg, 10 ||X - Xa||^2, 11 ||Xbar - Xa||^2
+__device__ void finalize_check(Ctrl* S, const double* A, int mode) {
+    KP c;
+    kkt_parts(S, A[0], A[7], A[6], A[2], c);
+    S->checks += 1;
+    if (mode == MODE_INIT) {
+        report(S, c);
+        S->kkt0 = c.kkt;
+        S->kkt_prev = c.kkt;
+        if (!isfinite(c.kkt)) { S->status = ST_NUMERIC; S->res_slot = S->cur; S->res_avg = 0; }
+        else if (c.rel <= S->tol) { S->status = ST_OK; S->res_slot = S->cur; S->res_avg = 0; }
+        return;
+    }
+    if (S->k == 0) {
+        // No accepted step since the last restart: only the pass budget is checked.
+        if (S->passes >= S->max_passes) {
+            report(S, c);
+            S->status = ST_MAX_ITER;
+            S->res_slot = S->cur;
+            S->res_avg = 0;
+        }
+        return;
+    }
+    KP b;
+    kkt_parts(S, A[1], A[9], A[8], A[3], b);
+    if (!isfinite(c.kkt) || !isfinite(b.kkt)) {
+        report(S, c);
+        S->status = ST_NUMERIC;
+        S->res_slot = S->cur;
+        S->res_avg = 0;
+        return;
+    }
+    // Restart candidate (Sec. 5): current iff its KKT is strictly smaller.
+    const bool use_avg = S->adaptive_restart ? !(c.kkt < b.kkt) : true;
+    const KP& kk = use_avg ? b : c;
+    const int cand = use_avg ? S->bar : S->cur;
+    report(S, kk);
+    if (kk.rel <= S->tol || S->passes >= S->max_passes) {
+        S->status = kk.rel <= S->tol ? ST_OK : ST_MAX_ITER;
+        S->res_slot = cand;
+        S->res_avg = use_avg ? 1 : 0;
+        return;
+    }
+    bool restart;
+    if (S->adaptive_restart) {
+        restart = (kk.kkt <= S->beta_suff * S->kkt0) ||
+                  (kk.kkt <= S->beta_nec * S->kkt0 && kk.kkt > S->kkt_prev) ||
+                  ((double)S->k >= S->beta_art * (double)S->total);
+    } else {
+        restart = b.kkt <= S->beta * S->kkt0;   // Eq. (6)
+    }
+    if (!restart) {
+        S->kkt_prev = kk.kkt;
+        return;
+    }
+    if (S->pw_update) {
+        // PrimalWeightUpdate of Sec. 5 against the previous restart point.
+        const double dX = sqrt(use_avg ? A[11] : A[10]);
+        const double dy = sqrt(use_avg ? A[5] : A[4]);
+        if (dX > S->eps_zero && dy > S->eps_zero)
+            S->omega = exp(S->theta * log(dy / dX) + (1.0 - S->theta) * log(S->omega));
+    }
+    S->cur = cand;
+    S->anc = cand;
+    // The average restarts empty: its slot content is not read while k == 0.
+    {
+        int used = 1 << cand;
+        int picks[3] = {0, 0, 0};
+        int np = 0;
+        for (int s = 0; s < NSLOT && np < 3; ++s)
+            if (!(used & (1 << s))) picks[np++] = s;
+        S->bar = picks[0];
+        S->nxt = picks[1];
+        S->barn = picks[2];
+    }
+    S->k = 0;
+    S->kkt0 = kk.kkt;
+    S->kkt_prev = kk.kkt;
+    S->restarts += 1;
+    S->tau = S->eta / S->omega;
+    S->sigma = S->eta * S->omega;
+}
+
+__device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double* red, int* s_last) {
+    const long long m = I.m, n = I.n;
+    const long long e = (long long)lvt * VT + threadIdx.x;
+    const bool init = mode == MODE_INIT;
+    const bool avg = !init && S->k > 0;
+    double* Vc = slot_v(I, S->cur);
+    double* Vb = slot_v(I, S->bar);
+    const double* Va = slot_v(I, S->anc);
+    double a[VP];
+#pragma unroll
+    for (int k = 0; k < VP; ++k) a[k] = 0.0;
+    if (e < m + n) {
+        const bool row = e < m;
+        const long long idx = row ? e : e - m;          // i or j
+        const long long yo = row ? idx : m + idx;       // offset of p_i / q_j in a vector set
+        const long long so = row ? m + n + idx : 2 * m + n + idx;   // offset of r_i / c_j
+        const double b = row ? I.f[idx] : I.g[idx];
+        double s = 0.0;
+        if (init || avg) {
+            if (row) { for (int st = 0; st < I.nstrips; ++st) s += I.rowpart[(long long)st * m + idx]; }
+            else { for (int ch = 0; ch < I.nchunks; ++ch) s += I.colpart[(long long)ch * I.ldx + idx]; }
+        }
+        const double y = Vc[yo];
+        if (init) {
+            Vc[so] = s;
+            a[0] = (s - b) * (s - b);
+            a[2] = b * y;
+        } else {
+            const double r = Vc[so];
+            a[0] = (r - b) * (r - b);
+            a[2] = b * y;
+            const double ya = Va[yo];
+            a[4] = (y - ya) * (y - ya);
+            if (avg) {
+                Vb[so] = s;
+                const double yb = Vb[yo];
+                a[1] = (s - b) * (s - b);
+                a[3] = b * yb;
+                a[5] = (yb - ya) * (yb - ya);
+            }
+        }
+    }
+    const long long T = I.ntiles;
+    const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < TP; ++k) a[6 + k] += I.tpart[t * TP + k];
+    }
+    block_sum<VP>(a, red);
+    if (threadIdx.x == 0) {
+        double* vp = I.vpart + (long long)lvt * VP;
+#pragma unroll
+        for (int k = 0; k < VP; ++k) vp[k] = a[k];
+        __threadfence();
+        const unsigned old = atomicAdd(I.ticket, 1u);
+        *s_last = (old == (unsigned)(I.nvt - 1));
+    }
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        double b[VP];
+#pragma unroll
+        for (int k = 0; k < VP; ++k) b[k] = 0.0;
+        for (int v = threadIdx.x; v < I.nvt; v += blockDim.x) {
+            const double* vp = I.vpart + (long long)v * VP;
+#pragma unroll
+            for (int k = 0; k < VP; ++k) b[k] += __ldcg(vp + k);
+        }
+        block_sum<VP>(b, red);
+        if (threadIdx.x == 0) {
+            *I.ticket = 0u;
+            finalize_check(S, b, mode);
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
+                                                 int NV, unsigned* wctr, int mode) {
+    __shared__ double red[(VT / 32) * VP];
+    __shared__ int s_t, s_last;
+    const int wc = wc_index(WC_CHECK, 0);
+    reset_other_counters(wctr, wc);
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= NV) break;
+        const TileRef tr = vmap[t];
+        const Inst& I = insts[tr.inst];
+        Ctrl* S = I.ctrl;
+        if (S->status != ST_RUNNING) continue;
+        checkvec_tile(I, S, tr.local, mode, red, &s_last);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ||C||_F^2 per plan tile (once per solve, for the relative dual residual)
+// ---------------------------------------------------------------------------
+template <typename TC>
+__device__ __forceinline__ void sumsq_tile(const Inst& I, int lt, int lane) {
+    const long long m = I.m, n = I.n, ldc = I.ldc;
+    const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
+    const long long j0 = (long long)strip * STRIP + lane * 4;
+    const long long i0 = (long long)chunk * I.tile_rows;
+    const long long i1 = min(i0 + (long long)I.tile_rows, m);
+    const TC* C = reinterpret_cast<const TC*>(I.C);
+    double s = 0.0;
+    if (j0 < n) {
+        for (long long i = i0; i < i1; ++i) {
+            double c[4];
+            if (j0 + 4 <= n) ldc4<double>(C + i * ldc + j0, c);
+            else ldc4_tail<double>(C + i * ldc + j0, n - j0, c);
+            s += c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + c[3] * c[3];
+        }
+    }
+    s = warp_sum(s);
+    if (lane == 0) I.tpart[(long long)lt * TP + 0] = s;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(TWARPS * 32)
+k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc) {
+    reset_other_counters(wctr, wc);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int t = warp_next(&wctr[wc]);
+        if (t >= T) break;
+        const TileRef tr = tmap[t];
+        sumsq_tile<TC>(insts[tr.inst], tr.local, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int err(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
+
+int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
+                void* stream, int wc_override) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
+    if (ttype == TT_F64) k_pass<double, double, 2><<<cfg.tile_blocks_f64, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    else if (ttype == TT_BF16) {
+        if (cfg.pass_u == 4) k_pass<unsigned short, float, 4><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+        else k_pass<unsigned short, float, 2><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    } else {
+        if (cfg.pass_u == 4) k_pass<float, float, 4><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+        else k_pass<float, float, 2><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    }
+    return err(cudaGetLastError());
+}
+int launch_dual(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, const LaunchCfg& cfg,
+                void* stream) {
+    const int blocks = NV < cfg.vec_blocks ? NV : cfg.vec_blocks;
+    k_dual<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr);
+    return err(cudaGetLastError());
+}
+int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, int mode,
+               const LaunchCfg& cfg, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int wc = wc_index(WC_KKT, ttype);
+    if (ttype == TT_F64) k_kkt<double, double><<<cfg.tile_blocks_f64, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
+    else if (ttype == TT_BF16) k_kkt<unsigned short, float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
+    else k_kkt<float, float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
+    return err(cudaGetLastError());
+}
+int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, int mode,
+                    const LaunchCfg& cfg, void* stream) {
+    const int blocks = NV < cfg.vec_blocks ? NV : cfg.vec_blocks;
+    k_checkvec<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr, mode);
+    return err(cudaGetLastError());
+}
+int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
+                   void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int wc = wc_index(WC_AUX, ctype == 2 ? TT_F64 : (ctype == 1 ? TT_BF16 : TT_F32));
+    if (ctype == 2) k_sumsq_C<double><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    else if (ctype == 1) k_sumsq_C<unsigned short><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    else k_sumsq_C<float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    return err(cudaGetLastError());
+}
+
+static int occ(const void* fn, int threads) {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, threads, 0);
+    return a > 0 ? a : 1;
+}
+int occupancy_tile_blocks_per_sm(int ttype) {
+    if (ttype == TT_F64) {
+        const int a = occ((const void*)k_pass<double, double, 2>, TWARPS * 32);
+        const int b = occ((const void*)k_kkt<double, double>, TWARPS * 32);
+        return a < b ? a : b;
+    }
+    const int a = occ((const void*)k_pass<float, float, 2>, TWARPS * 32);
+    const int b = occ((const void*)k_kkt<float, float>, TWARPS * 32);
+    const int c = occ((const void*)k_pass<unsigned short, float, 4>, TWARPS * 32);
+    const int d = occ((const void*)k_kkt<unsigned short, float>, TWARPS * 32);
+    int r = a;
+    if (b < r) r = b;
+    if (c < r) r = c;
+    if (d < r) r = d;
+    return r;
+}
+int occupancy_vec_blocks_per_sm() {
+    const int a = occ((const void*)k_dual, VT);
+    const int b = occ((const void*)k_checkvec, VT);
+    return a < b ? a : b;
+}
+
+}  // namespace pdot

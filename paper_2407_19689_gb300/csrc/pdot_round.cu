@@ -1,0 +1,132 @@
+// pdot_round.cu -- Algorithm 3 of arXiv 2407.19689 (rounding onto the
+// transportation polytope, after Altschuler et al.) on the device.
+// Runs once per solve, so the kernels are plain and order-deterministic:
+// row sums by one warp per row, column sums by fixed row groups, and a final
+// write of diag(x) X diag(y) + err_r err_c^T / ||err_r||_1 with <C, X_feas>.
+#include <cuda_runtime.h>
+
+#include "pdot_internal.h"
+
+namespace pdot {
+
+namespace {
+
+template <typename TX>
+__device__ __forceinline__ double scaled(const TX* X, long long ldx, long long i, long long j, const double* rs,
+                                         const double* cs) {
+    double v = (double)X[i * ldx + j];
+    if (rs) v *= rs[i];
+    if (cs) v *= cs[j];
+    return v;
+}
+
+// rowout[i] = sum_j rs_i X_ij cs_j   (one warp per row)
+template <typename TX>
+__global__ void k_round_rows(const TX* X, long long m, long long n, long long ldx, const double* rs,
+                             const double* cs, double* rowout) {
+    const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    double s = 0.0;
+    for (long long j = lane; j < n; j += 32) s += scaled(X, ldx, row, j, rs, cs);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) rowout[row] = s;
+}
+
+// colpart[g][j] = sum over rows i of group g of rs_i X_ij cs_j
+template <typename TX>
+__global__ void k_round_cols(const TX* X, long long m, long long n, long long ldx, const double* rs,
+                             const double* cs, double* colpart, int parts) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int grp = blockIdx.y;
+    if (j >= n) return;
+    const long long r0 = m * grp / parts, r1 = m * (grp + 1) / parts;
+    double s = 0.0;
+    for (long long i = r0; i < r1; ++i) s += scaled(X, ldx, i, j, rs, cs);
+    colpart[(long long)grp * n + j] = s;
+}
+
+__global__ void k_colreduce(const double* colpart, int parts, long long n, double* out) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int g = 0; g < parts; ++g) s += colpart[(long long)g * n + j];
+    out[j] = s;
+}
+
+template <typename TX, typename TC>
+__global__ void k_round_write(const TX* X, long long m, long long n, long long ldx, const double* rs,
+                              const double* cs, const double* er, const double* ec, double inv_l1, TX* out,
+                              long long ldo, const TC* C, long long ldc, double* objpart, int parts) {
+    __shared__ double red[32];
+    const int grp = blockIdx.x;
+    const long long r0 = m * grp / parts, r1 = m * (grp + 1) / parts;
+    double obj = 0.0;
+    for (long long i = r0; i < r1; ++i) {
+        for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+            const double v = scaled(X, ldx, i, j, rs, cs) + er[i] * ec[j] * inv_l1;
+            const TX vo = (TX)v;
+            out[i * ldo + j] = vo;
+            if (C) obj += (double)C[i * ldc + j] * (double)vo;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) obj += __shfl_xor_sync(0xffffffffu, obj, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = obj;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        objpart[grp] = s;
+    }
+}
+
+struct Bf16 {
+    unsigned short b;
+    __device__ operator double() const { return (double)__uint_as_float(((unsigned)b) << 16); }
+};
+
+}  // namespace
+
+int launch_round_rowsum(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
+                        const double* cs, double* rowout, double* colpart, int parts, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const dim3 rb((unsigned)((m + 7) / 8));
+    const dim3 cb((unsigned)((n + 255) / 256), (unsigned)parts);
+    if (xtype == 2) {
+        k_round_rows<double><<<rb, 256, 0, st>>>((const double*)X, m, n, ldx, rs, cs, rowout);
+        k_round_cols<double><<<cb, 256, 0, st>>>((const double*)X, m, n, ldx, rs, cs, colpart, parts);
+    } else {
+        k_round_rows<float><<<rb, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, rowout);
+        k_round_cols<float><<<cb, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, colpart, parts);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_colreduce(const double* colpart, int parts, long long n, double* out, void* stream) {
+    k_colreduce<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(colpart, parts, n, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_round_write(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
+                       const double* cs, const double* er, const double* ec, double inv_l1, void* Xout,
+                       long long ldo, const void* C, int ctype, long long ldc, double* objpart, int parts,
+                       void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (xtype == 2) {
+        k_round_write<double, double><<<parts, 256, 0, st>>>((const double*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                             (double*)Xout, ldo, (const double*)C, ldc, objpart,
+                                                             parts);
+    } else if (ctype == 1) {
+        k_round_write<float, Bf16><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                          (float*)Xout, ldo, (const Bf16*)C, ldc, objpart, parts);
+    } else {
+        k_round_write<float, float><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                           (float*)Xout, ldo, (const float*)C, ldc, objpart,
+                                                           parts);
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace pdot

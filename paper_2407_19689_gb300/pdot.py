@@ -1,0 +1,385 @@
+"""Python binding of the C ABI in ``include/pdot.h`` (ctypes; argument
+marshalling only -- every step of the solver runs in libpdot.so's kernels).
+
+The functions named ``pdot_*`` mirror the C entry points one to one and take
+raw device pointers.  ``Solver`` is a convenience wrapper over them that takes
+torch CUDA tensors (torch provides device memory and the stream only).
+
+Importing this module does not load the library; the first call does, and it
+raises ``PdotError`` when ``libpdot.so`` has not been built (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+F32, BF16, F64 = 0, 1, 2
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, MAX_ITER, TIMEOUT, BUSY, PENDING, CANCELLED = range(10)
+
+
+class PdotError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{status_str(status) if _LIB else status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int64),
+        ("time_limit_s", ctypes.c_double),
+        ("restart_check_every", ctypes.c_int32),
+        ("adaptive_step", ctypes.c_int32),
+        ("adaptive_restart", ctypes.c_int32),
+        ("primal_weight_update", ctypes.c_int32),
+        ("beta", ctypes.c_double),
+        ("beta_suff", ctypes.c_double),
+        ("beta_nec", ctypes.c_double),
+        ("beta_art", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("eta0", ctypes.c_double),
+        ("omega0", ctypes.c_double),
+        ("R", ctypes.c_double),
+        ("eps_zero", ctypes.c_double),
+        ("rel_mode", ctypes.c_int32),
+        ("x_dtype", ctypes.c_int32),
+        ("round_plan", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+        ("max_batch_slots", ctypes.c_int32),
+        ("chunk_checks", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("primal_obj", ctypes.c_double),
+        ("dual_obj", ctypes.c_double),
+        ("gap", ctypes.c_double),
+        ("kkt", ctypes.c_double),
+        ("rel_kkt", ctypes.c_double),
+        ("rel_primal", ctypes.c_double),
+        ("rel_dual", ctypes.c_double),
+        ("rel_gap", ctypes.c_double),
+        ("iters", ctypes.c_int64),
+        ("passes", ctypes.c_int64),
+        ("restarts", ctypes.c_int64),
+        ("rejected_steps", ctypes.c_int64),
+        ("eta", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("hbm_bytes", ctypes.c_double),
+        ("rounded_obj", ctypes.c_double),
+        ("returned_average", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KktParts(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("rp2", "rd2", "cx", "dual", "gap", "kkt", "rel_p", "rel_d", "rel_gap", "rel_kkt")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("C", ctypes.c_void_p),
+        ("c_dtype", ctypes.c_int32),
+        ("ldc", ctypes.c_int64),
+        ("f", ctypes.c_void_p),
+        ("g", ctypes.c_void_p),
+        ("tol", ctypes.c_double),
+        ("X_out", ctypes.c_void_p),
+        ("p_out", ctypes.c_void_p),
+        ("q_out", ctypes.c_void_p),
+        ("user_tag", ctypes.c_uint64),
+    ]
+
+
+# Every symbol include/pdot.h declares (checked by the CPU tests).
+DECLARED = [
+    "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
+    "pdot_solve_host", "pdot_pdhg_steps", "pdot_kkt", "pdot_round", "pdot_batch_submit", "pdot_poll",
+    "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass",
+]
+
+_LIB = None
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libpdot.so (building it first only when asked)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise PdotError(ERR_CUDA, f"{_build.LIB} is not built; call __graft_entry__.build() or "
+                                  "paper_2407_19689_gb300._build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int32
+    H = ctypes.c_void_p
+    sig = {
+        "pdot_default_options": (None, [ctypes.POINTER(Options)]),
+        "pdot_status_str": (ctypes.c_char_p, [i32]),
+        "pdot_last_error": (ctypes.c_char_p, [H]),
+        "pdot_create": (i32, [ctypes.POINTER(Options), i32, vp, ctypes.POINTER(H)]),
+        "pdot_destroy": (i32, [H]),
+        "pdot_solve": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, vp, vp, vp, ctypes.POINTER(Result)]),
+        "pdot_solve_host": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, vp, vp, vp, ctypes.POINTER(Result)]),
+        "pdot_pdhg_steps": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i64, dbl, dbl, vp, vp, vp, vp, vp, vp]),
+        "pdot_kkt": (i32, [H, i64, i64, vp, i32, i64, vp, vp, vp, vp, vp, ctypes.POINTER(KktParts)]),
+        "pdot_round": (i32, [H, i64, i64, vp, vp, vp, vp]),
+        "pdot_batch_submit": (i32, [H, ctypes.POINTER(Request), i32, ctypes.POINTER(ctypes.c_uint64)]),
+        "pdot_poll": (i32, [H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), i32,
+                            ctypes.POINTER(i32)]),
+        "pdot_cancel": (i32, [H, ctypes.c_uint64]),
+        "pdot_batch_pending": (i32, [H, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "pdot_launch_count": (i64, [H]),
+        "pdot_time_pass": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i32, ctypes.POINTER(dbl),
+                                 ctypes.POINTER(dbl)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    return load().pdot_status_str(int(s)).decode()
+
+
+def _check(h, st: int, allow=(OK,)):
+    if st not in allow:
+        msg = load().pdot_last_error(h).decode() if h else ""
+        raise PdotError(st, msg)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# 1:1 wrappers of the C entry points (raw pointers; ints for addresses)
+# ---------------------------------------------------------------------------
+
+def pdot_default_options() -> Options:
+    o = Options()
+    load().pdot_default_options(ctypes.byref(o))
+    return o
+
+
+def pdot_create(opts: Options | None = None, device: int = 0, stream: int = 0):
+    h = ctypes.c_void_p()
+    st = load().pdot_create(ctypes.byref(opts) if opts is not None else None, device, stream or None,
+                            ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def pdot_destroy(h) -> int:
+    return load().pdot_destroy(h)
+
+
+def pdot_solve(h, m, n, C, c_dtype, ldc, f, g, tol, X_out=0, p_out=0, q_out=0):
+    r = Result()
+    st = load().pdot_solve(h, m, n, C, c_dtype, ldc, f, g, tol, X_out or None, p_out or None, q_out or None,
+                           ctypes.byref(r))
+    return st, r
+
+
+def pdot_solve_host(h, m, n, C, c_dtype, ldc, f, g, tol, X_out=0, p_out=0, q_out=0):
+    r = Result()
+    st = load().pdot_solve_host(h, m, n, C, c_dtype, ldc, f, g, tol, X_out or None, p_out or None,
+                                q_out or None, ctypes.byref(r))
+    return st, r
+
+
+def pdot_pdhg_steps(h, m, n, C, c_dtype, ldc, f, g, k, eta, omega, X, p, q, Xbar=0, pbar=0, qbar=0) -> int:
+    return load().pdot_pdhg_steps(h, m, n, C, c_dtype, ldc, f, g, k, eta, omega, X, p, q, Xbar or None,
+                                  pbar or None, qbar or None)
+
+
+def pdot_kkt(h, m, n, C, c_dtype, ldc, f, g, X, p, q):
+    out = KktParts()
+    st = load().pdot_kkt(h, m, n, C, c_dtype, ldc, f, g, X, p, q, ctypes.byref(out))
+    return st, out
+
+
+def pdot_round(h, m, n, X, f, g, X_out) -> int:
+    return load().pdot_round(h, m, n, X, f, g, X_out)
+
+
+def pdot_batch_submit(h, reqs: list[Request]):
+    arr = (Request * len(reqs))(*reqs)
+    ids = (ctypes.c_uint64 * len(reqs))()
+    st = load().pdot_batch_submit(h, arr, len(reqs), ids)
+    return st, list(ids)
+
+
+def pdot_poll(h, cap: int = 256):
+    ids = (ctypes.c_uint64 * cap)()
+    res = (Result * cap)()
+    nd = ctypes.c_int32()
+    st = load().pdot_poll(h, ids, res, cap, ctypes.byref(nd))
+    return st, [(ids[i], res[i]) for i in range(nd.value)]
+
+
+def pdot_cancel(h, ticket: int) -> int:
+    return load().pdot_cancel(h, ticket)
+
+
+def pdot_batch_pending(h):
+    q, r = ctypes.c_int32(), ctypes.c_int32()
+    st = load().pdot_batch_pending(h, ctypes.byref(q), ctypes.byref(r))
+    return st, q.value, r.value
+
+
+def pdot_launch_count(h) -> int:
+    return load().pdot_launch_count(h)
+
+
+def pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps):
+    ms, b = ctypes.c_double(), ctypes.c_double()
+    st = load().pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps, ctypes.byref(ms), ctypes.byref(b))
+    return st, ms.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# torch-tensor convenience layer
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _cdtype(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported cost dtype {t.dtype}")
+
+
+def _xdtype_torch(x_dtype: int):
+    torch = _torch()
+    return torch.float64 if x_dtype == F64 else torch.float32
+
+
+@dataclass
+class Solution:
+    result: dict
+    status: int
+    X: object = None
+    p: object = None
+    q: object = None
+
+
+class Solver:
+    """Owns one pdot handle on a CUDA device; tensors in, tensors out."""
+
+    def __init__(self, options: Options | None = None, device: int = 0, stream=None, **overrides):
+        torch = _torch()
+        self.options = options if options is not None else pdot_default_options()
+        for k, v in overrides.items():
+            setattr(self.options, k, v)
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.h = pdot_create(self.options, device, stream)
+
+    def close(self):
+        if self.h is not None:
+            pdot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _cuda(self, t, dtype=None):
+        torch = _torch()
+        t = t if isinstance(t, torch.Tensor) else torch.as_tensor(t)
+        if dtype is not None and t.dtype != dtype:
+            t = t.to(dtype)
+        return t.to(f"cuda:{self.device}").contiguous()
+
+    def _prep(self, C, f, g):
+        torch = _torch()
+        C = self._cuda(C)
+        if C.dim() != 2:
+            raise ValueError("C must be 2-D")
+        f = self._cuda(f, torch.float64)
+        g = self._cuda(g, torch.float64)
+        return C, f, g
+
+    def solve(self, C, f, g, tol: float | None = None, want_plan: bool = True) -> Solution:
+        torch = _torch()
+        C, f, g = self._prep(C, f, g)
+        m, n = C.shape
+        xt = _xdtype_torch(self.options.x_dtype)
+        X = torch.empty((m, n), dtype=xt, device=C.device) if want_plan else None
+        p = torch.empty(m, dtype=torch.float64, device=C.device)
+        q = torch.empty(n, dtype=torch.float64, device=C.device)
+        st, r = pdot_solve(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(),
+                           tol if tol is not None else self.options.tol, X.data_ptr() if X is not None else 0,
+                           p.data_ptr(), q.data_ptr())
+        _check(self.h, st, allow=(OK, MAX_ITER, TIMEOUT, ERR_NUMERIC))
+        return Solution(r.as_dict(), st, X, p, q)
+
+    def pdhg_steps(self, C, f, g, X, p, q, k: int, eta: float, omega: float = 1.0):
+        torch = _torch()
+        C, f, g = self._prep(C, f, g)
+        m, n = C.shape
+        xt = _xdtype_torch(self.options.x_dtype)
+        X = self._cuda(X, xt).clone()
+        p = self._cuda(p, torch.float64).clone()
+        q = self._cuda(q, torch.float64).clone()
+        Xb, pb, qb = torch.empty_like(X), torch.empty_like(p), torch.empty_like(q)
+        st = pdot_pdhg_steps(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(), k,
+                             eta, omega, X.data_ptr(), p.data_ptr(), q.data_ptr(), Xb.data_ptr(), pb.data_ptr(),
+                             qb.data_ptr())
+        _check(self.h, st)
+        return X, p, q, Xb, pb, qb
+
+    def kkt(self, C, f, g, X, p, q) -> dict:
+        torch = _torch()
+        C, f, g = self._prep(C, f, g)
+        m, n = C.shape
+        X = self._cuda(X, _xdtype_torch(self.options.x_dtype))
+        p = self._cuda(p, torch.float64)
+        q = self._cuda(q, torch.float64)
+        st, out = pdot_kkt(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(),
+                           X.data_ptr(), p.data_ptr(), q.data_ptr())
+        _check(self.h, st)
+        return out.as_dict()
+
+    def round(self, X, f, g):
+        torch = _torch()
+        X = self._cuda(X, _xdtype_torch(self.options.x_dtype))
+        f = self._cuda(f, torch.float64)
+        g = self._cuda(g, torch.float64)
+        m, n = X.shape
+        out = torch.empty_like(X)
+        _check(self.h, pdot_round(self.h, m, n, X.data_ptr(), f.data_ptr(), g.data_ptr(), out.data_ptr()))
+        return out
+
+    def launch_count(self) -> int:
+        return pdot_launch_count(self.h)

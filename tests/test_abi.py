@@ -1,0 +1,71 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads without a GPU
+and exports every function include/pdot.h declares; the ctypes structs match
+the header's field lists.  No compute call is made here."""
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pdot.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdot_[a-z_]+)\s*\(", src)))
+
+
+def _struct_fields(name):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    bodies = dict((nm, body) for body, nm in re.findall(r"typedef struct \{([^}]*)\}\s*(\w+);", src))
+    body = bodies[name]
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            fields.append(re.search(r"(\w+)\s*$", part).group(1))
+    return fields
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2407_19689_gb300 import _build, pdot
+    _build.build()
+    return pdot.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2407_19689_gb300 import pdot
+    names = _declared_functions()
+    assert sorted(pdot.DECLARED) == names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("cname,pyname", [("pdot_options", "Options"), ("pdot_result", "Result"),
+                                          ("pdot_kkt_parts", "KktParts"), ("pdot_request", "Request")])
+def test_ctypes_structs_follow_header(cname, pyname):
+    from paper_2407_19689_gb300 import pdot
+    py = [f for f, _ in getattr(pdot, pyname)._fields_]
+    assert py == _struct_fields(cname)
+
+
+def test_default_options_and_status_strings(lib):
+    from paper_2407_19689_gb300 import pdot
+    o = pdot.pdot_default_options()
+    assert o.tol == 1e-4 and o.restart_check_every == 64 and o.beta_suff == 0.1 and o.beta_nec == 0.9
+    assert o.beta_art == 0.36 and o.theta == 0.5 and o.omega0 == 1.0 and o.adaptive_step == 1
+    assert pdot.status_str(pdot.OK) == "PDOT_OK" and pdot.status_str(pdot.BUSY) == "PDOT_BUSY"
+
+
+def test_null_handle_is_rejected_without_gpu(lib):
+    from paper_2407_19689_gb300 import pdot
+    st, _ = pdot.pdot_solve(None, 4, 4, 0, pdot.F32, 4, 0, 0, 1e-4)
+    assert st == pdot.ERR_ARG
+    assert pdot.pdot_destroy(None) == pdot.OK

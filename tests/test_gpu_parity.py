@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived in the design notes): FP32 plans with FP64 duals match the
+oracle's iterates to 1e-5 relative (Frobenius / 2-norm) after k steps; FP64
+plans to 1e-11.  Full solves are compared on objectives (the iterates are not
+unique, reading C14) against the exact LP optimum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2407_19689_gb300 import instances as I  # noqa: E402
+from paper_2407_19689_gb300 import pdot  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    oracle.build()
+    pdot.load(build_if_missing=True)
+
+
+@pytest.fixture(scope="module")
+def s32():
+    s = pdot.Solver(device=0, time_limit_s=120.0)
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def s64():
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0)
+    yield s
+    s.close()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def _rand_state(m, n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.random((m, n)) / (m * n) * (rng.random((m, n)) < 0.5)
+    return X, rng.standard_normal(m) * 0.05, rng.standard_normal(n) * 0.05
+
+
+SHAPES = [(300, 517), (64, 64), (1, 7), (129, 3), (1000, 260), (37, 1)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_pdhg_steps_fp32(s32, m, n, k):
+    ins = I.points_instance(m, n, 1000 + m + n)
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    Co = _np(C)
+    for start, omega in [("zero", 1.0), ("rand", 3.7)]:
+        X0, p0, q0 = (np.zeros((m, n)), np.zeros(m), np.zeros(n)) if start == "zero" else _rand_state(m, n, k)
+        X0 = X0.astype(np.float32).astype(np.float64)
+        eta = 0.5 / math.sqrt(m + n)
+        g = s32.pdhg_steps(C, ins.f, ins.g, X0, p0, q0, k=k, eta=eta, omega=omega)
+        o = oracle.pdhg_steps(Co, ins.f, ins.g, X0, p0, q0, k=k, eta=eta, omega=omega)
+        for a, b, name in zip(g, o, ("X", "p", "q", "Xbar", "pbar", "qbar")):
+            e = rel(_np(a), b)
+            assert e < 1e-5, (name, start, e)
+
+
+@pytest.mark.parametrize("m,n", [(300, 517), (77, 130)])
+def test_pdhg_steps_bf16_cost(s32, m, n):
+    """BF16 costs: the oracle solves the same BF16-rounded C in FP64 (reading C16)."""
+    ins = I.points_instance(m, n, 2000 + m)
+    C = torch.tensor(ins.C, dtype=torch.bfloat16, device=DEV)
+    z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
+    eta = 0.5 / math.sqrt(m + n)
+    g = s32.pdhg_steps(C, ins.f, ins.g, *z, k=30, eta=eta)
+    o = oracle.pdhg_steps(_np(C), ins.f, ins.g, *z, k=30, eta=eta)
+    for a, b in zip(g, o):
+        assert rel(_np(a), b) < 1e-5
+
+
+@pytest.mark.parametrize("m,n", [(64, 64), (130, 67), (1, 1)])
+def test_pdhg_steps_fp64(s64, m, n):
+    ins = I.points_instance(m, n, 3000 + m)
+    C = torch.tensor(ins.C, device=DEV)
+    X0, p0, q0 = _rand_state(m, n, 5)
+    g = s64.pdhg_steps(C, ins.f, ins.g, X0, p0, q0, k=50, eta=0.3, omega=0.8)
+    o = oracle.pdhg_steps(ins.C, ins.f, ins.g, X0, p0, q0, k=50, eta=0.3, omega=0.8)
+    for a, b in zip(g, o):
+        assert rel(_np(a), b) < 1e-11
+
+
+def test_pdhg_steps_strided_cost_takes_padded_copy(s32):
+    """ldc > n with rows not on 16-byte boundaries: the library copies C into an
+    aligned buffer; the result must not change."""
+    m, n = 45, 61
+    ins = I.points_instance(m, n, 4000)
+    big = torch.zeros((m, n + 3), dtype=torch.float32, device=DEV)
+    big[:, :n] = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    C = big[:, :n]
+    f = torch.tensor(ins.f, device=DEV)
+    g = torch.tensor(ins.g, device=DEV)
+    X = torch.zeros((m, n), dtype=torch.float32, device=DEV)
+    p = torch.zeros(m, dtype=torch.float64, device=DEV)
+    q = torch.zeros(n, dtype=torch.float64, device=DEV)
+    st = pdot.pdot_pdhg_steps(s32.h, m, n, C.data_ptr(), pdot.F32, n + 3, f.data_ptr(), g.data_ptr(), 20, 0.1, 1.0,
+                              X.data_ptr(), p.data_ptr(), q.data_ptr())
+    assert st == pdot.OK
+    o = oracle.pdhg_steps(_np(C), ins.f, ins.g, np.zeros((m, n)), np.zeros(m), np.zeros(n), k=20, eta=0.1)
+    assert rel(_np(X), o[0]) < 1e-5 and rel(_np(p), o[1]) < 1e-5 and rel(_np(q), o[2]) < 1e-5
+
+
+@pytest.mark.parametrize("m,n", [(300, 517), (1, 5), (64, 64)])
+def test_kkt_parity(s32, s64, m, n):
+    ins = I.points_instance(m, n, 5000 + m)
+    X, p, q = _rand_state(m, n, 9)
+    p += 0.3  # make some reduced costs negative
+    X32 = X.astype(np.float32).astype(np.float64)
+    C32 = ins.C.astype(np.float32).astype(np.float64)
+    g = s32.kkt(torch.tensor(C32, dtype=torch.float32, device=DEV), ins.f, ins.g, X32, p, q)
+    o = oracle.kkt(C32, ins.f, ins.g, X32, p, q)
+    for key in ("rp2", "rd2", "cx", "dual", "kkt", "rel_kkt"):
+        assert abs(g[key] - getattr(o, key)) <= 1e-5 * max(abs(getattr(o, key)), 1e-30), key
+    g64 = s64.kkt(torch.tensor(ins.C, device=DEV), ins.f, ins.g, X, p, q)
+    o64 = oracle.kkt(ins.C, ins.f, ins.g, X, p, q)
+    for key in ("rp2", "rd2", "cx", "dual", "gap", "kkt", "rel_p", "rel_d", "rel_gap", "rel_kkt"):
+        assert abs(g64[key] - getattr(o64, key)) <= 1e-12 * max(abs(getattr(o64, key)), 1e-300), key
+
+
+def test_solve_64x64_fp64_reaches_exact_optimum(s64):
+    """The small single-instance workload: 64 + 64 uniform points in [0,1]^2,
+    squared-Euclidean cost, U(0.1, 1) weights, FP64; tol 1e-6."""
+    ins = I.points_instance(64, 64, I.seed_for(0))
+    opt, *_ = oracle.exact_transport(ins.C, ins.f, ins.g)
+    sol = s64.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-6)
+    r = sol.result
+    assert sol.status == pdot.OK and r["rel_kkt"] <= 1e-6
+    assert abs(r["primal_obj"] - opt) / opt < 2e-6
+    # same reading on both sides: the FP64 oracle reaches the tolerance in a similar number of passes
+    ro = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=1e-6))
+    assert 0.5 * ro.passes <= r["passes"] <= 2.0 * ro.passes
+    # the reported KKT parts are those of the returned point
+    k = oracle.kkt(ins.C, ins.f, ins.g, _np(sol.X), _np(sol.p), _np(sol.q))
+    assert abs(k.rel_kkt - r["rel_kkt"]) <= 1e-9 * max(k.rel_kkt, 1e-30) + 1e-15
+    assert abs(k.cx - r["primal_obj"]) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n,seed,marg", [(64, 64, I.seed_for(0), "uniform"), (90, 47, 11, "dirichlet"),
+                                           (33, 150, 12, "dirichlet")])
+def test_solve_fp32_plan(s32, m, n, seed, marg):
+    ins = I.points_instance(m, n, seed, marginals=marg)
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    Co = _np(C)
+    opt, *_ = oracle.exact_transport(Co, ins.f, ins.g)
+    for tol, bound in [(1e-4, 2e-3), (1e-6, 2e-5)]:
+        sol = s32.solve(C, ins.f, ins.g, tol=tol)
+        r = sol.result
+        assert sol.status == pdot.OK, r
+        assert abs(r["primal_obj"] - opt) / opt < bound, (tol, r)
+        k = oracle.kkt(Co, ins.f, ins.g, _np(sol.X), _np(sol.p), _np(sol.q))
+        assert k.rel_kkt <= 1.05 * tol, (k.rel_kkt, r["rel_kkt"])
+
+
+def test_solve_is_deterministic(s32):
+    ins = I.points_instance(150, 170, 21)
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    a = s32.solve(C, ins.f, ins.g, tol=1e-6)
+    b = s32.solve(C, ins.f, ins.g, tol=1e-6)
+    assert a.result["passes"] == b.result["passes"] and a.result["primal_obj"] == b.result["primal_obj"]
+    assert torch.equal(a.X, b.X) and torch.equal(a.p, b.p)
+
+
+def test_solve_host_matches_device(s32):
+    ins = I.points_instance(70, 90, 31)
+    C = ins.C.astype(np.float32)
+    X = np.empty((70, 90), np.float32)
+    p, q = np.empty(70), np.empty(90)
+    st, r = pdot.pdot_solve_host(s32.h, 70, 90, C.ctypes.data, pdot.F32, 90, ins.f.ctypes.data,
+                                 ins.g.ctypes.data, 1e-5, X.ctypes.data, p.ctypes.data, q.ctypes.data)
+    assert st == pdot.OK
+    d = s32.solve(torch.tensor(C, device=DEV), ins.f, ins.g, tol=1e-5)
+    assert r.primal_obj == d.result["primal_obj"] and r.passes == d.result["passes"]
+    assert np.array_equal(X, d.X.cpu().numpy())
+
+
+def test_theory_mode_and_rel_mode_one():
+    ins = I.points_instance(24, 20, 41)
+    opt, *_ = oracle.exact_transport(ins.C, ins.f, ins.g)
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0, adaptive_step=0, adaptive_restart=0, primal_weight_update=0,
+                    beta=0.2)
+    sol = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-8)
+    assert sol.status == pdot.OK and abs(sol.result["primal_obj"] - opt) / opt < 1e-6
+    ro = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=1e-8, adaptive_step=0, adaptive_restart=0,
+                                                          primal_weight_update=0, beta=0.2))
+    assert sol.result["passes"] == ro.passes and sol.result["restarts"] == ro.restarts
+    s.close()
+    s1 = pdot.Solver(device=0, x_dtype=pdot.F64, rel_mode=1, time_limit_s=120.0)
+    sol1 = s1.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-6)
+    k = oracle.kkt(ins.C, ins.f, ins.g, _np(sol1.X), _np(sol1.p), _np(sol1.q), rel_mode=1)
+    assert sol1.status == pdot.OK and k.rel_kkt <= 1e-6
+    s1.close()
+
+
+@pytest.mark.parametrize("xt", [pdot.F32, pdot.F64])
+def test_round_parity(xt):
+    s = pdot.Solver(device=0, x_dtype=xt)
+    rng = np.random.default_rng(3)
+    m, n = 50, 70
+    f, g = rng.dirichlet(np.ones(m)), rng.dirichlet(np.ones(n))
+    X = np.outer(f, g) * rng.uniform(0.5, 1.5, (m, n))
+    if xt == pdot.F32:
+        X = X.astype(np.float32).astype(np.float64)
+    Xf = _np(s.round(X, f, g))
+    Xo = oracle.round_plan(X, f, g)
+    assert rel(Xf, Xo) < (1e-6 if xt == pdot.F32 else 1e-13)
+    if xt == pdot.F64:
+        np.testing.assert_allclose(Xf.sum(1), f, atol=1e-15)
+        np.testing.assert_allclose(Xf.sum(0), g, atol=1e-15)
+    s.close()
+
+
+def test_solve_with_rounding_gives_feasible_upper_bound():
+    ins = I.points_instance(60, 45, 51)
+    opt, *_ = oracle.exact_transport(ins.C, ins.f, ins.g)
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, round_plan=1, time_limit_s=120.0)
+    sol = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-6)
+    Xf = _np(sol.X)
+    np.testing.assert_allclose(Xf.sum(1), ins.f, atol=1e-14)
+    np.testing.assert_allclose(Xf.sum(0), ins.g, atol=1e-14)
+    assert sol.result["rounded_obj"] >= opt - 1e-14
+    assert abs(sol.result["rounded_obj"] - float(np.sum(ins.C * Xf))) < 1e-13
+    assert (sol.result["rounded_obj"] - opt) / opt < 1e-4
+    s.close()
+
+
+def test_argument_errors(s32):
+    ins = I.points_instance(8, 9, 61)
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    f = torch.tensor(ins.f, device=DEV)
+    g = torch.tensor(ins.g * 1.5, device=DEV)   # sum(g) != sum(f)
+    st, _ = pdot.pdot_solve(s32.h, 8, 9, C.data_ptr(), pdot.F32, 9, f.data_ptr(), g.data_ptr(), 1e-4)
+    assert st == pdot.ERR_ARG
+    g = torch.tensor(ins.g, device=DEV)
+    st, _ = pdot.pdot_solve(s32.h, 8, 9, C.data_ptr(), pdot.F32, 8, f.data_ptr(), g.data_ptr(), 1e-4)
+    assert st == pdot.ERR_ARG   # ldc < n
+    st, _ = pdot.pdot_solve(s32.h, 0, 9, C.data_ptr(), pdot.F32, 9, f.data_ptr(), g.data_ptr(), 1e-4)
+    assert st == pdot.ERR_ARG
+    st, _ = pdot.pdot_solve(s32.h, 8, 9, C.data_ptr(), pdot.F64, 9, f.data_ptr(), g.data_ptr(), 1e-4)
+    assert st == pdot.ERR_ARG   # F32 plan with F64 cost
+    st, _ = pdot.pdot_solve(s32.h, 8, 9, C.data_ptr(), pdot.F32, 9, f.data_ptr(), g.data_ptr(), 0.0)
+    assert st == pdot.ERR_ARG
+    # the handle stays usable
+    sol = s32.solve(C, ins.f, ins.g, tol=1e-4)
+    assert sol.status == pdot.OK
+
+
+def test_max_iter_returns_candidate():
+    ins = I.points_instance(100, 100, 71)
+    s = pdot.Solver(device=0, max_iter=128)
+    sol = s.solve(torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g, tol=1e-9)
+    assert sol.status == pdot.MAX_ITER and sol.result["passes"] == 128
+    k = oracle.kkt(ins.C.astype(np.float32).astype(np.float64), ins.f, ins.g, _np(sol.X), _np(sol.p), _np(sol.q))
+    assert abs(k.rel_kkt - sol.result["rel_kkt"]) <= 1e-4 * k.rel_kkt
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size cases (the 4096^2 image workload), checked where the oracle can
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def grid64():
+    ins = I.grid_blob_instance(64, I.seed_for(1))
+    return ins
+
+
+def test_full_size_4096_kstep_parity(s32, grid64):
+    """Two PDHG steps at the full 4096 x 4096 size, every element compared."""
+    ins = grid64
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    Co = _np(C)
+    m = n = 4096
+    z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
+    eta = 0.7 / math.sqrt(m + n)
+    g = s32.pdhg_steps(C, ins.f, ins.g, *z, k=3, eta=eta, omega=1.0)
+    o = oracle.pdhg_steps(Co, ins.f, ins.g, *z, k=3, eta=eta, omega=1.0)
+    for a, b in zip(g[:3], o[:3]):
+        assert rel(_np(a), b) < 1e-5
+
+
+def test_full_size_4096_solve_kkt_is_honest(s32, grid64):
+    """A 1e-4 solve at 4096^2: the FP64 oracle recomputes the KKT of the
+    returned (X, p, q) and agrees with the GPU's report."""
+    ins = grid64
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    sol = s32.solve(C, ins.f, ins.g, tol=1e-4)
+    assert sol.status == pdot.OK
+    k = oracle.kkt(_np(C), ins.f, ins.g, _np(sol.X), _np(sol.p), _np(sol.q))
+    assert k.rel_kkt <= 1.01e-4
+    assert abs(k.rel_kkt - sol.result["rel_kkt"]) <= 1e-3 * k.rel_kkt
+    assert abs(k.cx - sol.result["primal_obj"]) <= 1e-6 * abs(k.cx)
