@@ -167,6 +167,8 @@ struct pdot_handle {
     TileRef* d_tmap = nullptr;
     TileRef* d_vmap = nullptr;
     size_t tmap_cap = 0, vmap_cap = 0;
+    int* d_cnt = nullptr;        // [0] plan tiles, [1] vector tiles of the single-instance path
+    int* h_cnt = nullptr;        // pinned staging
     Ctrl* h_ctrl = nullptr;      // pinned
     Inst* h_inst = nullptr;      // pinned
     int* h_status = nullptr;     // pinned [2]
@@ -233,6 +235,9 @@ void ensure_maps(pdot_handle* h) {
     for (int t = 0; t < w.nvt; ++t) vm[(size_t)t] = TileRef{0, t};
     CK(cudaMemcpyAsync(h->d_tmap, tm.data(), sizeof(TileRef) * tm.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->d_vmap, vm.data(), sizeof(TileRef) * vm.size(), cudaMemcpyHostToDevice, h->stream));
+    h->h_cnt[0] = w.ntiles;
+    h->h_cnt[1] = w.nvt;
+    CK(cudaMemcpyAsync(h->d_cnt, h->h_cnt, 2 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));   // vectors above are pageable and go out of scope
 }
 
@@ -347,29 +352,17 @@ void stage_instance(pdot_handle* h, const Inst& I) {
     CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
 }
 
-double compute_norm_C(pdot_handle* h, int ctype) {
-    const Work& w = h->ws;
-    CKL(launch_sumsq_C(ctype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream));
-    launch_count(h, 1);
-    std::vector<double> parts((size_t)w.ntiles * TP);
-    CK(cudaMemcpyAsync(parts.data(), w.tpart, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    double s = 0.0;
-    for (int t = 0; t < w.ntiles; ++t) s += parts[(size_t)t * TP];
-    return std::sqrt(s);
-}
-
 void run_check(pdot_handle* h, int ttype, int mode) {
     const Work& w = h->ws;
-    CKL(launch_kkt(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, mode, h->cfg, h->stream));
-    CKL(launch_checkvec(h->d_inst, h->d_vmap, w.nvt, h->wctr, mode, h->cfg, h->stream));
+    CKL(launch_kkt(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, mode, h->cfg, h->stream));
+    CKL(launch_checkvec(h->d_inst, h->d_vmap, h->d_cnt + 1, w.nvt, h->wctr, mode, h->cfg, h->stream));
     launch_count(h, 2);
 }
 
 void run_step(pdot_handle* h, int ttype) {
     const Work& w = h->ws;
-    CKL(launch_pass(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream));
-    CKL(launch_dual(h->d_inst, h->d_vmap, w.nvt, h->wctr, h->cfg, h->stream));
+    CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream));
+    CKL(launch_dual(h->d_inst, h->d_vmap, h->d_cnt + 1, w.nvt, h->wctr, h->cfg, h->stream));
     launch_count(h, 2);
 }
 
@@ -431,6 +424,7 @@ void fill_result(const Ctrl& S, pdot_result* r, pdot_status st) {
 pdot_status map_status(int st) {
     switch (st) {
         case ST_OK: return PDOT_OK;
+        case ST_ARG: return PDOT_ERR_ARG;
         case ST_NUMERIC: return PDOT_ERR_NUMERIC;
         case ST_MAX_ITER: return PDOT_MAX_ITER;
         case ST_TIMEOUT: return PDOT_TIMEOUT;
@@ -504,10 +498,9 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     const void* Cd = prepare_C(h, m, n, C, ctype, ldc, &ldc_used);
     const Inst I = make_inst(w, Cd, ctype, ldc_used, f, g);
     stage_instance(h, I);
-    const double norm_C = compute_norm_C(h, ctype);
 
     Ctrl* S = h->h_ctrl;
-    init_ctrl(h, S, m, n, tol, norm_b, norm_C, false, 0.0, 0.0);
+    init_ctrl(h, S, m, n, tol, norm_b, 0.0, false, 0.0, 0.0);   // norms: computed by the init check
     CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
     const size_t xs = xsize_of(w.xtype);
     CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xs, h->stream));                 // X = 0 (C1)
@@ -683,6 +676,438 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Continuous-batching engine.
+//
+// Every resident instance owns a workspace (cudaMallocAsync, stream ordered)
+// and a controller; all of them advance together through the same
+// multi-instance kernels: one chunk = chunk_checks x (K x (pass, dual) +
+// (kkt, checkvec)) plus a controller snapshot copied to pinned host memory,
+// captured once as a CUDA graph (tile maps and counts live in device memory,
+// so a new batch composition only rewrites those buffers).  Between chunks
+// pdot_poll retires finished instances (stream-ordered output copies and
+// frees), admits queued requests while the HBM budget and slot count allow,
+// runs their init checks, and launches the next chunk, which then overlaps
+// with the host's bookkeeping.  Instances join at chunk boundaries, so every
+// instance's checks fall after multiples of K of its own passes.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BSlot {
+    uint64_t id = 0;
+    pdot_request req{};
+    int ttype = 0;
+    Work w;
+    size_t bytes = 0;
+    Clock::time_point t_submit;
+    bool cancel = false;
+    bool timed_out = false;
+    bool fresh = true;        // admitted, init check not run yet
+    Ctrl last{};              // last snapshot of its controller
+};
+
+template <typename T>
+struct DevArr {
+    T* d = nullptr;
+    T* h = nullptr;   // pinned staging
+    size_t cap = 0;
+    void ensure(size_t n) {
+        if (n <= cap) return;
+        size_t c = cap ? cap : 64;
+        while (c < n) c *= 2;
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+        d = nullptr;
+        h = nullptr;
+        cap = 0;
+        CK(cudaMalloc(&d, sizeof(T) * c));
+        CK(cudaMallocHost(&h, sizeof(T) * c));
+        cap = c;
+    }
+    void release() {
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+        d = nullptr;
+        h = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace
+
+struct BatchEngine {
+    std::deque<BSlot*> queue;
+    std::vector<BSlot*> live;
+    std::vector<std::pair<uint64_t, pdot_result>> done;
+    uint64_t next_id = 1;
+    size_t budget = 0, used = 0;
+    DevArr<Inst> insts;
+    DevArr<TileRef> tmap[NTT];
+    DevArr<TileRef> vmap;
+    DevArr<TileRef> tmap_init[NTT];
+    DevArr<TileRef> vmap_init;
+    DevArr<Ctrl> snap;
+    DevArr<Ctrl> ctrl_stage;
+    DevArr<int> cnt;          // [0..2] tiles per type, [3] vector tiles, [4] instances, [5..7] init tiles, [8] init vts
+    Graph graph;
+    long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev_chunk = nullptr, ev_copy = nullptr;
+    bool inflight = false;
+    int nv_live = 0;
+    int64_t chunks = 0;
+};
+
+namespace {
+
+size_t slot_bytes(pdot_handle* h, const pdot_request& r, int tile_rows) {
+    size_t b = work_bytes(r.m, r.n, h->opt.x_dtype, tile_rows, nullptr);
+    const size_t need_align = r.c_dtype == PDOT_BF16 ? 8 : 16;
+    if (((uintptr_t)r.C % need_align) != 0 || r.ldc % 4 != 0)
+        b += align_up((size_t)r.m * ((r.n + 3) / 4 * 4) * csize_of(r.c_dtype), 256);
+    return b;
+}
+
+BatchEngine* batch_of(pdot_handle* h) {
+    if (!h->batch) {
+        BatchEngine* B = new BatchEngine();
+        h->batch = B;
+        CK(cudaEventCreateWithFlags(&B->ev_chunk, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&B->ev_copy, cudaEventDisableTiming));
+        if (h->opt.hbm_budget_bytes > 0) {
+            B->budget = (size_t)h->opt.hbm_budget_bytes;
+        } else {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            B->budget = (size_t)(0.9 * (double)fr);
+        }
+        B->cnt.ensure(16);
+    }
+    return h->batch;
+}
+
+void batch_free_slot(pdot_handle* h, BSlot* s) {
+    if (s->w.base) CK(cudaFreeAsync(s->w.base, h->stream));
+    s->w.base = nullptr;
+    h->batch->used -= s->bytes;
+}
+
+// Rebuild the device-side composition: instance table, tile maps per type,
+// vector-tile map, and the init maps of freshly admitted instances.
+void batch_compose(pdot_handle* h) {
+    BatchEngine* B = h->batch;
+    const int L = (int)B->live.size();
+    B->insts.ensure((size_t)std::max(L, 1));
+    B->snap.ensure(B->insts.cap);
+    size_t nt[NTT] = {0, 0, 0}, nti[NTT] = {0, 0, 0}, nv = 0, nvi = 0;
+    for (BSlot* s : B->live) {
+        nt[s->ttype] += (size_t)s->w.ntiles;
+        nv += (size_t)s->w.nvt;
+        if (s->fresh) {
+            nti[s->ttype] += (size_t)s->w.ntiles;
+            nvi += (size_t)s->w.nvt;
+        }
+    }
+    for (int t = 0; t < NTT; ++t) {
+        B->tmap[t].ensure(std::max<size_t>(nt[t], 1));
+        B->tmap_init[t].ensure(std::max<size_t>(nti[t], 1));
+    }
+    B->vmap.ensure(std::max<size_t>(nv, 1));
+    B->vmap_init.ensure(std::max<size_t>(nvi, 1));
+    size_t ot[NTT] = {0, 0, 0}, oti[NTT] = {0, 0, 0}, ov = 0, ovi = 0;
+    for (int i = 0; i < L; ++i) {
+        BSlot* s = B->live[(size_t)i];
+        long long ldc = s->req.ldc;
+        const void* Cd = s->req.C;
+        if (s->w.Cpad) {
+            Cd = s->w.Cpad;
+            ldc = (s->req.n + 3) / 4 * 4;
+        }
+        B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
+        const int tt = s->ttype;
+        for (int t = 0; t < s->w.ntiles; ++t) {
+            B->tmap[tt].h[ot[tt]++] = TileRef{i, t};
+            if (s->fresh) B->tmap_init[tt].h[oti[tt]++] = TileRef{i, t};
+        }
+        for (int t = 0; t < s->w.nvt; ++t) {
+            B->vmap.h[ov++] = TileRef{i, t};
+            if (s->fresh) B->vmap_init.h[ovi++] = TileRef{i, t};
+        }
+    }
+    const cudaStream_t st = h->stream;
+    if (L > 0) CK(cudaMemcpyAsync(B->insts.d, B->insts.h, sizeof(Inst) * (size_t)L, cudaMemcpyHostToDevice, st));
+    for (int t = 0; t < NTT; ++t) {
+        if (ot[t]) CK(cudaMemcpyAsync(B->tmap[t].d, B->tmap[t].h, sizeof(TileRef) * ot[t], cudaMemcpyHostToDevice, st));
+        if (oti[t])
+            CK(cudaMemcpyAsync(B->tmap_init[t].d, B->tmap_init[t].h, sizeof(TileRef) * oti[t], cudaMemcpyHostToDevice, st));
+        B->cnt.h[t] = (int)ot[t];
+        B->cnt.h[5 + t] = (int)oti[t];
+    }
+    if (ov) CK(cudaMemcpyAsync(B->vmap.d, B->vmap.h, sizeof(TileRef) * ov, cudaMemcpyHostToDevice, st));
+    if (ovi) CK(cudaMemcpyAsync(B->vmap_init.d, B->vmap_init.h, sizeof(TileRef) * ovi, cudaMemcpyHostToDevice, st));
+    B->cnt.h[3] = (int)ov;
+    B->cnt.h[4] = L;
+    B->cnt.h[8] = (int)ovi;
+    CK(cudaMemcpyAsync(B->cnt.d, B->cnt.h, sizeof(int) * 9, cudaMemcpyHostToDevice, st));
+    B->nv_live = (int)ov;
+    // Init checks of the fresh instances (X = 0, p = q = 0; norms; marginal checks).
+    if (nvi > 0) {
+        CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, st));
+        for (int t = 0; t < NTT; ++t) {
+            if (!oti[t]) continue;
+            CKL(launch_kkt(t, B->insts.d, B->tmap_init[t].d, B->cnt.d + 5 + t, h->wctr, MODE_INIT, h->cfg, st));
+            launch_count(h, 1);
+        }
+        CKL(launch_checkvec(B->insts.d, B->vmap_init.d, B->cnt.d + 8, (int)nvi, h->wctr, MODE_INIT, h->cfg, st));
+        launch_count(h, 1);
+        for (BSlot* s : B->live) s->fresh = false;
+    }
+}
+
+void batch_issue_chunk(pdot_handle* h, int types) {
+    BatchEngine* B = h->batch;
+    const int K = std::max(1, h->opt.restart_check_every);
+    const int checks = std::max(1, h->opt.chunk_checks);
+    const cudaStream_t st = h->stream;
+    const int nvh = std::max(1, B->nv_live);
+    for (int c = 0; c < checks; ++c) {
+        for (int s = 0; s < K; ++s) {
+            for (int t = 0; t < NTT; ++t) {
+                if (!(types & (1 << t))) continue;
+                CKL(launch_pass(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, h->cfg, st));
+                launch_count(h, 1);
+            }
+            CKL(launch_dual(B->insts.d, B->vmap.d, B->cnt.d + 3, h->cfg.vec_blocks, h->wctr, h->cfg, st));
+            launch_count(h, 1);
+        }
+        for (int t = 0; t < NTT; ++t) {
+            if (!(types & (1 << t))) continue;
+            CKL(launch_kkt(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, MODE_CHECK, h->cfg, st));
+            launch_count(h, 1);
+        }
+        CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + 3, h->cfg.vec_blocks, h->wctr, MODE_CHECK, h->cfg, st));
+        launch_count(h, 1);
+    }
+    (void)nvh;
+    CKL(launch_snapshot(B->insts.d, B->cnt.d + 4, (int)B->snap.cap, B->snap.d, st));
+    launch_count(h, 1);
+    CK(cudaMemcpyAsync(B->snap.h, B->snap.d, sizeof(Ctrl) * B->snap.cap, cudaMemcpyDeviceToHost, st));
+}
+
+void batch_launch_chunk(pdot_handle* h) {
+    BatchEngine* B = h->batch;
+    int types = 0;
+    for (BSlot* s : B->live) types |= 1 << s->ttype;
+    const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->snap.d,
+                              (long long)(uintptr_t)B->vmap.d,
+                              (long long)(uintptr_t)B->tmap[0].d ^ ((long long)(uintptr_t)B->tmap[1].d << 1) ^
+                                  ((long long)(uintptr_t)B->tmap[2].d << 2),
+                              types, h->opt.restart_check_every, h->opt.chunk_checks,
+                              (long long)B->snap.cap};
+    if (!h->opt.use_graph) {
+        batch_issue_chunk(h, types);
+    } else {
+        if (!B->graph.exec || memcmp(key, B->graph_key, sizeof(key)) != 0) {
+            B->graph.reset();
+            const int64_t before = h->launches;
+            CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                batch_issue_chunk(h, types);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(h->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                h->launches = before;
+                throw;
+            }
+            CK(cudaStreamEndCapture(h->stream, &B->graph.g));
+            CK(cudaGraphInstantiate(&B->graph.exec, B->graph.g, 0));
+            B->graph.kernels = (int)(h->launches - before);
+            h->launches = before;
+            memcpy(B->graph_key, key, sizeof(key));
+        }
+        CK(cudaGraphLaunch(B->graph.exec, h->stream));
+        launch_count(h, B->graph.kernels);
+    }
+    CK(cudaEventRecord(B->ev_chunk, h->stream));
+    B->inflight = true;
+    B->chunks += 1;
+}
+
+pdot_result batch_result(pdot_handle* h, const BSlot* s, int status) {
+    pdot_result r;
+    memset(&r, 0, sizeof(r));
+    fill_result(s->last, &r, map_status(status));
+    const double mn = (double)s->req.m * (double)s->req.n;
+    const double bc = (double)csize_of(s->req.c_dtype), bx = (double)xsize_of(h->opt.x_dtype);
+    r.hbm_bytes = (double)s->last.passes * mn * (bc + 4.0 * bx) + (double)s->last.checks * mn * (bc + 3.0 * bx);
+    r.rounded_obj = std::numeric_limits<double>::quiet_NaN();
+    r.seconds = std::chrono::duration<double>(Clock::now() - s->t_submit).count();
+    return r;
+}
+
+// Retire finished / cancelled / timed-out instances; true if any left.
+bool batch_retire(pdot_handle* h) {
+    BatchEngine* B = h->batch;
+    bool changed = false;
+    std::vector<BSlot*> keep;
+    keep.reserve(B->live.size());
+    const double tlim = h->opt.time_limit_s;
+    for (size_t i = 0; i < B->live.size(); ++i) {
+        BSlot* s = B->live[i];
+        s->last = B->snap.h[i];
+        int stt = s->last.status;
+        if (s->cancel) stt = ST_CANCELLED;
+        else if (stt == ST_RUNNING && tlim > 0.0 &&
+                 std::chrono::duration<double>(Clock::now() - s->t_submit).count() > tlim) {
+            stt = ST_TIMEOUT;
+            s->last.res_slot = s->last.cur;
+            s->last.res_avg = 0;
+        }
+        if (stt == ST_RUNNING) {
+            keep.push_back(s);
+            continue;
+        }
+        if (stt != ST_CANCELLED && stt != ST_ARG) {
+            const size_t xs = xsize_of(s->w.xtype);
+            const int slot = s->last.res_slot;
+            if (s->req.X_out) {
+                const char* src = (const char*)s->w.X + (size_t)slot * (size_t)(s->w.m * s->w.ldx) * xs;
+                CK(cudaMemcpy2DAsync(s->req.X_out, (size_t)s->w.n * xs, src, (size_t)s->w.ldx * xs,
+                                     (size_t)s->w.n * xs, (size_t)s->w.m, cudaMemcpyDeviceToDevice, h->stream));
+            }
+            const double* V = s->w.V + (size_t)slot * 2 * (size_t)(s->w.m + s->w.n);
+            if (s->req.p_out)
+                CK(cudaMemcpyAsync(s->req.p_out, V, sizeof(double) * (size_t)s->w.m, cudaMemcpyDeviceToDevice, h->stream));
+            if (s->req.q_out)
+                CK(cudaMemcpyAsync(s->req.q_out, V + s->w.m, sizeof(double) * (size_t)s->w.n, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+        }
+        batch_free_slot(h, s);
+        B->done.emplace_back(s->id, batch_result(h, s, stt));
+        delete s;
+        changed = true;
+    }
+    B->live.swap(keep);
+    return changed;
+}
+
+bool batch_admit(pdot_handle* h) {
+    BatchEngine* B = h->batch;
+    bool changed = false;
+    const int max_slots = std::max(1, h->opt.max_batch_slots);
+    // Size the pinned controller staging once: async uploads from it are in
+    // flight until the next chunk has run.
+    B->ctrl_stage.ensure(std::max<size_t>((size_t)max_slots, B->live.size()) + 1);
+    while (!B->queue.empty() && (int)B->live.size() < max_slots) {
+        BSlot* s = B->queue.front();
+        if (s->cancel) {
+            B->queue.pop_front();
+            pdot_result r;
+            memset(&r, 0, sizeof(r));
+            r.status = PDOT_CANCELLED;
+            r.rounded_obj = std::numeric_limits<double>::quiet_NaN();
+            B->done.emplace_back(s->id, r);
+            delete s;
+            continue;
+        }
+        if (B->used + s->bytes > B->budget) break;   // FIFO: wait for memory to free up
+        B->queue.pop_front();
+        const pdot_request& r = s->req;
+        const int tr = pick_tile_rows(h, r.m, r.n, s->ttype);
+        const size_t wb = work_bytes(r.m, r.n, h->opt.x_dtype, tr, nullptr);
+        void* base = nullptr;
+        CK(cudaMallocAsync(&base, s->bytes, h->stream));
+        s->w.base = base;
+        s->w.bytes = wb;
+        work_bytes(r.m, r.n, h->opt.x_dtype, tr, &s->w);
+        if (s->bytes > wb) {
+            const long long ldp = (r.n + 3) / 4 * 4;
+            const size_t cs = csize_of(r.c_dtype);
+            s->w.Cpad = (char*)base + wb;
+            CK(cudaMemcpy2DAsync(s->w.Cpad, ldp * cs, r.C, (size_t)r.ldc * cs, (size_t)r.n * cs, (size_t)r.m,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        }
+        B->used += s->bytes;
+        // controller
+        Ctrl* S = &B->ctrl_stage.h[B->live.size()];
+        init_ctrl(h, S, r.m, r.n, r.tol > 0.0 ? r.tol : h->opt.tol, 0.0, 0.0, false, 0.0, 0.0);
+        CK(cudaMemcpyAsync(s->w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(s->w.ticket, 0, sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(s->w.X, 0, (size_t)s->w.m * s->w.ldx * xsize_of(s->w.xtype), h->stream));
+        CK(cudaMemsetAsync(s->w.V, 0, sizeof(double) * 2 * (size_t)(s->w.m + s->w.n), h->stream));
+        s->fresh = true;
+        B->live.push_back(s);
+        changed = true;
+    }
+    return changed;
+}
+
+void batch_apply_cancels(pdot_handle* h) {
+    // Stop cancelled / timed-out resident instances on the device before the next chunk.
+    BatchEngine* B = h->batch;
+    B->cnt.h[15] = ST_CANCELLED;   // pinned source word of the status writes
+    for (size_t i = 0; i < B->live.size(); ++i) {
+        BSlot* s = B->live[i];
+        if (!s->cancel) continue;
+        CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[15], sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    }
+}
+
+pdot_status batch_poll(pdot_handle* h, uint64_t* ids, pdot_result* results, int cap, int* n_done) {
+    BatchEngine* B = batch_of(h);
+    if (B->inflight) {
+        CK(cudaEventSynchronize(B->ev_chunk));
+        B->inflight = false;
+        batch_retire(h);
+    }
+    batch_apply_cancels(h);
+    bool changed = batch_admit(h);
+    const bool had_done = !B->done.empty();
+    if (had_done) CK(cudaEventRecord(B->ev_copy, h->stream));
+    if (changed || B->chunks == 0) batch_compose(h);
+    else if (had_done) batch_compose(h);
+    if (!B->live.empty()) batch_launch_chunk(h);
+    if (had_done) CK(cudaEventSynchronize(B->ev_copy));
+    int k = 0;
+    const int take = std::min<int>(cap, (int)B->done.size());
+    for (; k < take; ++k) {
+        if (ids) ids[k] = B->done[(size_t)k].first;
+        if (results) results[k] = B->done[(size_t)k].second;
+    }
+    B->done.erase(B->done.begin(), B->done.begin() + take);
+    *n_done = k;
+    return PDOT_OK;
+}
+
+void batch_destroy(pdot_handle* h) {
+    BatchEngine* B = h->batch;
+    if (!B) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (BSlot* s : B->live) {
+        if (s->w.base) cudaFreeAsync(s->w.base, h->stream);
+        delete s;
+    }
+    for (BSlot* s : B->queue) delete s;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    B->graph.reset();
+    B->insts.release();
+    for (int t = 0; t < NTT; ++t) {
+        B->tmap[t].release();
+        B->tmap_init[t].release();
+    }
+    B->vmap.release();
+    B->vmap_init.release();
+    B->snap.release();
+    B->ctrl_stage.release();
+    B->cnt.release();
+    if (B->ev_chunk) cudaEventDestroy(B->ev_chunk);
+    if (B->ev_copy) cudaEventDestroy(B->ev_copy);
+    delete B;
+    h->batch = nullptr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -772,6 +1197,8 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         CK(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
         CK(cudaMallocHost(&h->h_inst, sizeof(Inst)));
         CK(cudaMallocHost(&h->h_status, 2 * sizeof(int)));
+        CK(cudaMalloc(&h->d_cnt, 4 * sizeof(int)));
+        CK(cudaMallocHost(&h->h_cnt, 4 * sizeof(int)));
         return PDOT_OK;
     });
     if (st != PDOT_OK) {
@@ -782,12 +1209,10 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
     return PDOT_OK;
 }
 
-void pdot_batch_destroy(pdot_handle* h);
-
 pdot_status pdot_destroy(pdot_handle* h) {
     if (!h) return PDOT_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    pdot_batch_destroy(h);
+    batch_destroy(h);
     h->chunk.reset();
     free_work(h->ws);
     if (h->d_tmap) cudaFree(h->d_tmap);
@@ -799,6 +1224,8 @@ pdot_status pdot_destroy(pdot_handle* h) {
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->h_inst) cudaFreeHost(h->h_inst);
     if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->d_cnt) cudaFree(h->d_cnt);
+    if (h->h_cnt) cudaFreeHost(h->h_cnt);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return PDOT_OK;
@@ -885,6 +1312,7 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
         for (int64_t s = 0; s < k; ++s) run_step(h, ttype);
         CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (S->status == ST_ARG) throw ArgError{"invalid marginals"};
         if (S->status == ST_NUMERIC) return PDOT_ERR_NUMERIC;
         const int cur = S->cur, bar = k > 0 ? S->bar : S->cur;
         copy_plan_out(h, cur, X, cudaMemcpyDeviceToDevice);
@@ -914,15 +1342,15 @@ pdot_status pdot_kkt(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_d
         long long ldc_used = ldc;
         const void* Cd = prepare_C(h, m, n, C, c_dtype, ldc, &ldc_used);
         stage_instance(h, make_inst(w, Cd, c_dtype, ldc_used, f, g));
-        const double norm_C = compute_norm_C(h, c_dtype);
         Ctrl* S = h->h_ctrl;
-        init_ctrl(h, S, m, n, -1.0, norm_b, norm_C, false, 0.0, 0.0);
+        init_ctrl(h, S, m, n, -1.0, norm_b, 0.0, false, 0.0, 0.0);
         CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
         upload_state(h, X, p, q);
         run_check(h, ttype, MODE_INIT);
         CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (S->status == ST_ARG) throw ArgError{"invalid marginals"};
         out->rp2 = S->r_rp2; out->rd2 = S->r_rd2; out->cx = S->r_cx; out->dual = S->r_dual; out->gap = S->r_gap;
         out->kkt = S->r_kkt; out->rel_p = S->r_rel_p; out->rel_d = S->r_rel_d; out->rel_gap = S->r_rel_gap;
         out->rel_kkt = S->r_rel;
@@ -945,6 +1373,71 @@ pdot_status pdot_round(pdot_handle* h, int64_t m, int64_t n, const void* X, cons
 }
 
 int64_t pdot_launch_count(pdot_handle* h) { return h ? h->launches : 0; }
+
+pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int count, uint64_t* ticket_ids) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        if (count < 0 || (count > 0 && (!reqs || !ticket_ids))) throw ArgError{"bad request array"};
+        BatchEngine* B = batch_of(h);
+        std::vector<BSlot*> slots;
+        try {
+            for (int i = 0; i < count; ++i) {
+                const pdot_request& r = reqs[i];
+                check_common_args(h, r.m, r.n, r.C, r.c_dtype, r.ldc, r.f, r.g);
+                BSlot* s = new BSlot();
+                slots.push_back(s);
+                s->req = r;
+                s->ttype = ttype_of(r.c_dtype);
+                s->bytes = slot_bytes(h, r, pick_tile_rows(h, r.m, r.n, s->ttype));
+                if (s->bytes > B->budget) {
+                    for (BSlot* x : slots) delete x;
+                    h->last_error = "request exceeds the HBM budget";
+                    return PDOT_BUSY;
+                }
+            }
+        } catch (...) {
+            for (BSlot* x : slots) delete x;
+            throw;
+        }
+        const auto now = Clock::now();
+        for (int i = 0; i < count; ++i) {
+            slots[(size_t)i]->id = B->next_id++;
+            slots[(size_t)i]->t_submit = now;
+            ticket_ids[i] = slots[(size_t)i]->id;
+            B->queue.push_back(slots[(size_t)i]);
+        }
+        return PDOT_OK;
+    });
+}
+
+pdot_status pdot_poll(pdot_handle* h, uint64_t* done_ids, pdot_result* done_results, int cap, int* n_done) {
+    if (!h || !n_done || cap < 0) return PDOT_ERR_ARG;
+    *n_done = 0;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        return batch_poll(h, done_ids, done_results, cap, n_done);
+    });
+}
+
+pdot_status pdot_cancel(pdot_handle* h, uint64_t ticket) {
+    if (!h) return PDOT_ERR_ARG;
+    BatchEngine* B = h->batch;
+    if (!B) return PDOT_ERR_ARG;
+    for (BSlot* s : B->queue)
+        if (s->id == ticket) { s->cancel = true; return PDOT_OK; }
+    for (BSlot* s : B->live)
+        if (s->id == ticket) { s->cancel = true; return PDOT_OK; }
+    return PDOT_ERR_ARG;
+}
+
+pdot_status pdot_batch_pending(pdot_handle* h, int* queued, int* running) {
+    if (!h) return PDOT_ERR_ARG;
+    BatchEngine* B = h->batch;
+    if (queued) *queued = B ? (int)B->queue.size() : 0;
+    if (running) *running = B ? (int)B->live.size() : 0;
+    return PDOT_OK;
+}
 
 pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
                            const double* f, const double* g, int reps, double* ms_per_pass, double* bytes_per_pass) {
@@ -979,7 +1472,7 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         // its own, so the next launch finds its counter at zero.
         for (int r = 0; r < reps; ++r) {
             const int wc = (r & 1) ? wc_index(WC_AUX, ttype) : wc_index(WC_PASS, ttype);
-            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, w.ntiles, h->wctr, h->cfg, h->stream, wc));
+            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream, wc));
         }
         CK(cudaEventRecord(e1, h->stream));
         CK(cudaEventSynchronize(e1));
@@ -997,24 +1490,3 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// batch engine (placeholder until the continuous-batching engine lands)
-// ---------------------------------------------------------------------------
-extern "C" {
-void pdot_batch_destroy(pdot_handle*) {}
-pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request*, int, uint64_t*) {
-    if (h) h->last_error = "batch engine not available";
-    return PDOT_ERR_ARG;
-}
-pdot_status pdot_poll(pdot_handle* h, uint64_t*, pdot_result*, int, int* n_done) {
-    if (n_done) *n_done = 0;
-    if (h) h->last_error = "batch engine not available";
-    return PDOT_ERR_ARG;
-}
-pdot_status pdot_cancel(pdot_handle*, uint64_t) { return PDOT_ERR_ARG; }
-pdot_status pdot_batch_pending(pdot_handle*, int* queued, int* running) {
-    if (queued) *queued = 0;
-    if (running) *running = 0;
-    return PDOT_OK;
-}
-}

@@ -29,7 +29,7 @@ constexpr int MODE_CHECK = 0;
 constexpr int MODE_INIT = 1;
 
 // Status codes (same values as pdot_status in include/pdot.h).
-constexpr int ST_OK = 0, ST_NUMERIC = 4, ST_MAX_ITER = 5, ST_TIMEOUT = 6, ST_CANCELLED = 9;
+constexpr int ST_OK = 0, ST_ARG = 1, ST_NUMERIC = 4, ST_MAX_ITER = 5, ST_TIMEOUT = 6, ST_CANCELLED = 9;
 
 struct Ctrl {
     // iteration state
@@ -99,15 +99,19 @@ struct LaunchCfg {
     int pass_u;           // rows per load batch in the FP32-plan pass (2 or 4)
 };
 
-int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
-                void* stream, int wc_override = -1);
-int launch_dual(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, const LaunchCfg& cfg, void* stream);
-int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, int mode,
+// Tile and vector-tile counts are read from device memory, so one captured
+// graph serves every batch composition; nv_hint sizes the vector grids.
+int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                const LaunchCfg& cfg, void* stream, int wc_override = -1);
+int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
+                const LaunchCfg& cfg, void* stream);
+int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,
                const LaunchCfg& cfg, void* stream);
-int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, int mode, const LaunchCfg& cfg,
-                    void* stream);
-int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
-                   void* stream);
+int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
+                    const LaunchCfg& cfg, void* stream);
+int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                   const LaunchCfg& cfg, void* stream);
+int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream);
 int occupancy_tile_blocks_per_sm(int ttype);
 int occupancy_vec_blocks_per_sm();
 

@@ -220,7 +220,7 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
                 const A R = (c[u][e] - pv[u]) - qv[e];          // reduced cost C - p - q
                 A v = x[u][e] - tau * R;
                 v = v > A(0) ? v : A(0);                         // projection onto X >= 0
-                v = valid[e] ? v : A(0);                         // padding columns stay 0
+                v = (valid[e] && rv) ? v : A(0);                 // padding columns / rows past the tile stay 0
                 const A d = v - x[u][e];
                 dxa += d * d;
                 rs += v;
@@ -255,7 +255,8 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
 
 template <typename TC, typename TX, int U>
 __global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
-k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc) {
+k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
+    const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -393,7 +394,8 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, int* s_l
 }
 
 __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
-                                             int NV, unsigned* wctr) {
+                                             const int* __restrict__ NVp, unsigned* wctr) {
+    const int NV = *NVp;
     __shared__ double red[(VT / 32) * 3];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_DUAL, 0);
@@ -480,12 +482,13 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
             A rs = A(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                if (!valid[e]) continue;
+                if (!valid[e] || !rv) continue;
                 const A Rc = (c[u][e] - pv[u]) - qv[e];
                 t[0] += c[u][e] * x[u][e];
                 t[1] += Rc < A(0) ? Rc * Rc : A(0);             // [p + q - C]^+ squared
                 const A da = x[u][e] - xa[u][e];
                 t[4] += da * da;
+                if (init) t[2] += c[u][e] * c[u][e];             // ||C||_F^2 (once per solve)
                 if (avg) {
                     const A Rb = (c[u][e] - pbv[u]) - qbv[e];
                     t[2] += c[u][e] * xb[u][e];
@@ -522,7 +525,8 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
 
 template <typename TC, typename TX>
 __global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
-k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc, int mode) {
+k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc, int mode) {
+    const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -569,8 +573,21 @@ __device__ void report(Ctrl* S, const KP& k) {
 }
 
 // A: 0 rp2 cur, 1 rp2 avg, 2 dual cur, 3 dual avg, 4 ||dy_anchor||^2 cur, 5 avg,
-//    6 <C,X>, 7 rd2 cur, 8 <C,Xbar>, 9 rd2 avg, 10 ||X - Xa||^2, 11 ||Xbar - Xa||^2
+//    6 <C,X>, 7 rd2 cur, 8 <C,Xbar>, 9 rd2 avg, 10 ||X - Xa||^2, 11 ||Xbar - Xa||^2.
+// In MODE_INIT: 1 sum f, 3 sum g, 4 ||[f;g]||^2, 5 invalid marginal entries,
+//    8 ||C||_F^2.
 __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
+    if (mode == MODE_INIT) {
+        // Data norms for the relative measures, and the marginal checks of the ABI.
+        S->norm_b = sqrt(A[4]);
+        S->norm_C = sqrt(A[8]);
+        const double sf = A[1], sg = A[3];
+        if (A[5] > 0.0 || !(fabs(sf - sg) <= 1e-9 * fmax(sf, 1.0))) {
+            S->status = ST_ARG;
+            S->res_slot = S->cur;
+            return;
+        }
+    }
     KP c;
     kkt_parts(S, A[0], A[7], A[6], A[2], c);
     S->checks += 1;
@@ -679,6 +696,10 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
             Vc[so] = s;
             a[0] = (s - b) * (s - b);
             a[2] = b * y;
+            // marginal statistics: sum f, sum g, ||[f;g]||^2, invalid entries
+            if (row) a[1] = b; else a[3] = b;
+            a[4] = b * b;
+            a[5] = (b >= 0.0 && isfinite(b)) ? 0.0 : 1.0;
         } else {
             const double r = Vc[so];
             a[0] = (r - b) * (r - b);
@@ -730,7 +751,8 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
 }
 
 __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
-                                                 int NV, unsigned* wctr, int mode) {
+                                                 const int* __restrict__ NVp, unsigned* wctr, int mode) {
+    const int NV = *NVp;
     __shared__ double red[(VT / 32) * VP];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_CHECK, 0);
@@ -775,7 +797,8 @@ __device__ __forceinline__ void sumsq_tile(const Inst& I, int lt, int lane) {
 
 template <typename TC>
 __global__ void __launch_bounds__(TWARPS * 32)
-k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* wctr, int wc) {
+k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
+    const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -787,12 +810,24 @@ k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int 
 }
 
 // ---------------------------------------------------------------------------
+// Snapshot of every resident instance's controller (one D2H copy per chunk)
+// ---------------------------------------------------------------------------
+__global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict__ count, Ctrl* out) {
+    const int n = *count;
+    const int words = (int)(sizeof(Ctrl) / sizeof(int));
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * words; t += gridDim.x * blockDim.x) {
+        const int i = t / words, w = t % words;
+        reinterpret_cast<int*>(out + i)[w] = reinterpret_cast<const int*>(insts[i].ctrl)[w];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static int err(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 
-int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
-                void* stream, int wc_override) {
+int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                const LaunchCfg& cfg, void* stream, int wc_override) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
     if (ttype == TT_F64) k_pass<double, double, 2><<<cfg.tile_blocks_f64, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
@@ -805,13 +840,13 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, un
     }
     return err(cudaGetLastError());
 }
-int launch_dual(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, const LaunchCfg& cfg,
-                void* stream) {
-    const int blocks = NV < cfg.vec_blocks ? NV : cfg.vec_blocks;
+int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
+                const LaunchCfg& cfg, void* stream) {
+    const int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
     k_dual<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr);
     return err(cudaGetLastError());
 }
-int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, int mode,
+int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,
                const LaunchCfg& cfg, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_index(WC_KKT, ttype);
@@ -820,19 +855,28 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, int T, uns
     else k_kkt<float, float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
     return err(cudaGetLastError());
 }
-int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, int NV, unsigned* wctr, int mode,
+int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream) {
-    const int blocks = NV < cfg.vec_blocks ? NV : cfg.vec_blocks;
+    const int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
     k_checkvec<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr, mode);
     return err(cudaGetLastError());
 }
-int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, int T, unsigned* wctr, const LaunchCfg& cfg,
-                   void* stream) {
+int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                   const LaunchCfg& cfg, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_index(WC_AUX, ctype == 2 ? TT_F64 : (ctype == 1 ? TT_BF16 : TT_F32));
     if (ctype == 2) k_sumsq_C<double><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
     else if (ctype == 1) k_sumsq_C<unsigned short><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
     else k_sumsq_C<float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    return err(cudaGetLastError());
+}
+
+int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream) {
+    const int words = (int)(sizeof(Ctrl) / sizeof(int));
+    int blocks = (max_count * words + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    k_snapshot<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_insts, count, out);
     return err(cudaGetLastError());
 }
 

@@ -383,3 +383,69 @@ class Solver:
 
     def launch_count(self) -> int:
         return pdot_launch_count(self.h)
+
+
+class BatchSolver:
+    """Continuous-batching front end over pdot_batch_submit / pdot_poll.
+
+    ``submit`` queues one solve (torch CUDA tensors; they are kept alive until
+    the ticket is reported) and returns its ticket; ``poll`` advances the
+    engine by one chunk and returns the finished tickets.
+    """
+
+    def __init__(self, options: Options | None = None, device: int = 0, stream=None, **overrides):
+        self.solver = Solver(options, device, stream, **overrides)
+        self.h = self.solver.h
+        self._keep = {}
+
+    @property
+    def options(self):
+        return self.solver.options
+
+    def close(self):
+        self._keep.clear()
+        self.solver.close()
+
+    def submit(self, C, f, g, tol: float = 0.0, want_plan: bool = True, tag: int = 0) -> int:
+        torch = _torch()
+        C, f, g = self.solver._prep(C, f, g)
+        m, n = C.shape
+        xt = _xdtype_torch(self.options.x_dtype)
+        X = torch.empty((m, n), dtype=xt, device=C.device) if want_plan else None
+        p = torch.empty(m, dtype=torch.float64, device=C.device)
+        q = torch.empty(n, dtype=torch.float64, device=C.device)
+        r = Request(m=m, n=n, C=C.data_ptr(), c_dtype=_cdtype(C), ldc=C.stride(0), f=f.data_ptr(), g=g.data_ptr(),
+                    tol=tol, X_out=X.data_ptr() if X is not None else None, p_out=p.data_ptr(),
+                    q_out=q.data_ptr(), user_tag=tag)
+        st, ids = pdot_batch_submit(self.h, [r])
+        _check(self.h, st)
+        self._keep[ids[0]] = (C, f, g, X, p, q)
+        return ids[0]
+
+    def poll(self, cap: int = 1024) -> list[tuple[int, Solution]]:
+        st, done = pdot_poll(self.h, cap)
+        _check(self.h, st)
+        out = []
+        for tid, r in done:
+            C, f, g, X, p, q = self._keep.pop(tid, (None,) * 6)
+            out.append((tid, Solution(r.as_dict(), r.status, X, p, q)))
+        return out
+
+    def cancel(self, ticket: int) -> int:
+        return pdot_cancel(self.h, ticket)
+
+    def pending(self) -> tuple[int, int]:
+        st, q, r = pdot_batch_pending(self.h)
+        return q, r
+
+    def run(self) -> dict:
+        """Poll until every submitted ticket is reported."""
+        res = {}
+        while True:
+            for tid, sol in self.poll():
+                res[tid] = sol
+            q, r = self.pending()
+            if q == 0 and r == 0:
+                for tid, sol in self.poll():
+                    res[tid] = sol
+                return res

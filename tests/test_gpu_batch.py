@@ -1,0 +1,100 @@
+"""GPU tests of the batch engine (continuous batching): every instance's
+result in a batch equals its single-instance solve (the same kernels, the
+same per-instance tiles and fixed-order reductions), alone or in any mix,
+whenever it joins; cancellation, admission by budget."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2407_19689_gb300 import instances as I  # noqa: E402
+from paper_2407_19689_gb300 import pdot  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    oracle.build()
+    pdot.load(build_if_missing=True)
+
+
+def _inst(k):
+    sizes = [(64, 64), (130, 97), (257, 300), (1, 9), (40, 333), (512, 128), (77, 77), (300, 41)]
+    m, n = sizes[k % len(sizes)]
+    ins = I.points_instance(m, n, 7000 + k, marginals="dirichlet", alpha=1.0)
+    return torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g
+
+
+def _same(a, b):
+    ra, rb = a.result, b.result
+    assert ra["status"] == rb["status"] == pdot.OK
+    assert ra["passes"] == rb["passes"] and ra["restarts"] == rb["restarts"]
+    assert ra["primal_obj"] == rb["primal_obj"] and ra["rel_kkt"] == rb["rel_kkt"]
+    assert torch.equal(a.X, b.X) and torch.equal(a.p, b.p) and torch.equal(a.q, b.q)
+
+
+def test_batch_equals_single_solves():
+    single = pdot.Solver(device=0, time_limit_s=120.0)
+    batch = pdot.BatchSolver(device=0, time_limit_s=120.0)
+    insts = [_inst(k) for k in range(12)]
+    ids = [batch.submit(C, f, g, tol=1e-6) for C, f, g in insts]
+    res = batch.run()
+    assert sorted(res) == sorted(ids)
+    for tid, (C, f, g) in zip(ids, insts):
+        _same(res[tid], single.solve(C, f, g, tol=1e-6))
+        opt, *_ = oracle.exact_transport(C.double().cpu().numpy(), f, g)
+        assert abs(res[tid].result["primal_obj"] - opt) / opt < 2e-5
+    single.close()
+    batch.close()
+
+
+def test_continuous_admission_alone_vs_mix():
+    """Requests submitted while others run join at a chunk boundary; each
+    result equals the same request solved alone."""
+    batch = pdot.BatchSolver(device=0, time_limit_s=120.0, chunk_checks=1)
+    alone = pdot.BatchSolver(device=0, time_limit_s=120.0, chunk_checks=1)
+    insts = [_inst(k) for k in range(8)]
+    ids = [batch.submit(*insts[k], tol=1e-6) for k in range(3)]
+    got = {}
+    for tid, sol in batch.poll():
+        got[tid] = sol
+    ids += [batch.submit(*insts[k], tol=1e-6) for k in range(3, 6)]
+    for tid, sol in batch.poll():
+        got[tid] = sol
+    ids += [batch.submit(*insts[k], tol=1e-4 if k == 6 else 1e-6) for k in range(6, 8)]
+    got.update(batch.run())
+    for k, tid in enumerate(ids):
+        a = alone.submit(*insts[k], tol=1e-4 if k == 6 else 1e-6)
+        ra = alone.run()
+        _same(got[tid], ra[a])
+    batch.close()
+    alone.close()
+
+
+def test_cancel_and_budget():
+    b = pdot.BatchSolver(device=0, hbm_budget_bytes=64 << 20, time_limit_s=60.0)
+    C, f, g = _inst(2)
+    t1 = b.submit(C, f, g, tol=1e-9)
+    t2 = b.submit(C, f, g, tol=1e-6)
+    assert b.cancel(t1) == pdot.OK
+    res = b.run()
+    assert res[t1].status == pdot.CANCELLED and res[t2].status == pdot.OK
+    big = torch.zeros((4096, 4096), dtype=torch.float32, device=DEV)
+    fb = np.full(4096, 1 / 4096)
+    with pytest.raises(pdot.PdotError) as e:
+        b.submit(big, fb, fb)
+    assert e.value.status == pdot.BUSY
+    b.close()
+
+
+def test_batch_rejects_bad_marginals_on_device():
+    b = pdot.BatchSolver(device=0, time_limit_s=60.0)
+    C, f, g = _inst(1)
+    t_bad = b.submit(C, f, g * 2.0)
+    t_ok = b.submit(C, f, g, tol=1e-4)
+    res = b.run()
+    assert res[t_bad].status == pdot.ERR_ARG and res[t_ok].status == pdot.OK
+    b.close()
