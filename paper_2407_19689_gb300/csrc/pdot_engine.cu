@@ -88,7 +88,7 @@ size_t work_bytes(long long m, long long n, int xtype, int tile_rows, Work* w) {
     const int nstrips = (int)((n + STRIP - 1) / STRIP);
     const int nchunks = (int)((m + tile_rows - 1) / tile_rows);
     const long long ntiles = (long long)nstrips * nchunks;
-    const int nvt = (int)((m + n + VT - 1) / VT);
+    const int nvt = (int)((m + n + VE - 1) / VE);
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     const size_t oX = take((size_t)NSLOT * m * ldx * xsize_of(xtype));

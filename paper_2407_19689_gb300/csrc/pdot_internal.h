@@ -10,7 +10,8 @@
 //          [p (m) | q (n) | r = X1 (m) | c = X^T1 (n)].
 //   rowpart[nstrips][m], colpart[nchunks][ldx]: FP64 partial row/column sums
 //          written by the plan-tile kernels and reduced in a fixed order.
-//   tpart[ntiles][TP], vpart[nvt][VP]: FP64 per-tile scalar partials.
+//   tpart[ntiles][TP], vpart[nvt][VP]: FP64 per-tile scalar partials
+//          (nvt = ceil((m+n)/VE) vector tiles).
 //   Ctrl : the scalar state of Algorithm 2 and the Sec. 5 controller.
 #pragma once
 #include <cstdint>
@@ -20,7 +21,9 @@ namespace pdot {
 constexpr int NSLOT = 5;
 constexpr int STRIP = 128;   // plan-tile width: 32 lanes x 4 consecutive columns
 constexpr int TWARPS = 8;    // warps per CTA in the plan-tile kernels
-constexpr int VT = 256;      // entries per vector tile = threads per CTA in vector kernels
+constexpr int VT = 256;      // threads per CTA in the vector kernels
+constexpr int VE = 32;       // entries per vector tile (one warp wide)
+constexpr int VG = VT / 32;  // partial-sum groups per vector tile
 constexpr int TP = 6;        // scalars per plan-tile partial
 constexpr int VP = 12;       // scalars per vector-tile partial
 

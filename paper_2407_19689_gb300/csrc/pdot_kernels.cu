@@ -326,9 +326,35 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
     S->sigma = eta * S->omega;
 }
 
-__device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, int* s_last) {
+// Fixed-order sum of a partial column: group g (of VG) adds partials g, g+VG, ...
+// of entry `idx`, then group 0 combines the VG group sums in order.
+__device__ __forceinline__ double group_sum(const double* part, long long stride, int count, long long idx,
+                                            bool active, double* sgrp) {
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    double s = 0.0;
+    if (active)
+        for (int k = grp; k < count; k += VG) s += part[(long long)k * stride + idx];
+    sgrp[grp * 32 + lane] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (grp == 0) {
+#pragma unroll
+        for (int g2 = 0; g2 < VG; ++g2) t += sgrp[g2 * 32 + lane];
+    }
+    __syncthreads();
+    return t;
+}
+
+__device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* sgrp, int* s_last) {
     const long long m = I.m, n = I.n;
-    const long long e = (long long)lvt * VT + threadIdx.x;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const long long e = (long long)lvt * VE + lane;
+    const bool row = e < m, col = !row && e < m + n;
+    const long long idx = row ? e : e - m;
+    // One uniform call (it synchronises the block): rows reduce strip partials,
+    // columns reduce chunk partials.
+    const double s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
+                               row || col, sgrp);
     const double sigma = S->sigma;
     const long long k = S->k;
     const bool first = k == 0;
@@ -338,30 +364,18 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, int* s_l
     const double* Vb = slot_v(I, S->bar);
     double* Vbn = slot_v(I, S->barn);
     double a[3] = {0.0, 0.0, 0.0};   // ||dy||^2, dy^T A dx, ||dX||^2 (tile slice)
-    if (e < m) {
-        const long long i = e;
-        double s = 0.0;
-        for (int st = 0; st < I.nstrips; ++st) s += I.rowpart[(long long)st * m + i];
-        const double r = Vc[m + n + i], p = Vc[i];
-        const double pn = p + sigma * (I.f[i] - (2.0 * s - r));
-        Vn[i] = pn;
-        Vn[m + n + i] = s;
-        Vbn[i] = first ? pn : Vb[i] + w * (pn - Vb[i]);
-        const double dp = pn - p;
-        a[0] = dp * dp;
-        a[1] = dp * (s - r);
-    } else if (e < m + n) {
-        const long long j = e - m;
-        double s = 0.0;
-        for (int ch = 0; ch < I.nchunks; ++ch) s += I.colpart[(long long)ch * I.ldx + j];
-        const double c = Vc[2 * m + n + j], q = Vc[m + j];
-        const double qn = q + sigma * (I.g[j] - (2.0 * s - c));
-        Vn[m + j] = qn;
-        Vn[2 * m + n + j] = s;
-        Vbn[m + j] = first ? qn : Vb[m + j] + w * (qn - Vb[m + j]);
-        const double dq = qn - q;
-        a[0] = dq * dq;
-        a[1] = dq * (s - c);
+    if (grp == 0 && (row || col)) {
+        const long long yo = row ? idx : m + idx;               // p_i or q_j
+        const long long so = row ? m + n + idx : 2 * m + n + idx;   // r_i or c_j
+        const double b = row ? I.f[idx] : I.g[idx];
+        const double r = Vc[so], y = Vc[yo];
+        const double yn = y + sigma * (b - (2.0 * s - r));
+        Vn[yo] = yn;
+        Vn[so] = s;
+        Vbn[yo] = first ? yn : Vb[yo] + w * (yn - Vb[yo]);
+        const double dy = yn - y;
+        a[0] = dy * dy;
+        a[1] = dy * (s - r);
     }
     const long long T = I.ntiles;
     const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
@@ -397,6 +411,7 @@ __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, con
                                              const int* __restrict__ NVp, unsigned* wctr) {
     const int NV = *NVp;
     __shared__ double red[(VT / 32) * 3];
+    __shared__ double sgrp[VG * 32];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_DUAL, 0);
     reset_other_counters(wctr, wc);
@@ -410,7 +425,7 @@ __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, con
         const Inst& I = insts[tr.inst];
         Ctrl* S = I.ctrl;
         if (S->status != ST_RUNNING) continue;
-        dual_tile(I, S, tr.local, red, &s_last);
+        dual_tile(I, S, tr.local, red, sgrp, &s_last);
     }
 }
 
@@ -669,28 +684,29 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
     S->sigma = S->eta * S->omega;
 }
 
-__device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double* red, int* s_last) {
+__device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double* red, double* sgrp, int* s_last) {
     const long long m = I.m, n = I.n;
-    const long long e = (long long)lvt * VT + threadIdx.x;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const long long e = (long long)lvt * VE + lane;
     const bool init = mode == MODE_INIT;
     const bool avg = !init && S->k > 0;
+    const bool row = e < m, col = !row && e < m + n;
+    const long long idx = row ? e : e - m;          // i or j
+    double s = 0.0;
+    if (init || avg) {   // uniform across the block
+        s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx, row || col,
+                      sgrp);
+    }
     double* Vc = slot_v(I, S->cur);
     double* Vb = slot_v(I, S->bar);
     const double* Va = slot_v(I, S->anc);
     double a[VP];
 #pragma unroll
     for (int k = 0; k < VP; ++k) a[k] = 0.0;
-    if (e < m + n) {
-        const bool row = e < m;
-        const long long idx = row ? e : e - m;          // i or j
-        const long long yo = row ? idx : m + idx;       // offset of p_i / q_j in a vector set
+    if (grp == 0 && (row || col)) {
+        const long long yo = row ? idx : m + idx;               // offset of p_i / q_j in a vector set
         const long long so = row ? m + n + idx : 2 * m + n + idx;   // offset of r_i / c_j
         const double b = row ? I.f[idx] : I.g[idx];
-        double s = 0.0;
-        if (init || avg) {
-            if (row) { for (int st = 0; st < I.nstrips; ++st) s += I.rowpart[(long long)st * m + idx]; }
-            else { for (int ch = 0; ch < I.nchunks; ++ch) s += I.colpart[(long long)ch * I.ldx + idx]; }
-        }
         const double y = Vc[yo];
         if (init) {
             Vc[so] = s;
@@ -754,6 +770,7 @@ __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts,
                                                  const int* __restrict__ NVp, unsigned* wctr, int mode) {
     const int NV = *NVp;
     __shared__ double red[(VT / 32) * VP];
+    __shared__ double sgrp[VG * 32];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_CHECK, 0);
     reset_other_counters(wctr, wc);
@@ -767,7 +784,7 @@ __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts,
         const Inst& I = insts[tr.inst];
         Ctrl* S = I.ctrl;
         if (S->status != ST_RUNNING) continue;
-        checkvec_tile(I, S, tr.local, mode, red, &s_last);
+        checkvec_tile(I, S, tr.local, mode, red, sgrp, &s_last);
     }
 }
 
