@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--grid", type=int, default=64, help="grid side G: m = n = G^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
+                    help="grid: the single image-like instance (default, the headline); batch: 256 uneven "
+                         "instances through the batch engine vs one instance per launch; serve: Poisson "
+                         "request stream through the continuous-batching engine vs a plain FIFO server")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: 0.8 x measured capacity)")
+    ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
     return ap.parse_args()
 
 
@@ -321,10 +329,106 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# batched and served workloads (manual runs; one JSON line each)
+# ---------------------------------------------------------------------------
+def run_batch(args):
+    import torch
+
+    from paper_2407_19689_gb300 import _build, pdot
+    from paper_2407_19689_gb300 import instances as I
+    _build.build()
+    pdot.load()
+    dev = "cuda:0"
+    sizes = I.batch_sizes(args.batch_count, I.seed_for(3))
+    insts = []
+    for k, (m, n) in enumerate(sizes):
+        ins = I.batch_instance(m, n, I.seed_for(3, k + 1))
+        insts.append((torch.tensor(ins.C, dtype=torch.float32, device=dev), ins.f, ins.g))
+    elems = sum(m * n for m, n in sizes)
+
+    def batched():
+        b = pdot.BatchSolver(device=0, chunk_checks=4)
+        for C, f, g in insts:
+            b.submit(C, f, g, tol=args.tol, want_plan=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = b.run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        launches = b.solver.launch_count()
+        b.close()
+        return dt, res, launches
+
+    def plain():
+        s = pdot.Solver(device=0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = [s.solve(C, f, g, tol=args.tol, want_plan=False) for C, f, g in insts]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        s.close()
+        return dt, res
+
+    batched()   # warm-up (graph capture, allocator pools)
+    tb, rb, launches = batched()
+    tp, rp = plain()
+    okb = sum(1 for v in rb.values() if v.status == pdot.OK)
+    okp = sum(1 for v in rp if v.status == pdot.OK)
+    objs_b = sorted((tid, v.result["primal_obj"]) for tid, v in rb.items())
+    maxdiff = max(abs(a[1] - b.result["primal_obj"]) / abs(b.result["primal_obj"])
+                  for a, b in zip(objs_b, rp))
+    line = {"metric": METRIC, "value": len(insts) / tb, "unit": f"solves/s ({len(insts)} uneven instances to "
+            f"{args.tol:g} rel. KKT)", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tb * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals",
+            "data": "synthetic",
+            "config": {"workload": f"batch{len(insts)}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems,
+                       "tol": args.tol},
+            "batched": {"seconds": tb, "solves_per_s": len(insts) / tb, "ok": okb, "gpu_launches": launches},
+            "plain": {"seconds": tp, "solves_per_s": len(insts) / tp, "ok": okp,
+                      "form": "pdot_solve one instance at a time, same kernels"},
+            "speedup_vs_plain": tp / tb, "max_rel_obj_diff_batched_vs_plain": maxdiff}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+
+    from paper_2407_19689_gb300 import _build, pdot, serve
+    from paper_2407_19689_gb300 import instances as I
+    _build.build()
+    pdot.load()
+    rate = args.rate
+    if rate <= 0.0:
+        # capacity probe: a short saturated burst
+        probe = I.serve_requests(24, 1e9, I.seed_for(4, 1), hi=args.serve_max)
+        r = serve.serve_batched(probe)
+        rate = 0.8 * len(probe) / r["wall_s"]
+    reqs = I.serve_requests(args.requests, rate, I.seed_for(4), hi=args.serve_max)
+    rb = serve.serve_batched(reqs)
+    sb = serve.summary(rb)
+    rp = serve.serve_plain(reqs)
+    sp = serve.summary(rp)
+    diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
+    line = {"metric": METRIC, "value": sb["solves_per_s"], "unit": "solves/s (Poisson stream)",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": sb["wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals", "data": "synthetic",
+            "config": {"workload": f"serve{len(reqs)}_poisson_loguniform128-{args.serve_max}", "rate_per_s": rate,
+                       "admission_budget_bytes": 150 << 30},
+            "continuous_batching": sb, "plain_fifo": sp, "p99_speedup_vs_plain": sp["p99_s"] / sb["p99_s"],
+            "max_rel_obj_diff_vs_plain": float(np.max(diffs)) if diffs else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

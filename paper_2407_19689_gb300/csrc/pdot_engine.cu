@@ -59,6 +59,17 @@ struct ArgError {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The plan kernels read C in 16-byte units (row starts 16-byte aligned): FP32
+// and FP64 rows need ldc % 4 == 0, BF16 rows ldc % 8 == 0.
+bool c_layout_ok(const void* C, int ctype, long long ldc) {
+    const long long q = ctype == PDOT_BF16 ? 8 : 4;
+    return ((uintptr_t)C % 16) == 0 && ldc % q == 0;
+}
+long long padded_ldc(long long n, int ctype) {
+    const long long q = ctype == PDOT_BF16 ? 8 : 4;
+    return (n + q - 1) / q * q;
+}
+
 int ttype_of(int ctype) { return ctype == PDOT_F64 ? TT_F64 : (ctype == PDOT_BF16 ? TT_BF16 : TT_F32); }
 size_t csize_of(int ctype) { return ctype == PDOT_F64 ? 8 : (ctype == PDOT_BF16 ? 2 : 4); }
 size_t xsize_of(int xtype) { return xtype == PDOT_F64 ? 8 : 4; }
@@ -287,14 +298,13 @@ int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype) {
 const void* prepare_C(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                       long long* ldc_used) {
     const size_t cs = csize_of(ctype);
-    const size_t need_align = ctype == PDOT_BF16 ? 8 : 16;
-    if (((uintptr_t)C % need_align) == 0 && ldc % 4 == 0) {
+    if (c_layout_ok(C, ctype, ldc)) {
         *ldc_used = ldc;
         return C;
     }
     // Copy into a padded buffer whose rows start on 16-byte boundaries.
     Work& w = h->ws;
-    const long long ldp = (n + 3) / 4 * 4;
+    const long long ldp = padded_ldc(n, ctype);
     const size_t bytes = (size_t)m * ldp * cs;
     if (w.cpad_bytes < bytes) {
         if (w.Cpad) cudaFree(w.Cpad);
@@ -374,7 +384,9 @@ void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
 void launch_chunk(pdot_handle* h, int ttype, int K) {
     const Work& w = h->ws;
     const long long key[6] = {(long long)(uintptr_t)w.base, (long long)(uintptr_t)h->d_tmap ^ ((long long)(uintptr_t)h->d_vmap << 1),
-                              w.m * 4 + ttype, w.n, K, (long long)h->cfg.pass_u * 1000 + w.tile_rows};
+                              w.m * 4 + ttype, w.n, K,
+                              (long long)h->cfg.pdl * 1000000 + (long long)h->cfg.pass_bulk * 100000 +
+                                  (long long)h->cfg.pass_u * 1000 + w.tile_rows};
     if (!h->opt.use_graph) {
         issue_chunk_kernels(h, ttype, K);
         return;
@@ -425,6 +437,7 @@ pdot_status map_status(int st) {
     switch (st) {
         case ST_OK: return PDOT_OK;
         case ST_ARG: return PDOT_ERR_ARG;
+        case ST_DEVICE: return PDOT_ERR_CUDA;
         case ST_NUMERIC: return PDOT_ERR_NUMERIC;
         case ST_MAX_ITER: return PDOT_MAX_ITER;
         case ST_TIMEOUT: return PDOT_TIMEOUT;
@@ -760,9 +773,8 @@ namespace {
 
 size_t slot_bytes(pdot_handle* h, const pdot_request& r, int tile_rows) {
     size_t b = work_bytes(r.m, r.n, h->opt.x_dtype, tile_rows, nullptr);
-    const size_t need_align = r.c_dtype == PDOT_BF16 ? 8 : 16;
-    if (((uintptr_t)r.C % need_align) != 0 || r.ldc % 4 != 0)
-        b += align_up((size_t)r.m * ((r.n + 3) / 4 * 4) * csize_of(r.c_dtype), 256);
+    if (!c_layout_ok(r.C, r.c_dtype, r.ldc))
+        b += align_up((size_t)r.m * padded_ldc(r.n, r.c_dtype) * csize_of(r.c_dtype), 256);
     return b;
 }
 
@@ -819,7 +831,7 @@ void batch_compose(pdot_handle* h) {
         const void* Cd = s->req.C;
         if (s->w.Cpad) {
             Cd = s->w.Cpad;
-            ldc = (s->req.n + 3) / 4 * 4;
+            ldc = padded_ldc(s->req.n, s->req.c_dtype);
         }
         B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
         const int tt = s->ttype;
@@ -1020,7 +1032,7 @@ bool batch_admit(pdot_handle* h) {
         s->w.bytes = wb;
         work_bytes(r.m, r.n, h->opt.x_dtype, tr, &s->w);
         if (s->bytes > wb) {
-            const long long ldp = (r.n + 3) / 4 * 4;
+            const long long ldp = padded_ldc(r.n, r.c_dtype);
             const size_t cs = csize_of(r.c_dtype);
             s->w.Cpad = (char*)base + wb;
             CK(cudaMemcpy2DAsync(s->w.Cpad, ldp * cs, r.C, (size_t)r.ldc * cs, (size_t)r.n * cs, (size_t)r.m,
@@ -1190,6 +1202,14 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         h->cfg.pass_u = 2;
         const char* pu = getenv("PDOT_PASS_U");
         if (pu && atoi(pu) == 4) h->cfg.pass_u = 4;
+        const int bulk = setup_bulk_pass();
+        if (bulk > 0) throw CudaError{(cudaError_t)bulk};
+        h->cfg.bulk_blocks = h->sm_count * (-bulk);
+        h->cfg.pass_bulk = 1;
+        const char* pb = getenv("PDOT_PASS_BULK");
+        if (pb && atoi(pb) == 0) h->cfg.pass_bulk = 0;
+        const char* pp = getenv("PDOT_PDL");
+        h->cfg.pdl = (pp && atoi(pp) == 1) ? 1 : 0;
         h->cfg_base = h->cfg;
         CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
         CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));
@@ -1250,7 +1270,7 @@ pdot_status pdot_solve_host(pdot_handle* h, int64_t m, int64_t n, const void* C,
         if (m < 1 || n < 1 || ldc < n || !C || !f || !g) throw ArgError{"bad arguments"};
         const size_t cs = csize_of(c_dtype);
         const size_t xs = xsize_of(h->opt.x_dtype);
-        const long long ldp = (n + 3) / 4 * 4;
+        const long long ldp = padded_ldc(n, c_dtype);
         const size_t bC = align_up((size_t)m * ldp * cs, 256);
         const size_t bf = align_up(sizeof(double) * (size_t)m, 256), bg = align_up(sizeof(double) * (size_t)n, 256);
         const size_t bX = X_out ? align_up((size_t)m * n * xs, 256) : 0;

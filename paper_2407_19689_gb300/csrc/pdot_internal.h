@@ -32,7 +32,8 @@ constexpr int MODE_CHECK = 0;
 constexpr int MODE_INIT = 1;
 
 // Status codes (same values as pdot_status in include/pdot.h).
-constexpr int ST_OK = 0, ST_ARG = 1, ST_NUMERIC = 4, ST_MAX_ITER = 5, ST_TIMEOUT = 6, ST_CANCELLED = 9;
+constexpr int ST_OK = 0, ST_ARG = 1, ST_DEVICE = 3, ST_NUMERIC = 4, ST_MAX_ITER = 5, ST_TIMEOUT = 6,
+              ST_CANCELLED = 9;
 
 struct Ctrl {
     // iteration state
@@ -99,7 +100,10 @@ struct LaunchCfg {
     int tile_blocks;      // CTAs of the FP32-plan tile kernels (8 warps each)
     int tile_blocks_f64;  // CTAs of the FP64-plan tile kernels
     int vec_blocks;       // CTAs of the vector kernels (256 threads each)
-    int pass_u;           // rows per load batch in the FP32-plan pass (2 or 4)
+    int pass_u;           // rows per load batch in the FP32-plan register pass (2 or 4)
+    int pass_bulk;        // 1: FP32-plan passes use the bulk-copy pipeline kernel
+    int bulk_blocks;      // CTAs of the bulk-copy pass kernel
+    int pdl;              // 1: launch with programmatic dependent launch
 };
 
 // Tile and vector-tile counts are read from device memory, so one captured
@@ -117,5 +121,8 @@ int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const 
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream);
 int occupancy_tile_blocks_per_sm(int ttype);
 int occupancy_vec_blocks_per_sm();
+// Opt the bulk-copy pass kernel into its shared-memory size; returns minus
+// the CTAs per SM it can hold, or a positive cudaError_t code.
+int setup_bulk_pass();
 
 }  // namespace pdot

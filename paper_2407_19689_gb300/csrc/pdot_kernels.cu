@@ -137,6 +137,15 @@ __device__ __forceinline__ int warp_next(unsigned* ctr) {
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
+// Programmatic dependent launch: wait for the previous grid in the stream
+// (completion and memory visibility; a no-op without the launch attribute),
+// then let the next grid start launching its CTAs.  Every solve-loop kernel
+// calls this before touching any data or work counter.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int c = 0; c < WC_N; ++c)
@@ -256,6 +265,7 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
 template <typename TC, typename TX, int U>
 __global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
 k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
+    pdl_enter();
     const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
@@ -267,6 +277,294 @@ k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const i
         const Ctrl& S = *I.ctrl;
         if (S.status != ST_RUNNING) continue;
         pass_tile<TC, TX, U>(I, S, tr.local, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plan pass, bulk-copy pipeline (FP32 plans): the same arithmetic as
+// pass_tile, but every warp streams its rows through a ring of S shared-memory
+// stages filled by the bulk-copy engine (cp.async.bulk, completion counted on
+// one mbarrier per stage).  Rows in flight cost no registers, so each SM keeps
+// ~S x 1.5 KB per warp of reads outstanding.  The warp's row stream runs
+// across tile boundaries: the producer (lane 0) fetches the next tile from the
+// queue as soon as it has issued the current one's last row.
+// ---------------------------------------------------------------------------
+namespace bulk {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Bounded wait: a copy that never lands must not hang the GPU.
+constexpr long long WAIT_LIMIT = 1LL << 24;
+__device__ __forceinline__ bool wait_stage(unsigned bar, unsigned parity) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr int STAGE_BYTES = 3 * STRIP * 4;   // C (<= 512 B), X (512 B), Xbar (512 B)
+
+constexpr int MAX_TILE_ROWS = 256;
+template <int S>
+__host__ __device__ constexpr int warp_smem_bytes() { return S * STAGE_BYTES + S * 8 + S * 8 + MAX_TILE_ROWS * 4; }
+
+struct RowRef {       // what a stage holds
+    int tile;         // global tile index (into tmap), -1 = none
+    int row;          // matrix row
+};
+
+}  // namespace bulk
+
+template <typename TC, int S>
+__global__ void __launch_bounds__(TWARPS * 32)
+k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
+            unsigned* wctr, int wc) {
+    using namespace bulk;
+    pdl_enter();
+    const int T = *Tp;
+    reset_other_counters(wctr, wc);
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wbase = dsm + warp * warp_smem_bytes<S>();
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + S * STAGE_BYTES);
+    RowRef* refs = reinterpret_cast<RowRef*>(wbase + S * STAGE_BYTES + S * 8);
+    float* pbuf = reinterpret_cast<float*>(wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // ---- producer state (identical in every lane; lane 0 issues) ----
+    int p_tile = warp_next(&wctr[wc]);
+    long long p_row = 0, p_end = 0;
+    auto open_tile = [&](int t, long long& r0, long long& r1) {
+        const TileRef tr = tmap[t];
+        const Inst& I = insts[tr.inst];
+        const int chunk = tr.local / I.nstrips;
+        r0 = (long long)chunk * I.tile_rows;
+        r1 = min(r0 + (long long)I.tile_rows, I.m);
+    };
+    // Skip tiles of instances that are not running.
+    auto usable = [&](int t) -> bool {
+        const TileRef tr = tmap[t];
+        return insts[tr.inst].ctrl->status == ST_RUNNING;
+    };
+    while (p_tile < T && !usable(p_tile)) p_tile = warp_next(&wctr[wc]);
+    if (p_tile < T) open_tile(p_tile, p_row, p_end);
+
+    long long issued = 0, consumed = 0;
+    bool failed = false;
+    auto issue = [&]() {
+        // Issue the producer's next row into stage issued % S, then advance.
+        const int st = (int)(issued % S);
+        const TileRef tr = tmap[p_tile];
+        const Inst& I = insts[tr.inst];
+        const Ctrl& Sc = *I.ctrl;
+        const int strip = tr.local % I.nstrips;
+        const long long c0 = (long long)strip * STRIP;
+        const long long ncols = min((long long)STRIP, I.n - c0);
+        const unsigned xbytes = (unsigned)(((ncols + 3) / 4) * 4 * 4);
+        // C by the bulk engine unless the rounded-up copy could run past the
+        // caller's allocation (last row of a ragged strip): lanes load it then.
+        const long long cq = sizeof(TC) == 2 ? 8 : 4;
+        const bool c_bulk = !(p_row == I.m - 1 && (ncols % cq) != 0);
+        const unsigned cbytes = c_bulk ? (unsigned)(((ncols + cq - 1) / cq) * cq * sizeof(TC)) : 0u;
+        const bool first = Sc.k == 0;
+        if (lane == 0) {
+            refs[st].tile = p_tile;
+            refs[st].row = (int)p_row;
+            const unsigned bar = smem_u32(&bars[st]);
+            const unsigned dst = smem_u32(wbase + st * STAGE_BYTES);
+            fence_proxy_async();
+            mbar_expect_tx(bar, cbytes + xbytes + (first ? 0u : xbytes));
+            if (cbytes) g2s(dst, reinterpret_cast<const TC*>(I.C) + p_row * I.ldc + c0, cbytes, bar);
+            const float* X = reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot;
+            g2s(dst + STRIP * 4, X + p_row * I.ldx + c0, xbytes, bar);
+            if (!first) {
+                const float* Xb = reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot;
+                g2s(dst + 2 * STRIP * 4, Xb + p_row * I.ldx + c0, xbytes, bar);
+            }
+        }
+        ++issued;
+        if (++p_row >= p_end) {
+            p_tile = warp_next(&wctr[wc]);
+            while (p_tile < T && !usable(p_tile)) p_tile = warp_next(&wctr[wc]);
+            if (p_tile < T) open_tile(p_tile, p_row, p_end);
+        }
+    };
+    while (issued < S && p_tile < T) issue();
+
+    // ---- consumer state (per tile) ----
+    int c_tile = -1;
+    const Inst* CI = nullptr;
+    const Ctrl* CS = nullptr;
+    int c_strip = 0, c_chunk = 0;
+    long long j0 = 0;
+    bool on = false, valid[4] = {false, false, false, false};
+    float qv[4] = {0.f, 0.f, 0.f, 0.f};
+    float tau = 0.f, w = 0.f;
+    bool first = true;
+    double cs[4] = {0.0, 0.0, 0.0, 0.0}, dx2 = 0.0;
+    float csa[4] = {0.f, 0.f, 0.f, 0.f}, dxa = 0.f;
+    int rows_in_batch = 0;
+    auto flush_tile = [&]() {
+        if (c_tile < 0) return;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
+        dx2 += (double)dxa;
+        const TileRef tr = tmap[c_tile];
+        if (on) {
+            double* cp = CI->colpart + (long long)c_chunk * CI->ldx + j0;
+            reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
+            reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
+        }
+        const double d = warp_sum(dx2);
+        if (lane == 0) CI->tpart[(long long)tr.local * TP + 0] = d;
+    };
+
+    while (consumed < issued) {
+        const int st = (int)(consumed % S);
+        const unsigned parity = (unsigned)((consumed / S) & 1);
+        if (!wait_stage(smem_u32(&bars[st]), parity)) { failed = true; break; }
+        const RowRef ref = refs[st];
+        if (ref.tile != c_tile) {
+            flush_tile();
+            c_tile = ref.tile;
+            const TileRef tr = tmap[c_tile];
+            CI = &insts[tr.inst];
+            CS = CI->ctrl;
+            c_strip = tr.local % CI->nstrips;
+            c_chunk = tr.local / CI->nstrips;
+            j0 = (long long)c_strip * STRIP + lane * 4;
+            on = j0 < CI->n;
+            const double* q = slot_v(*CI, CS->cur) + CI->m;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                valid[e] = j0 + e < CI->n;
+                qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+            }
+            tau = (float)CS->tau;
+            w = (float)(1.0 / (double)(CS->k + 1));
+            first = CS->k == 0;
+            {
+                // Stage the tile's row duals once instead of one dependent load per row.
+                const double* p = slot_v(*CI, CS->cur);
+                const long long r0 = (long long)c_chunk * CI->tile_rows;
+                const long long r1 = min(r0 + (long long)CI->tile_rows, CI->m);
+                __syncwarp();
+                for (long long r = r0 + lane; r < r1; r += 32) pbuf[r - r0] = (float)p[r];
+                __syncwarp();
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { cs[e] = 0.0; csa[e] = 0.f; }
+            dx2 = 0.0;
+            dxa = 0.f;
+            rows_in_batch = 0;
+        }
+        const long long i = ref.row;
+        const unsigned char* stage = wbase + st * STAGE_BYTES;
+        float c[4], x[4], xb[4];
+        const long long c0 = (long long)c_strip * STRIP;
+        const long long ncols = min((long long)STRIP, CI->n - c0);
+        const long long cq = sizeof(TC) == 2 ? 8 : 4;
+        const bool c_bulk = !(i == CI->m - 1 && (ncols % cq) != 0);
+        if (on) {
+            if (c_bulk) {
+                if (sizeof(TC) == 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(stage + lane * 16);
+                    c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
+                } else {
+                    const uint2 t = *reinterpret_cast<const uint2*>(stage + lane * 8);
+                    c[0] = bf16_bits_to_f32(t.x & 0xffffu);
+                    c[1] = bf16_bits_to_f32(t.x >> 16);
+                    c[2] = bf16_bits_to_f32(t.y & 0xffffu);
+                    c[3] = bf16_bits_to_f32(t.y >> 16);
+                }
+            } else {
+                ldc4_tail<float>(reinterpret_cast<const TC*>(CI->C) + i * CI->ldc + j0, CI->n - j0, c);
+            }
+            const float4 tx = *reinterpret_cast<const float4*>(stage + STRIP * 4 + lane * 16);
+            x[0] = tx.x; x[1] = tx.y; x[2] = tx.z; x[3] = tx.w;
+            if (!first) {
+                const float4 tb = *reinterpret_cast<const float4*>(stage + 2 * STRIP * 4 + lane * 16);
+                xb[0] = tb.x; xb[1] = tb.y; xb[2] = tb.z; xb[3] = tb.w;
+            } else {
+                xb[0] = xb[1] = xb[2] = xb[3] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; }
+        }
+        // The stage has been read: release it to the producer.
+        __syncwarp();
+        ++consumed;
+        if (p_tile < T) issue();
+
+        const float pv = pbuf[i - (long long)c_chunk * CI->tile_rows];
+        float xn[4], xbn[4], rs = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float R = (c[e] - pv) - qv[e];
+            float v = x[e] - tau * R;
+            v = v > 0.f ? v : 0.f;
+            v = valid[e] ? v : 0.f;
+            const float d = v - x[e];
+            dxa += d * d;
+            rs += v;
+            csa[e] += v;
+            xn[e] = v;
+            xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
+        }
+        if (on) {
+            float* Xn = reinterpret_cast<float*>(CI->X) + (long long)CS->nxt * CI->xslot + i * CI->ldx + j0;
+            float* Xbn = reinterpret_cast<float*>(CI->X) + (long long)CS->barn * CI->xslot + i * CI->ldx + j0;
+            st4(Xn, xn);
+            st4(Xbn, xbn);
+        }
+        rs = warp_sum(rs);
+        if (lane == 0) CI->rowpart[(long long)c_strip * CI->m + i] = (double)rs;
+        if (++rows_in_batch == 8) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
+            dx2 += (double)dxa;
+            dxa = 0.f;
+            rows_in_batch = 0;
+        }
+    }
+    if (!failed) {
+        flush_tile();
+    } else if (lane == 0) {
+        // A stage never completed: report it and stop (bounded, never a trap).
+        Ctrl* Sw = const_cast<Ctrl*>(CS ? CS : insts[tmap[refs[(int)(consumed % S)].tile].inst].ctrl);
+        atomicExch(&Sw->status, ST_DEVICE);
+    }
+    // Drain: wait (bounded) for every copy still in flight before exiting.
+    while (consumed < issued) {
+        const int st = (int)(consumed % S);
+        wait_stage(smem_u32(&bars[st]), (unsigned)((consumed / S) & 1));
+        ++consumed;
     }
 }
 
@@ -409,12 +707,13 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* 
 
 __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                              const int* __restrict__ NVp, unsigned* wctr) {
-    const int NV = *NVp;
     __shared__ double red[(VT / 32) * 3];
     __shared__ double sgrp[VG * 32];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_DUAL, 0);
+    pdl_enter();
     reset_other_counters(wctr, wc);
+    const int NV = *NVp;
     for (;;) {
         if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
         __syncthreads();
@@ -541,6 +840,7 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
 template <typename TC, typename TX>
 __global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
 k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc, int mode) {
+    pdl_enter();
     const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
@@ -768,12 +1068,13 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
 
 __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                                  const int* __restrict__ NVp, unsigned* wctr, int mode) {
-    const int NV = *NVp;
     __shared__ double red[(VT / 32) * VP];
     __shared__ double sgrp[VG * 32];
     __shared__ int s_t, s_last;
     const int wc = wc_index(WC_CHECK, 0);
+    pdl_enter();
     reset_other_counters(wctr, wc);
+    const int NV = *NVp;
     for (;;) {
         if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
         __syncthreads();
@@ -815,6 +1116,7 @@ __device__ __forceinline__ void sumsq_tile(const Inst& I, int lt, int lane) {
 template <typename TC>
 __global__ void __launch_bounds__(TWARPS * 32)
 k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
+    pdl_enter();
     const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
@@ -830,6 +1132,7 @@ k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, cons
 // Snapshot of every resident instance's controller (one D2H copy per chunk)
 // ---------------------------------------------------------------------------
 __global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict__ count, Ctrl* out) {
+    pdl_enter();
     const int n = *count;
     const int words = (int)(sizeof(Ctrl) / sizeof(int));
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * words; t += gridDim.x * blockDim.x) {
@@ -843,49 +1146,88 @@ __global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict
 // ---------------------------------------------------------------------------
 static int err(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 
+// Launch with the programmatic-stream-serialization attribute when enabled.
+template <typename... KArgs, typename... Args>
+static int launch_k(bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                    Args... args) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(grid);
+    c.blockDim = dim3(block);
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        c.attrs = attr;
+        c.numAttrs = 1;
+    }
+    return err(cudaLaunchKernelEx(&c, kern, args...));
+}
+
+constexpr int BULK_S = 8;
+constexpr int bulk_smem() { return TWARPS * bulk::warp_smem_bytes<BULK_S>(); }
+
 int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream, int wc_override) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
-    if (ttype == TT_F64) k_pass<double, double, 2><<<cfg.tile_blocks_f64, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-    else if (ttype == TT_BF16) {
-        if (cfg.pass_u == 4) k_pass<unsigned short, float, 4><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-        else k_pass<unsigned short, float, 2><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-    } else {
-        if (cfg.pass_u == 4) k_pass<float, float, 4><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-        else k_pass<float, float, 2><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
+    const bool pdl = cfg.pdl != 0;
+    const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
+    if (cfg.pass_bulk && ttype != TT_F64) {
+        if (ttype == TT_BF16)
+            return launch_k(pdl, k_pass_bulk<unsigned short, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc);
+        return launch_k(pdl, k_pass_bulk<float, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                        d_tmap, T, wctr, wc);
     }
-    return err(cudaGetLastError());
+    if (ttype == TT_F64)
+        return launch_k(pdl, k_pass<double, double, 2>, (unsigned)cfg.tile_blocks_f64, th, 0, st, d_insts, d_tmap, T,
+                        wctr, wc);
+    if (ttype == TT_BF16) {
+        if (cfg.pass_u == 4)
+            return launch_k(pdl, k_pass<unsigned short, float, 4>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+        return launch_k(pdl, k_pass<unsigned short, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    }
+    if (cfg.pass_u == 4) return launch_k(pdl, k_pass<float, float, 4>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    return launch_k(pdl, k_pass<float, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
 }
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream) {
-    const int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
-    k_dual<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr);
-    return err(cudaGetLastError());
+    int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
+    if (blocks < 1) blocks = 1;
+    return launch_k(cfg.pdl != 0, k_dual, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV, wctr);
 }
 int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,
                const LaunchCfg& cfg, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_index(WC_KKT, ttype);
-    if (ttype == TT_F64) k_kkt<double, double><<<cfg.tile_blocks_f64, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
-    else if (ttype == TT_BF16) k_kkt<unsigned short, float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
-    else k_kkt<float, float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc, mode);
-    return err(cudaGetLastError());
+    const bool pdl = cfg.pdl != 0;
+    const unsigned th = TWARPS * 32;
+    if (ttype == TT_F64)
+        return launch_k(pdl, k_kkt<double, double>, (unsigned)cfg.tile_blocks_f64, th, 0, st, d_insts, d_tmap, T, wctr,
+                        wc, mode);
+    if (ttype == TT_BF16)
+        return launch_k(pdl, k_kkt<unsigned short, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T,
+                        wctr, wc, mode);
+    return launch_k(pdl, k_kkt<float, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T, wctr, wc,
+                    mode);
 }
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream) {
-    const int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
-    k_checkvec<<<blocks > 0 ? blocks : 1, VT, 0, (cudaStream_t)stream>>>(d_insts, d_vmap, NV, wctr, mode);
-    return err(cudaGetLastError());
+    int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
+    if (blocks < 1) blocks = 1;
+    return launch_k(cfg.pdl != 0, k_checkvec, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV,
+                    wctr, mode);
 }
 int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
                    const LaunchCfg& cfg, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_index(WC_AUX, ctype == 2 ? TT_F64 : (ctype == 1 ? TT_BF16 : TT_F32));
-    if (ctype == 2) k_sumsq_C<double><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-    else if (ctype == 1) k_sumsq_C<unsigned short><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-    else k_sumsq_C<float><<<cfg.tile_blocks, TWARPS * 32, 0, st>>>(d_insts, d_tmap, T, wctr, wc);
-    return err(cudaGetLastError());
+    const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
+    if (ctype == 2) return launch_k(false, k_sumsq_C<double>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    if (ctype == 1) return launch_k(false, k_sumsq_C<unsigned short>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    return launch_k(false, k_sumsq_C<float>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
 }
 
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream) {
@@ -918,6 +1260,19 @@ int occupancy_tile_blocks_per_sm(int ttype) {
     if (d < r) r = d;
     return r;
 }
+int setup_bulk_pass() {
+    const int bytes = bulk_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_pass_bulk<float, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_pass_bulk<unsigned short, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_bulk<float, BULK_S>, TWARPS * 32, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_bulk<unsigned short, BULK_S>, TWARPS * 32, bytes);
+    const int r = a < b ? a : b;
+    return -(r > 0 ? r : 1);   // negative: blocks per SM
+}
+
 int occupancy_vec_blocks_per_sm() {
     const int a = occ((const void*)k_dual, VT);
     const int b = occ((const void*)k_checkvec, VT);

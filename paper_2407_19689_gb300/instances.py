@@ -164,3 +164,30 @@ def serve_requests(count: int, rate_per_s: float, seed: int, lo: int = 128, hi: 
 def request_instance(r: Request) -> Instance:
     return points_instance(r.m, r.n, r.seed, d=r.d, cost=r.cost, marginals="dirichlet",
                            alpha=r.alpha, scale_to_unit=True)
+
+
+def device_cost_from_points(xs, ys, kind: str = "sqeuclid", scale_to_unit: bool = False, dtype=None):
+    """Cost matrix between two point clouds built on the GPU with torch ops
+    (input generation for the served workload; FP64, cast at the end)."""
+    import torch
+    x = torch.as_tensor(xs, dtype=torch.float64)
+    y = torch.as_tensor(ys, dtype=torch.float64)
+    if kind == "sqeuclid":
+        C = torch.cdist(x, y, p=2.0) ** 2
+    elif kind == "l1":
+        C = torch.cdist(x, y, p=1.0)
+    else:
+        raise ValueError(kind)
+    if scale_to_unit:
+        C = C / C.max()
+    return C.to(dtype) if dtype is not None else C
+
+
+def request_points(r: "Request"):
+    """Points and marginals of a served request (same draws as request_instance)."""
+    rng = np.random.default_rng(r.seed)
+    xs = rng.random((r.m, r.d))
+    ys = rng.random((r.n, r.d))
+    f = _normalise(rng.dirichlet(np.full(r.m, r.alpha)))
+    g = _normalise(rng.dirichlet(np.full(r.n, r.alpha)))
+    return xs, ys, f, g

@@ -78,6 +78,24 @@ def test_pdhg_steps_fp32(s32, m, n, k):
             assert e < 1e-5, (name, start, e)
 
 
+@pytest.mark.parametrize("m,n", [(300, 517), (129, 3), (77, 130)])
+def test_pdhg_steps_register_path(m, n, monkeypatch):
+    """The register-pipelined pass kernel (selected with PDOT_PASS_BULK=0 when a
+    handle is created) against the oracle, FP32 and BF16 costs."""
+    monkeypatch.setenv("PDOT_PASS_BULK", "0")
+    s = pdot.Solver(device=0)
+    ins = I.points_instance(m, n, 1500 + m)
+    eta = 0.5 / math.sqrt(m + n)
+    z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
+    for dt in (torch.float32, torch.bfloat16):
+        C = torch.tensor(ins.C, dtype=dt, device=DEV)
+        g = s.pdhg_steps(C, ins.f, ins.g, *z, k=25, eta=eta)
+        o = oracle.pdhg_steps(_np(C), ins.f, ins.g, *z, k=25, eta=eta)
+        for a, b in zip(g, o):
+            assert rel(_np(a), b) < 1e-5
+    s.close()
+
+
 @pytest.mark.parametrize("m,n", [(300, 517), (77, 130)])
 def test_pdhg_steps_bf16_cost(s32, m, n):
     """BF16 costs: the oracle solves the same BF16-rounded C in FP64 (reading C16)."""
