@@ -207,6 +207,30 @@ pdot_status pdot_cancel(pdot_handle *h, uint64_t ticket);
 /* Counts of queued (not yet admitted) and resident instances. */
 pdot_status pdot_batch_pending(pdot_handle *h, int *queued, int *running);
 
+/*
+ * Allocation-free Algorithm 3 rounding, for callers that cannot allocate
+ * device memory when they need it (memory owned by another allocator, a
+ * serving loop that forbids cudaMalloc/cudaFree after warm-up because they
+ * synchronise the device, a plug-in inside an application that owns all
+ * allocations).  Same result as pdot_round, but no handle and no allocation:
+ * the scratch is a 3.7 MB array in the library's device image, held by every
+ * GPU that loads the library until the process exits.  This entry point has
+ * no counterpart in the paper.
+ *   device: CUDA device to run on (made current); cuda_stream: stream to use
+ *   (NULL = legacy default stream); X (m x n, x_dtype), f (m), g (n): device
+ *   inputs; X_out: device output (may alias X).  Returns after the stream
+ *   synchronises.
+ *   Limits: 1 <= m, n <= 32768 and x_dtype F32 or F64, else PDOT_ERR_ARG.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls share the one array; calls that overlap on the GPU (other
+ *   streams or host threads) race and must be serialised by the caller.  Each
+ *   call writes every scratch word before reading it, so nothing carries over
+ *   from the previous call.
+ */
+pdot_status pdot_round_noalloc(int device, void *cuda_stream, int64_t m, int64_t n, pdot_dtype x_dtype,
+                               const void *X, const double *f, const double *g, void *X_out);
+
 /* Kernel launches issued by this handle since creation (diagnostics). */
 int64_t pdot_launch_count(pdot_handle *h);
 

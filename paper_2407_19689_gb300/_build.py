@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpdot.so")
-SOURCES = ["pdot_kernels.cu", "pdot_round.cu", "pdot_engine.cu"]
+SOURCES = ["pdot_kernels.cu", "pdot_round.cu", "pdot_engine.cu", "pdot_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "pdot_internal.h"), os.path.join(INCLUDE, "pdot.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]

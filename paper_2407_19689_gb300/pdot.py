@@ -112,7 +112,7 @@ class Request(ctypes.Structure):
 DECLARED = [
     "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
     "pdot_solve_host", "pdot_pdhg_steps", "pdot_kkt", "pdot_round", "pdot_batch_submit", "pdot_poll",
-    "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass",
+    "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass", "pdot_round_noalloc",
 ]
 
 _LIB = None
@@ -150,6 +150,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_launch_count": (i64, [H]),
         "pdot_time_pass": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i32, ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl)]),
+        "pdot_round_noalloc": (i32, [i32, vp, i64, i64, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -248,6 +249,12 @@ def pdot_batch_pending(h):
 
 def pdot_launch_count(h) -> int:
     return load().pdot_launch_count(h)
+
+
+def pdot_round_noalloc(device, stream, m, n, x_dtype, X, f, g, X_out) -> int:
+    """Algorithm 3 without a handle or any allocation (scratch lives in the
+    library's static device array); see include/pdot.h for the limits."""
+    return load().pdot_round_noalloc(device, stream or None, m, n, x_dtype, X, f, g, X_out)
 
 
 def pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps):
