@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: 0.8 x measured capacity)")
     ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
+    ap.add_argument("--pass-sweep", action="store_true",
+                    help="time the fused pass kernel alone over kernels x tile heights x sizes (tuning table)")
     return ap.parse_args()
 
 
@@ -421,8 +423,44 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_pass_sweep(args):
+    import torch
+
+    from paper_2407_19689_gb300 import _build, pdot
+    from paper_2407_19689_gb300 import instances as I
+    _build.build()
+    pdot.load()
+    peak, _ = measured_peak()
+    out = []
+    for G in (64, 128):
+        ins = I.grid_blob_instance(G, I.seed_for(1), build_cost=False)
+        P = torch.tensor(I.grid_coords(G), device="cuda:0")
+        C = torch.cdist(P, P) ** 2
+        C = (C / C.max()).float()
+        f = torch.tensor(ins.f, device="cuda:0")
+        g = torch.tensor(ins.g, device="cuda:0")
+        m = n = G * G
+        for bulk in ("1", "0"):
+            os.environ["PDOT_PASS_BULK"] = bulk
+            for tr in (0, 16, 32, 64, 128, 256, 512):
+                s = pdot.Solver(device=0, tile_rows=tr)
+                st, ms, b = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
+                                                30 if G == 64 else 10)
+                s.close()
+                row = {"m": m, "kernel": "bulk" if bulk == "1" else "register", "tile_rows": tr or "auto",
+                       "us": ms * 1e3, "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
+                out.append(row)
+                print(json.dumps(row), flush=True)
+        del C
+        torch.cuda.empty_cache()
+    os.environ.pop("PDOT_PASS_BULK", None)
+
+
 def main():
     args = parse()
+    if args.pass_sweep:
+        run_pass_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

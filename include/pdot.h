@@ -79,7 +79,7 @@ typedef struct {
     pdot_dtype x_dtype;            /* plan precision: PDOT_F32 (default) or PDOT_F64 */
     int32_t round_plan;            /* 1: return the Algorithm 3 rounding of the plan */
     int32_t use_graph;             /* 1: capture K-pass chunks as CUDA graphs (default) */
-    int32_t tile_rows;             /* rows per plan tile (16..256, multiple of 8); 0: autotune */
+    int32_t tile_rows;             /* rows per plan tile (even, 2..4096); 0: pick by shape */
     uint64_t hbm_budget_bytes;     /* batch admission budget; 0: 90% of free memory at create */
     int32_t max_batch_slots;       /* most instances resident at once in the batch engine */
     int32_t chunk_checks;          /* check periods per batch chunk launch (serving granularity) */

@@ -278,21 +278,26 @@ void validate_marginals(pdot_handle* h, long long m, long long n, const double* 
     *norm_b = std::sqrt(nb);
 }
 
-int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype) {
+int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool batch = false) {
     if (h->opt.tile_rows > 0) return h->opt.tile_rows;
-    const long long key = (m * 1000003LL + n) * 4 + ttype;
-    auto it = h->tune_cache.find(key);
-    if (it != h->tune_cache.end()) return it->second;
-    // Enough warp tiles to keep every resident warp busy several times over,
-    // with the tallest tile (fewest column partials) that achieves it.
-    const long long warps = (long long)(ttype == TT_F64 ? h->cfg.tile_blocks_f64 : h->cfg.tile_blocks) * TWARPS;
     const long long nstrips = (n + STRIP - 1) / STRIP;
-    int tr = 16;
-    for (int cand : {128, 64, 32, 16}) {
-        const long long tiles = nstrips * ((m + cand - 1) / cand);
-        if (tiles >= 4 * warps) { tr = cand; break; }
+    if (batch) {
+        // Many instances share the tile queue: moderate tiles keep it balanced.
+        return 64;
     }
-    return tr;
+    // One instance: split it evenly over the resident warps, one tile each
+    // (the last wave of a dynamic queue would otherwise leave a tail), with
+    // tiles as tall as that allows (fewer column partials).
+    const long long warps = (long long)(ttype == TT_F64 ? h->cfg.tile_blocks_f64
+                                                        : (h->cfg.pass_bulk ? h->cfg.bulk_blocks : h->cfg.tile_blocks)) *
+                            TWARPS;
+    long long nch = warps / nstrips;
+    if (nch < 1) nch = 1;
+    long long tr = (m + nch - 1) / nch;
+    tr = (tr + 1) / 2 * 2;
+    if (tr < 2) tr = 2;
+    if (tr > 4096) tr = 4096;
+    return (int)tr;
 }
 
 const void* prepare_C(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
@@ -1024,7 +1029,7 @@ bool batch_admit(pdot_handle* h) {
         if (B->used + s->bytes > B->budget) break;   // FIFO: wait for memory to free up
         B->queue.pop_front();
         const pdot_request& r = s->req;
-        const int tr = pick_tile_rows(h, r.m, r.n, s->ttype);
+        const int tr = pick_tile_rows(h, r.m, r.n, s->ttype, true);
         const size_t wb = work_bytes(r.m, r.n, h->opt.x_dtype, tr, nullptr);
         void* base = nullptr;
         CK(cudaMallocAsync(&base, s->bytes, h->stream));
@@ -1180,8 +1185,8 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
     else pdot_default_options(&h->opt);
     pdot_status st = guarded(h, [&]() -> pdot_status {
         if (h->opt.restart_check_every < 1) throw ArgError{"restart_check_every < 1"};
-        if (h->opt.tile_rows < 0 || h->opt.tile_rows > 256 || h->opt.tile_rows % 8 != 0) {
-            throw ArgError{"tile_rows must be 0 or a multiple of 8 in [8, 256]"};
+        if (h->opt.tile_rows < 0 || h->opt.tile_rows > 4096 || h->opt.tile_rows % 2 != 0) {
+            throw ArgError{"tile_rows must be 0 or an even number in [2, 4096]"};
         }
         int ndev = 0;
         CK(cudaGetDeviceCount(&ndev));
@@ -1409,7 +1414,7 @@ pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int coun
                 slots.push_back(s);
                 s->req = r;
                 s->ttype = ttype_of(r.c_dtype);
-                s->bytes = slot_bytes(h, r, pick_tile_rows(h, r.m, r.n, s->ttype));
+                s->bytes = slot_bytes(h, r, pick_tile_rows(h, r.m, r.n, s->ttype, true));
                 if (s->bytes > B->budget) {
                     for (BSlot* x : slots) delete x;
                     h->last_error = "request exceeds the HBM budget";

@@ -350,77 +350,85 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + S * STAGE_BYTES);
     RowRef* refs = reinterpret_cast<RowRef*>(wbase + S * STAGE_BYTES + S * 8);
     float* pbuf = reinterpret_cast<float*>(wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
+    const unsigned wbase_s = smem_u32(wbase);
+    const unsigned bars_s = smem_u32(bars);
     if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < S; ++s) mbar_init(bars_s + 8 * s, 1);
         fence_mbar_init();
     }
     __syncwarp();
+    constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
 
-    // ---- producer state (identical in every lane; lane 0 issues) ----
-    int p_tile = warp_next(&wctr[wc]);
-    long long p_row = 0, p_end = 0;
-    auto open_tile = [&](int t, long long& r0, long long& r1) {
-        const TileRef tr = tmap[t];
-        const Inst& I = insts[tr.inst];
-        const int chunk = tr.local / I.nstrips;
-        r0 = (long long)chunk * I.tile_rows;
-        r1 = min(r0 + (long long)I.tile_rows, I.m);
+    // ---- producer: the tile being issued, resolved once per tile ----
+    int p_tile = T;
+    long long p_row = 0, p_end = 0, p_last_ragged = -1;
+    const char* p_c = nullptr;          // C row p_row, column c0
+    const char* p_x = nullptr;          // X row p_row
+    const char* p_xb = nullptr;         // Xbar row p_row
+    long long p_cstride = 0, p_xstride = 0;
+    unsigned p_cbytes = 0, p_xbytes = 0;
+    bool p_first = true;
+    auto next_tile = [&]() {
+        for (;;) {
+            p_tile = warp_next(&wctr[wc]);
+            if (p_tile >= T) return;
+            const TileRef tr = tmap[p_tile];
+            const Inst& I = insts[tr.inst];
+            const Ctrl& Sc = *I.ctrl;
+            if (Sc.status != ST_RUNNING) continue;
+            const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
+            const long long c0 = (long long)strip * STRIP;
+            const long long ncols = min((long long)STRIP, I.n - c0);
+            p_row = (long long)chunk * I.tile_rows;
+            p_end = min(p_row + (long long)I.tile_rows, I.m);
+            p_cstride = I.ldc * (long long)sizeof(TC);
+            p_xstride = I.ldx * 4;
+            p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
+                                                p_row * I.ldx + c0);
+            p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
+                                                 p_row * I.ldx + c0);
+            p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
+            p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
+            // The rounded-up C copy could run past the caller's allocation on
+            // the last matrix row of a ragged strip: lanes load that row.
+            p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            p_first = Sc.k == 0;
+            return;
+        }
     };
-    // Skip tiles of instances that are not running.
-    auto usable = [&](int t) -> bool {
-        const TileRef tr = tmap[t];
-        return insts[tr.inst].ctrl->status == ST_RUNNING;
-    };
-    while (p_tile < T && !usable(p_tile)) p_tile = warp_next(&wctr[wc]);
-    if (p_tile < T) open_tile(p_tile, p_row, p_end);
-
     long long issued = 0, consumed = 0;
-    bool failed = false;
     auto issue = [&]() {
-        // Issue the producer's next row into stage issued % S, then advance.
         const int st = (int)(issued % S);
-        const TileRef tr = tmap[p_tile];
-        const Inst& I = insts[tr.inst];
-        const Ctrl& Sc = *I.ctrl;
-        const int strip = tr.local % I.nstrips;
-        const long long c0 = (long long)strip * STRIP;
-        const long long ncols = min((long long)STRIP, I.n - c0);
-        const unsigned xbytes = (unsigned)(((ncols + 3) / 4) * 4 * 4);
-        // C by the bulk engine unless the rounded-up copy could run past the
-        // caller's allocation (last row of a ragged strip): lanes load it then.
-        const long long cq = sizeof(TC) == 2 ? 8 : 4;
-        const bool c_bulk = !(p_row == I.m - 1 && (ncols % cq) != 0);
-        const unsigned cbytes = c_bulk ? (unsigned)(((ncols + cq - 1) / cq) * cq * sizeof(TC)) : 0u;
-        const bool first = Sc.k == 0;
         if (lane == 0) {
             refs[st].tile = p_tile;
             refs[st].row = (int)p_row;
-            const unsigned bar = smem_u32(&bars[st]);
-            const unsigned dst = smem_u32(wbase + st * STAGE_BYTES);
+            const unsigned bar = bars_s + 8 * st;
+            const unsigned dst = wbase_s + st * STAGE_BYTES;
+            const unsigned cb = p_row == p_last_ragged ? 0u : p_cbytes;
             fence_proxy_async();
-            mbar_expect_tx(bar, cbytes + xbytes + (first ? 0u : xbytes));
-            if (cbytes) g2s(dst, reinterpret_cast<const TC*>(I.C) + p_row * I.ldc + c0, cbytes, bar);
-            const float* X = reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot;
-            g2s(dst + STRIP * 4, X + p_row * I.ldx + c0, xbytes, bar);
-            if (!first) {
-                const float* Xb = reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot;
-                g2s(dst + 2 * STRIP * 4, Xb + p_row * I.ldx + c0, xbytes, bar);
-            }
+            mbar_expect_tx(bar, cb + p_xbytes + (p_first ? 0u : p_xbytes));
+            if (cb) g2s(dst, p_c, cb, bar);
+            g2s(dst + STRIP * 4, p_x, p_xbytes, bar);
+            if (!p_first) g2s(dst + 2 * STRIP * 4, p_xb, p_xbytes, bar);
         }
         ++issued;
-        if (++p_row >= p_end) {
-            p_tile = warp_next(&wctr[wc]);
-            while (p_tile < T && !usable(p_tile)) p_tile = warp_next(&wctr[wc]);
-            if (p_tile < T) open_tile(p_tile, p_row, p_end);
-        }
+        p_c += p_cstride;
+        p_x += p_xstride;
+        p_xb += p_xstride;
+        if (++p_row >= p_end) next_tile();
     };
+    next_tile();
     while (issued < S && p_tile < T) issue();
 
-    // ---- consumer state (per tile) ----
+    // ---- consumer: the tile being computed, resolved once per tile ----
     int c_tile = -1;
     const Inst* CI = nullptr;
-    const Ctrl* CS = nullptr;
-    int c_strip = 0, c_chunk = 0;
+    const TC* c_C = nullptr;
+    long long c_ldc = 0, c_ldx = 0, c_i0 = 0, c_n = 0, c_last_ragged = -1, c_chunk = 0;
+    float* c_xn = nullptr;      // X+ at row c_i0, column j0
+    float* c_xbn = nullptr;     // Xbar+ at row c_i0, column j0
+    double* c_rowpart = nullptr;
     long long j0 = 0;
     bool on = false, valid[4] = {false, false, false, false};
     float qv[4] = {0.f, 0.f, 0.f, 0.f};
@@ -429,69 +437,78 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     double cs[4] = {0.0, 0.0, 0.0, 0.0}, dx2 = 0.0;
     float csa[4] = {0.f, 0.f, 0.f, 0.f}, dxa = 0.f;
     int rows_in_batch = 0;
+    int c_local = 0;
+    const double* c_p = nullptr;   // p of the consumer's instance
+    long long c_i1 = 0, c_win = -1;
     auto flush_tile = [&]() {
         if (c_tile < 0) return;
 #pragma unroll
         for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
         dx2 += (double)dxa;
-        const TileRef tr = tmap[c_tile];
         if (on) {
-            double* cp = CI->colpart + (long long)c_chunk * CI->ldx + j0;
+            double* cp = CI->colpart + c_chunk * CI->ldx + j0;
             reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
             reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
         }
         const double d = warp_sum(dx2);
-        if (lane == 0) CI->tpart[(long long)tr.local * TP + 0] = d;
+        if (lane == 0) CI->tpart[(long long)c_local * TP + 0] = d;
+    };
+    auto open_consumer = [&](int t) {
+        flush_tile();
+        c_tile = t;
+        const TileRef tr = tmap[t];
+        CI = &insts[tr.inst];
+        const Ctrl& Sc = *CI->ctrl;
+        c_local = tr.local;
+        const int strip = tr.local % CI->nstrips;
+        c_chunk = tr.local / CI->nstrips;
+        const long long c0 = (long long)strip * STRIP;
+        c_n = CI->n;
+        c_ldc = CI->ldc;
+        c_ldx = CI->ldx;
+        c_i0 = c_chunk * CI->tile_rows;
+        const long long i1 = min(c_i0 + (long long)CI->tile_rows, CI->m);
+        const long long ncols = min((long long)STRIP, c_n - c0);
+        c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
+        j0 = c0 + lane * 4;
+        on = j0 < c_n;
+        c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        float* Xb = reinterpret_cast<float*>(CI->X);
+        c_xn = Xb + (long long)Sc.nxt * CI->xslot + c_i0 * c_ldx + j0;
+        c_xbn = Xb + (long long)Sc.barn * CI->xslot + c_i0 * c_ldx + j0;
+        c_rowpart = CI->rowpart + (long long)strip * CI->m;
+        const double* pv = slot_v(*CI, Sc.cur);
+        const double* q = pv + CI->m;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            valid[e] = j0 + e < c_n;
+            qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+        }
+        tau = (float)Sc.tau;
+        w = (float)(1.0 / (double)(Sc.k + 1));
+        first = Sc.k == 0;
+        c_p = pv;
+        c_i1 = i1;
+        c_win = -1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { cs[e] = 0.0; csa[e] = 0.f; }
+        dx2 = 0.0;
+        dxa = 0.f;
+        rows_in_batch = 0;
     };
 
+    bool failed = false;
     while (consumed < issued) {
         const int st = (int)(consumed % S);
-        const unsigned parity = (unsigned)((consumed / S) & 1);
-        if (!wait_stage(smem_u32(&bars[st]), parity)) { failed = true; break; }
+        if (!wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1))) { failed = true; break; }
         const RowRef ref = refs[st];
-        if (ref.tile != c_tile) {
-            flush_tile();
-            c_tile = ref.tile;
-            const TileRef tr = tmap[c_tile];
-            CI = &insts[tr.inst];
-            CS = CI->ctrl;
-            c_strip = tr.local % CI->nstrips;
-            c_chunk = tr.local / CI->nstrips;
-            j0 = (long long)c_strip * STRIP + lane * 4;
-            on = j0 < CI->n;
-            const double* q = slot_v(*CI, CS->cur) + CI->m;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                valid[e] = j0 + e < CI->n;
-                qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
-            }
-            tau = (float)CS->tau;
-            w = (float)(1.0 / (double)(CS->k + 1));
-            first = CS->k == 0;
-            {
-                // Stage the tile's row duals once instead of one dependent load per row.
-                const double* p = slot_v(*CI, CS->cur);
-                const long long r0 = (long long)c_chunk * CI->tile_rows;
-                const long long r1 = min(r0 + (long long)CI->tile_rows, CI->m);
-                __syncwarp();
-                for (long long r = r0 + lane; r < r1; r += 32) pbuf[r - r0] = (float)p[r];
-                __syncwarp();
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) { cs[e] = 0.0; csa[e] = 0.f; }
-            dx2 = 0.0;
-            dxa = 0.f;
-            rows_in_batch = 0;
-        }
+        if (ref.tile != c_tile) open_consumer(ref.tile);
         const long long i = ref.row;
+        const long long di = i - c_i0;
         const unsigned char* stage = wbase + st * STAGE_BYTES;
         float c[4], x[4], xb[4];
-        const long long c0 = (long long)c_strip * STRIP;
-        const long long ncols = min((long long)STRIP, CI->n - c0);
-        const long long cq = sizeof(TC) == 2 ? 8 : 4;
-        const bool c_bulk = !(i == CI->m - 1 && (ncols % cq) != 0);
         if (on) {
-            if (c_bulk) {
+            if (i != c_last_ragged) {
                 if (sizeof(TC) == 4) {
                     const float4 t = *reinterpret_cast<const float4*>(stage + lane * 16);
                     c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
@@ -503,7 +520,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
                     c[3] = bf16_bits_to_f32(t.y >> 16);
                 }
             } else {
-                ldc4_tail<float>(reinterpret_cast<const TC*>(CI->C) + i * CI->ldc + j0, CI->n - j0, c);
+                ldc4_tail<float>(c_C + i * c_ldc, c_n - j0, c);
             }
             const float4 tx = *reinterpret_cast<const float4*>(stage + STRIP * 4 + lane * 16);
             x[0] = tx.x; x[1] = tx.y; x[2] = tx.z; x[3] = tx.w;
@@ -517,12 +534,23 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
 #pragma unroll
             for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; }
         }
+        // Row duals are staged in shared memory per window of MAX_TILE_ROWS rows
+        // instead of one dependent global load per row.
+        const long long win = di / MAX_TILE_ROWS;
+        if (win != c_win) {
+            const long long r0 = c_i0 + win * MAX_TILE_ROWS;
+            const long long r1 = min(r0 + (long long)MAX_TILE_ROWS, c_i1);
+            __syncwarp();
+            for (long long r = r0 + lane; r < r1; r += 32) pbuf[r - r0] = (float)c_p[r];
+            __syncwarp();
+            c_win = win;
+        }
+        const float pv = pbuf[di - win * MAX_TILE_ROWS];
         // The stage has been read: release it to the producer.
         __syncwarp();
         ++consumed;
         if (p_tile < T) issue();
 
-        const float pv = pbuf[i - (long long)c_chunk * CI->tile_rows];
         float xn[4], xbn[4], rs = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -538,13 +566,11 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
             xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
         }
         if (on) {
-            float* Xn = reinterpret_cast<float*>(CI->X) + (long long)CS->nxt * CI->xslot + i * CI->ldx + j0;
-            float* Xbn = reinterpret_cast<float*>(CI->X) + (long long)CS->barn * CI->xslot + i * CI->ldx + j0;
-            st4(Xn, xn);
-            st4(Xbn, xbn);
+            st4(c_xn + di * c_ldx, xn);
+            st4(c_xbn + di * c_ldx, xbn);
         }
         rs = warp_sum(rs);
-        if (lane == 0) CI->rowpart[(long long)c_strip * CI->m + i] = (double)rs;
+        if (lane == 0) c_rowpart[i] = (double)rs;
         if (++rows_in_batch == 8) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
@@ -557,13 +583,13 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
         flush_tile();
     } else if (lane == 0) {
         // A stage never completed: report it and stop (bounded, never a trap).
-        Ctrl* Sw = const_cast<Ctrl*>(CS ? CS : insts[tmap[refs[(int)(consumed % S)].tile].inst].ctrl);
-        atomicExch(&Sw->status, ST_DEVICE);
+        const int t = refs[(int)(consumed % S)].tile;
+        atomicExch(&insts[tmap[t].inst].ctrl->status, ST_DEVICE);
     }
     // Drain: wait (bounded) for every copy still in flight before exiting.
     while (consumed < issued) {
         const int st = (int)(consumed % S);
-        wait_stage(smem_u32(&bars[st]), (unsigned)((consumed / S) & 1));
+        wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1));
         ++consumed;
     }
 }
@@ -630,8 +656,10 @@ __device__ __forceinline__ double group_sum(const double* part, long long stride
                                             bool active, double* sgrp) {
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     double s = 0.0;
-    if (active)
+    if (active) {
+#pragma unroll 4
         for (int k = grp; k < count; k += VG) s += part[(long long)k * stride + idx];
+    }
     sgrp[grp * 32 + lane] = s;
     __syncthreads();
     double t = 0.0;

@@ -37,7 +37,9 @@ def _same(a, b):
 
 
 def test_batch_equals_single_solves():
-    single = pdot.Solver(device=0, time_limit_s=120.0)
+    # The batch engine uses 64-row tiles; a single solve with the same tiling
+    # reduces its partial sums in the same order and must match bit for bit.
+    single = pdot.Solver(device=0, time_limit_s=120.0, tile_rows=64)
     batch = pdot.BatchSolver(device=0, time_limit_s=120.0)
     insts = [_inst(k) for k in range(12)]
     ids = [batch.submit(C, f, g, tol=1e-6) for C, f, g in insts]
