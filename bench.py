@@ -440,14 +440,15 @@ def run_pass_sweep(args):
         f = torch.tensor(ins.f, device="cuda:0")
         g = torch.tensor(ins.g, device="cuda:0")
         m = n = G * G
-        for bulk in ("1", "0"):
+        for bulk in ("2", "1", "0"):
             os.environ["PDOT_PASS_BULK"] = bulk
-            for tr in (0, 16, 32, 64, 128, 256, 512):
+            for tr in ((0, 32, 64, 128) if bulk != "0" else (0, 64)):
                 s = pdot.Solver(device=0, tile_rows=tr)
                 st, ms, b = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
                                                 30 if G == 64 else 10)
                 s.close()
-                row = {"m": m, "kernel": "bulk" if bulk == "1" else "register", "tile_rows": tr or "auto",
+                row = {"m": m, "kernel": {"2": "bulk-group", "1": "bulk-row", "0": "register"}[bulk],
+                       "tile_rows": tr or "auto",
                        "us": ms * 1e3, "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
                 out.append(row)
                 print(json.dumps(row), flush=True)

@@ -137,6 +137,7 @@ Inst make_inst(const Work& w, const void* C, int ctype, long long ldc, const dou
     I.rowpart = w.rowpart; I.colpart = w.colpart; I.tpart = w.tpart; I.vpart = w.vpart;
     I.ctrl = w.ctrl; I.ticket = w.ticket;
     I.nstrips = w.nstrips; I.nchunks = w.nchunks; I.tile_rows = w.tile_rows; I.ntiles = w.ntiles; I.nvt = w.nvt;
+    I.l2_keep_c = 0;
     return I;
 }
 
@@ -185,7 +186,8 @@ struct pdot_handle {
     int* h_status = nullptr;     // pinned [2]
     Graph chunk;                 // K x (pass, dual) + (kkt, checkvec)
     long long chunk_key[6] = {0, 0, 0, 0, 0, 0};
-    std::map<long long, int> tune_cache;   // (m, n, ttype) -> tile_rows
+    std::map<long long, std::pair<int, int>> tune_cache;   // (m, n, ttype) -> (pass kernel, tile_rows)
+    int autotune = 1;            // time pass-kernel candidates on a shape's first solve
     // host staging for pdot_solve_host
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -193,6 +195,8 @@ struct pdot_handle {
     size_t round_scratch_bytes = 0;
 
     BatchEngine* batch = nullptr;
+    int l2_hint = 0;             // L2 eviction-priority hints in the bulk pass (measured slower; opt-in)
+    long long l2_bytes = 0;
 };
 
 namespace {
@@ -278,19 +282,21 @@ void validate_marginals(pdot_handle* h, long long m, long long n, const double* 
     *norm_b = std::sqrt(nb);
 }
 
-int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool batch = false) {
+// Rows per plan tile.  `kernel`: the FP32-plan pass kernel the tiles are for
+// (0 register, 1 bulk per row, 2 bulk per 4-row group).
+int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kernel, bool batch) {
     if (h->opt.tile_rows > 0) return h->opt.tile_rows;
     const long long nstrips = (n + STRIP - 1) / STRIP;
-    if (batch) {
-        // Many instances share the tile queue: moderate tiles keep it balanced.
-        return 64;
-    }
-    // One instance: split it evenly over the resident warps, one tile each
-    // (the last wave of a dynamic queue would otherwise leave a tail), with
-    // tiles as tall as that allows (fewer column partials).
-    const long long warps = (long long)(ttype == TT_F64 ? h->cfg.tile_blocks_f64
-                                                        : (h->cfg.pass_bulk ? h->cfg.bulk_blocks : h->cfg.tile_blocks)) *
-                            TWARPS;
+    if (batch) return 64;   // many instances share the tile queue: moderate tiles keep it balanced
+    if (ttype == TT_F64) kernel = 0;
+    if (kernel == 2) return 32;   // grouped kernel: short tiles through the dynamic queue
+    // Otherwise split the instance evenly over the resident warps, one tile
+    // each (the last wave of a dynamic queue would leave a tail), as tall as
+    // that allows (fewer column partials).
+    const long long blocks = ttype == TT_F64 ? h->cfg.tile_blocks_f64
+                             : kernel == 1   ? h->cfg.bulk_blocks
+                                             : h->cfg.tile_blocks;
+    const long long warps = blocks * TWARPS;
     long long nch = warps / nstrips;
     if (nch < 1) nch = 1;
     long long tr = (m + nch - 1) / nch;
@@ -298,6 +304,15 @@ int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool bat
     if (tr < 2) tr = 2;
     if (tr > 4096) tr = 4096;
     return (int)tr;
+}
+
+int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool batch = false) {
+    if (!batch && h->opt.tile_rows <= 0) {
+        const long long key = (m * 1000003LL + n) * 4 + ttype;
+        auto it = h->tune_cache.find(key);
+        if (it != h->tune_cache.end() && it->second.first == h->cfg.pass_bulk) return it->second.second;
+    }
+    return tile_rows_for(h, m, n, ttype, h->cfg.pass_bulk, batch);
 }
 
 const void* prepare_C(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
@@ -360,9 +375,18 @@ void init_ctrl(pdot_handle* h, Ctrl* S, long long m, long long n, double tol, do
 
 void launch_count(pdot_handle* h, int k) { h->launches += k; }
 
+// Keep C resident in L2 when it takes at most half of it (it is re-read every
+// pass; the plan streams get evict-first so they do not push it out).
+bool keep_c_in_l2(pdot_handle* h, const Inst& I) {
+    if (!h->l2_hint || h->l2_bytes <= 0) return false;
+    const double cbytes = (double)I.m * (double)I.ldc * (double)csize_of(I.ctype);
+    return cbytes <= 0.5 * (double)h->l2_bytes;
+}
+
 // Upload the instance descriptor and reset the work counters.
 void stage_instance(pdot_handle* h, const Inst& I) {
     *h->h_inst = I;
+    h->h_inst->l2_keep_c = keep_c_in_l2(h, I) ? 1 : 0;
     CK(cudaMemcpyAsync(h->d_inst, h->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
 }
@@ -498,6 +522,74 @@ void check_common_args(pdot_handle* h, long long m, long long n, const void* C, 
 double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const void* Xsrc, long long ldx,
                       const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc);
 
+// Autotuner: on the first single-instance solve of a shape (m, n, dtype),
+// time the fused pass for each candidate (kernel, tile height) on this
+// device with CUDA events -- three real steps first so the running average
+// is read, then repeated passes on the same state -- and keep the fastest.
+// Small shapes are launch-bound: they take the default without timing.
+void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
+                   const double* f, const double* g) {
+    const int ttype = ttype_of(ctype);
+    if (ttype == TT_F64 || h->opt.tile_rows > 0 || !h->cfg_base.pass_bulk) return;
+    const long long key = (m * 1000003LL + n) * 4 + ttype;
+    auto it = h->tune_cache.find(key);
+    if (it != h->tune_cache.end()) {
+        h->cfg.pass_bulk = it->second.first;
+        return;
+    }
+    if (!h->autotune || m * n < (1LL << 22)) {
+        const int kern = h->autotune ? 1 : h->cfg_base.pass_bulk;
+        h->tune_cache[key] = {kern, tile_rows_for(h, m, n, ttype, kern, false)};
+        h->cfg.pass_bulk = kern;
+        return;
+    }
+    const int cands[3][2] = {{1, 0}, {2, 32}, {2, 64}};
+    float best = 1e30f;
+    int best_k = 1, best_tr = tile_rows_for(h, m, n, ttype, 1, false);
+    const int reps = m * n >= (1LL << 26) ? 6 : 20;
+    for (const auto& c : cands) {
+        const int kern = c[0];
+        const int tr = c[1] ? c[1] : tile_rows_for(h, m, n, ttype, kern, false);
+        h->cfg.pass_bulk = kern;
+        ensure_work(h, m, n, h->opt.x_dtype, tr);
+        ensure_maps(h);
+        Work& w = h->ws;
+        long long ldc_used = ldc;
+        const void* Cd = prepare_C(h, m, n, C, ctype, ldc, &ldc_used);
+        stage_instance(h, make_inst(w, Cd, ctype, ldc_used, f, g));
+        Ctrl* S = h->h_ctrl;
+        init_ctrl(h, S, m, n, -1.0, 1.0, 1.0, true, 0.5 / std::sqrt((double)(m + n)), 1.0);
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xsize_of(w.xtype), h->stream));
+        CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));
+        run_check(h, ttype, MODE_INIT);
+        for (int s2 = 0; s2 < 3; ++s2) run_step(h, ttype);
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < reps; ++r) {
+            const int wc = (r & 1) ? wc_index(WC_AUX, ttype) : wc_index(WC_PASS, ttype);
+            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream, wc));
+        }
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        launch_count(h, reps + 5);
+        if (ms < best) {
+            best = ms;
+            best_k = kern;
+            best_tr = tr;
+        }
+    }
+    h->tune_cache[key] = {best_k, best_tr};
+    h->cfg.pass_bulk = best_k;
+}
+
 pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                        const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
                        pdot_result* res) {
@@ -508,6 +600,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     double norm_b = 0.0;
     validate_marginals(h, m, n, f, g, false, &norm_b);
     const int ttype = ttype_of(ctype);
+    autotune_pass(h, m, n, C, ctype, ldc, f, g);
     const int tr = pick_tile_rows(h, m, n, ttype);
     ensure_work(h, m, n, h->opt.x_dtype, tr);
     ensure_maps(h);
@@ -771,6 +864,7 @@ struct BatchEngine {
     cudaEvent_t ev_chunk = nullptr, ev_copy = nullptr;
     bool inflight = false;
     int nv_live = 0;
+    int nv_grid = 32;          // vector-kernel grid: live vector tiles rounded up to a power of two
     int64_t chunks = 0;
 };
 
@@ -865,6 +959,13 @@ void batch_compose(pdot_handle* h) {
     B->cnt.h[8] = (int)ovi;
     CK(cudaMemcpyAsync(B->cnt.d, B->cnt.h, sizeof(int) * 9, cudaMemcpyHostToDevice, st));
     B->nv_live = (int)ov;
+    {
+        // One CTA per vector tile: size the grid by the live count (bucketed,
+        // so the chunk graph is re-captured only when the bucket changes).
+        int g = 32;
+        while (g < (int)ov) g *= 2;
+        B->nv_grid = g;
+    }
     // Init checks of the fresh instances (X = 0, p = q = 0; norms; marginal checks).
     if (nvi > 0) {
         CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, st));
@@ -892,7 +993,7 @@ void batch_issue_chunk(pdot_handle* h, int types) {
                 CKL(launch_pass(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, h->cfg, st));
                 launch_count(h, 1);
             }
-            CKL(launch_dual(B->insts.d, B->vmap.d, B->cnt.d + 3, h->cfg.vec_blocks, h->wctr, h->cfg, st));
+            CKL(launch_dual(B->insts.d, B->vmap.d, B->cnt.d + 3, B->nv_grid, h->wctr, h->cfg, st));
             launch_count(h, 1);
         }
         for (int t = 0; t < NTT; ++t) {
@@ -900,7 +1001,7 @@ void batch_issue_chunk(pdot_handle* h, int types) {
             CKL(launch_kkt(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, MODE_CHECK, h->cfg, st));
             launch_count(h, 1);
         }
-        CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + 3, h->cfg.vec_blocks, h->wctr, MODE_CHECK, h->cfg, st));
+        CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + 3, B->nv_grid, h->wctr, MODE_CHECK, h->cfg, st));
         launch_count(h, 1);
     }
     (void)nvh;
@@ -917,7 +1018,7 @@ void batch_launch_chunk(pdot_handle* h) {
                               (long long)(uintptr_t)B->vmap.d,
                               (long long)(uintptr_t)B->tmap[0].d ^ ((long long)(uintptr_t)B->tmap[1].d << 1) ^
                                   ((long long)(uintptr_t)B->tmap[2].d << 2),
-                              types, h->opt.restart_check_every, h->opt.chunk_checks,
+                              types | ((long long)B->nv_grid << 8), h->opt.restart_check_every, h->opt.chunk_checks,
                               (long long)B->snap.cap};
     if (!h->opt.use_graph) {
         batch_issue_chunk(h, types);
@@ -1210,9 +1311,25 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         const int bulk = setup_bulk_pass();
         if (bulk > 0) throw CudaError{(cudaError_t)bulk};
         h->cfg.bulk_blocks = h->sm_count * (-bulk);
+        const int grp = setup_group_pass();
+        if (grp > 0) throw CudaError{(cudaError_t)grp};
+        h->cfg.group_blocks = h->sm_count * (-grp);
         h->cfg.pass_bulk = 1;
         const char* pb = getenv("PDOT_PASS_BULK");
-        if (pb && atoi(pb) == 0) h->cfg.pass_bulk = 0;
+        if (pb) {
+            const int v = atoi(pb);
+            if (v >= 0 && v <= 2) {
+                h->cfg.pass_bulk = v;
+                h->autotune = 0;   // an explicit kernel choice disables the tuner
+            }
+        }
+        const char* at = getenv("PDOT_AUTOTUNE");
+        if (at && atoi(at) == 0) h->autotune = 0;
+        int l2 = 0;
+        CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device));
+        h->l2_bytes = l2;
+        const char* lh = getenv("PDOT_L2HINT");
+        if (lh && atoi(lh) == 1) h->l2_hint = 1;
         const char* pp = getenv("PDOT_PDL");
         h->cfg.pdl = (pp && atoi(pp) == 1) ? 1 : 0;
         h->cfg_base = h->cfg;

@@ -72,7 +72,8 @@ struct Inst {
     double* vpart;
     Ctrl* ctrl;
     unsigned int* ticket;
-    int nstrips, nchunks, tile_rows, ntiles, nvt, pad_;
+    int nstrips, nchunks, tile_rows, ntiles, nvt;
+    int l2_keep_c;       // 1: C fits in L2 next to the streams; load it evict-last, stream X evict-first
 };
 
 struct TileRef {
@@ -101,8 +102,9 @@ struct LaunchCfg {
     int tile_blocks_f64;  // CTAs of the FP64-plan tile kernels
     int vec_blocks;       // CTAs of the vector kernels (256 threads each)
     int pass_u;           // rows per load batch in the FP32-plan register pass (2 or 4)
-    int pass_bulk;        // 1: FP32-plan passes use the bulk-copy pipeline kernel
+    int pass_bulk;        // FP32-plan pass kernel: 0 register pipeline, 1 bulk copies per row, 2 per 4-row group
     int bulk_blocks;      // CTAs of the bulk-copy pass kernel
+    int group_blocks;     // CTAs of the grouped bulk-copy pass kernel
     int pdl;              // 1: launch with programmatic dependent launch
 };
 
@@ -124,5 +126,6 @@ int occupancy_vec_blocks_per_sm();
 // Opt the bulk-copy pass kernel into its shared-memory size; returns minus
 // the CTAs per SM it can hold, or a positive cudaError_t code.
 int setup_bulk_pass();
+int setup_group_pass();
 
 }  // namespace pdot

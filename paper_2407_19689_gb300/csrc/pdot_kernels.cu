@@ -303,6 +303,31 @@ __device__ __forceinline__ void g2s(unsigned dst, const void* src, unsigned byte
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// Bulk copy with an L2 eviction-priority policy (createpolicy descriptor).
+__device__ __forceinline__ void g2s_hint(unsigned dst, const void* src, unsigned bytes, unsigned bar,
+                                         unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st4_hint(float* p, const float (&v)[4], unsigned long long pol) {
+    asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3]), "l"(pol)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -368,6 +393,9 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     long long p_cstride = 0, p_xstride = 0;
     unsigned p_cbytes = 0, p_xbytes = 0;
     bool p_first = true;
+    bool p_hint = false;                // keep this instance's C in L2 (it fits)
+    const unsigned long long pol_keep = policy_evict_last();
+    const unsigned long long pol_stream = policy_evict_first();
     auto next_tile = [&]() {
         for (;;) {
             p_tile = warp_next(&wctr[wc]);
@@ -394,6 +422,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
             // the last matrix row of a ragged strip: lanes load that row.
             p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
             p_first = Sc.k == 0;
+            p_hint = I.l2_keep_c != 0;
             return;
         }
     };
@@ -408,9 +437,16 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
             const unsigned cb = p_row == p_last_ragged ? 0u : p_cbytes;
             fence_proxy_async();
             mbar_expect_tx(bar, cb + p_xbytes + (p_first ? 0u : p_xbytes));
-            if (cb) g2s(dst, p_c, cb, bar);
-            g2s(dst + STRIP * 4, p_x, p_xbytes, bar);
-            if (!p_first) g2s(dst + 2 * STRIP * 4, p_xb, p_xbytes, bar);
+            if (p_hint) {
+                // C is re-read every pass and fits in L2: keep it; stream the plan.
+                if (cb) g2s_hint(dst, p_c, cb, bar, pol_keep);
+                g2s_hint(dst + STRIP * 4, p_x, p_xbytes, bar, pol_stream);
+                if (!p_first) g2s_hint(dst + 2 * STRIP * 4, p_xb, p_xbytes, bar, pol_stream);
+            } else {
+                if (cb) g2s(dst, p_c, cb, bar);
+                g2s(dst + STRIP * 4, p_x, p_xbytes, bar);
+                if (!p_first) g2s(dst + 2 * STRIP * 4, p_xb, p_xbytes, bar);
+            }
         }
         ++issued;
         p_c += p_cstride;
@@ -439,6 +475,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     int rows_in_batch = 0;
     int c_local = 0;
     const double* c_p = nullptr;   // p of the consumer's instance
+    bool c_hint = false;
     long long c_i1 = 0, c_win = -1;
     auto flush_tile = [&]() {
         if (c_tile < 0) return;
@@ -489,6 +526,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
         first = Sc.k == 0;
         c_p = pv;
         c_i1 = i1;
+        c_hint = CI->l2_keep_c != 0;
         c_win = -1;
 #pragma unroll
         for (int e = 0; e < 4; ++e) { cs[e] = 0.0; csa[e] = 0.f; }
@@ -566,8 +604,13 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
             xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
         }
         if (on) {
-            st4(c_xn + di * c_ldx, xn);
-            st4(c_xbn + di * c_ldx, xbn);
+            if (c_hint) {
+                st4_hint(c_xn + di * c_ldx, xn, pol_stream);
+                st4_hint(c_xbn + di * c_ldx, xbn, pol_stream);
+            } else {
+                st4(c_xn + di * c_ldx, xn);
+                st4(c_xbn + di * c_ldx, xbn);
+            }
         }
         rs = warp_sum(rs);
         if (lane == 0) c_rowpart[i] = (double)rs;
@@ -587,6 +630,320 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
         atomicExch(&insts[tmap[t].inst].ctrl->status, ST_DEVICE);
     }
     // Drain: wait (bounded) for every copy still in flight before exiting.
+    while (consumed < issued) {
+        const int st = (int)(consumed % S);
+        wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1));
+        ++consumed;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plan pass, grouped bulk-copy pipeline (default for FP32 plans).  Like
+// k_pass_bulk, but a stage holds a group of up to R consecutive rows of one
+// tile: one mbarrier wait and one bookkeeping step per group, the group's
+// 3R row copies issued by 3R lanes at once, and the R row sums reduced by a
+// multi-row butterfly (6 shuffles for 4 rows instead of 20).
+// ---------------------------------------------------------------------------
+namespace bulk {
+
+struct GroupRef {
+    int tile;     // global tile index
+    int row0;     // first matrix row of the group
+    int count;    // rows in the group (1..R)
+    int pad;
+};
+
+template <int R, int S>
+__host__ __device__ constexpr int warp_smem_bytes_g() { return S * R * STAGE_BYTES + S * 8 + S * 16 + MAX_TILE_ROWS * 4; }
+
+// Sum v[r] over the 32 lanes for R = 4 rows with 6 shuffles.  The total of
+// row r ends in lanes 8r .. 8r+7.
+__device__ __forceinline__ float rows4_sum(const float (&v)[4], int lane) {
+    const bool hi16 = lane & 16;
+    const float s0 = __shfl_xor_sync(0xffffffffu, hi16 ? v[0] : v[2], 16);
+    const float s1 = __shfl_xor_sync(0xffffffffu, hi16 ? v[1] : v[3], 16);
+    const float a0 = (hi16 ? v[2] : v[0]) + s0;   // row 0 (low half) / row 2 (high half)
+    const float a1 = (hi16 ? v[3] : v[1]) + s1;   // row 1 / row 3
+    const bool hi8 = lane & 8;
+    const float t = __shfl_xor_sync(0xffffffffu, hi8 ? a0 : a1, 8);
+    float b = (hi8 ? a1 : a0) + t;
+    b += __shfl_xor_sync(0xffffffffu, b, 4);
+    b += __shfl_xor_sync(0xffffffffu, b, 2);
+    b += __shfl_xor_sync(0xffffffffu, b, 1);
+    return b;
+}
+
+}  // namespace bulk
+
+template <typename TC, int S>
+__global__ void __launch_bounds__(TWARPS * 32)
+k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
+             unsigned* wctr, int wc) {
+    using namespace bulk;
+    constexpr int R = 4;
+    pdl_enter();
+    const int T = *Tp;
+    reset_other_counters(wctr, wc);
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wbase = dsm + warp * warp_smem_bytes_g<R, S>();
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + S * R * STAGE_BYTES);
+    GroupRef* refs = reinterpret_cast<GroupRef*>(wbase + S * R * STAGE_BYTES + S * 8);
+    float* pbuf = reinterpret_cast<float*>(wbase + S * R * STAGE_BYTES + S * 24);
+    const unsigned wbase_s = smem_u32(wbase);
+    const unsigned bars_s = smem_u32(bars);
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(bars_s + 8 * s, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
+
+    // ---- producer ----
+    int p_tile = T;
+    long long p_row = 0, p_end = 0, p_last_ragged = -1;
+    const char* p_c = nullptr;
+    const char* p_x = nullptr;
+    const char* p_xb = nullptr;
+    long long p_cstride = 0, p_xstride = 0;
+    unsigned p_cbytes = 0, p_xbytes = 0;
+    bool p_first = true;
+    auto next_tile = [&]() {
+        for (;;) {
+            p_tile = warp_next(&wctr[wc]);
+            if (p_tile >= T) return;
+            const TileRef tr = tmap[p_tile];
+            const Inst& I = insts[tr.inst];
+            const Ctrl& Sc = *I.ctrl;
+            if (Sc.status != ST_RUNNING) continue;
+            const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
+            const long long c0 = (long long)strip * STRIP;
+            const long long ncols = min((long long)STRIP, I.n - c0);
+            p_row = (long long)chunk * I.tile_rows;
+            p_end = min(p_row + (long long)I.tile_rows, I.m);
+            p_cstride = I.ldc * (long long)sizeof(TC);
+            p_xstride = I.ldx * 4;
+            p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
+                                                p_row * I.ldx + c0);
+            p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
+                                                 p_row * I.ldx + c0);
+            p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
+            p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
+            p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            p_first = Sc.k == 0;
+            return;
+        }
+    };
+    long long issued = 0, consumed = 0;   // in groups
+    auto issue = [&]() {
+        const int st = (int)(issued % S);
+        const int g = (int)min((long long)R, p_end - p_row);
+        const unsigned bar = bars_s + 8 * st;
+        const unsigned dst = wbase_s + st * (R * STAGE_BYTES);
+        // The C copy of the last matrix row of a ragged strip is skipped (lanes load it).
+        const bool skip_c = p_last_ragged >= p_row && p_last_ragged < p_row + g;
+        const unsigned bytes = (unsigned)g * (p_cbytes + p_xbytes + (p_first ? 0u : p_xbytes)) - (skip_c ? p_cbytes : 0u);
+        if (lane == 0) {
+            refs[st].tile = p_tile;
+            refs[st].row0 = (int)p_row;
+            refs[st].count = g;
+            fence_proxy_async();
+            mbar_expect_tx(bar, bytes);
+        }
+        __syncwarp();
+        // Lane k copies array (k % 3) of row (k / 3): 3g copies issued at once.
+        if (lane < 3 * g) {
+            const int r = lane / 3, arr = lane % 3;
+            const unsigned d = dst + r * STAGE_BYTES + arr * (STRIP * 4);
+            fence_proxy_async();   // this lane's copy follows the warp's generic reads of the stage
+            if (arr == 0) {
+                if (!(skip_c && p_row + r == p_last_ragged)) g2s(d, p_c + r * p_cstride, p_cbytes, bar);
+            } else if (arr == 1) {
+                g2s(d, p_x + r * p_xstride, p_xbytes, bar);
+            } else if (!p_first) {
+                g2s(d, p_xb + r * p_xstride, p_xbytes, bar);
+            }
+        }
+        ++issued;
+        p_c += g * p_cstride;
+        p_x += g * p_xstride;
+        p_xb += g * p_xstride;
+        p_row += g;
+        if (p_row >= p_end) next_tile();
+    };
+    next_tile();
+    while (issued < S && p_tile < T) issue();
+
+    // ---- consumer ----
+    int c_tile = -1;
+    const Inst* CI = nullptr;
+    const TC* c_C = nullptr;
+    long long c_ldc = 0, c_ldx = 0, c_i0 = 0, c_n = 0, c_last_ragged = -1, c_chunk = 0;
+    float* c_xn = nullptr;
+    float* c_xbn = nullptr;
+    double* c_rowpart = nullptr;
+    long long j0 = 0;
+    bool on = false, valid[4] = {false, false, false, false};
+    float qv[4] = {0.f, 0.f, 0.f, 0.f};
+    float tau = 0.f, w = 0.f;
+    bool first = true;
+    double cs[4] = {0.0, 0.0, 0.0, 0.0}, dx2 = 0.0;
+    float csa[4] = {0.f, 0.f, 0.f, 0.f}, dxa = 0.f;
+    int rows_in_batch = 0;
+    int c_local = 0;
+    const double* c_p = nullptr;
+    long long c_i1 = 0, c_win = -1;
+    auto flush_tile = [&]() {
+        if (c_tile < 0) return;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
+        dx2 += (double)dxa;
+        if (on) {
+            double* cp = CI->colpart + c_chunk * CI->ldx + j0;
+            reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
+            reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
+        }
+        const double d = warp_sum(dx2);
+        if (lane == 0) CI->tpart[(long long)c_local * TP + 0] = d;
+    };
+    auto open_consumer = [&](int t) {
+        flush_tile();
+        c_tile = t;
+        const TileRef tr = tmap[t];
+        CI = &insts[tr.inst];
+        const Ctrl& Sc = *CI->ctrl;
+        c_local = tr.local;
+        const int strip = tr.local % CI->nstrips;
+        c_chunk = tr.local / CI->nstrips;
+        const long long c0 = (long long)strip * STRIP;
+        c_n = CI->n;
+        c_ldc = CI->ldc;
+        c_ldx = CI->ldx;
+        c_i0 = c_chunk * CI->tile_rows;
+        c_i1 = min(c_i0 + (long long)CI->tile_rows, CI->m);
+        const long long ncols = min((long long)STRIP, c_n - c0);
+        c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
+        j0 = c0 + lane * 4;
+        on = j0 < c_n;
+        c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        float* Xb = reinterpret_cast<float*>(CI->X);
+        c_xn = Xb + (long long)Sc.nxt * CI->xslot + c_i0 * c_ldx + j0;
+        c_xbn = Xb + (long long)Sc.barn * CI->xslot + c_i0 * c_ldx + j0;
+        c_rowpart = CI->rowpart + (long long)strip * CI->m;
+        c_p = slot_v(*CI, Sc.cur);
+        const double* q = c_p + CI->m;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            valid[e] = j0 + e < c_n;
+            qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+        }
+        tau = (float)Sc.tau;
+        w = (float)(1.0 / (double)(Sc.k + 1));
+        first = Sc.k == 0;
+        c_win = -1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { cs[e] = 0.0; csa[e] = 0.f; }
+        dx2 = 0.0;
+        dxa = 0.f;
+        rows_in_batch = 0;
+    };
+
+    bool failed = false;
+    while (consumed < issued) {
+        const int st = (int)(consumed % S);
+        if (!wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1))) { failed = true; break; }
+        const GroupRef ref = refs[st];
+        if (ref.tile != c_tile) open_consumer(ref.tile);
+        const unsigned char* stage = wbase + st * (R * STAGE_BYTES);
+        float rsv[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            rsv[r] = 0.f;
+            if (r >= ref.count) continue;
+            const long long i = ref.row0 + r;
+            const long long di = i - c_i0;
+            const unsigned char* rst = stage + r * STAGE_BYTES;
+            // Row duals staged per window of MAX_TILE_ROWS rows.
+            const long long win = di / MAX_TILE_ROWS;
+            if (win != c_win) {
+                const long long r0 = c_i0 + win * MAX_TILE_ROWS;
+                const long long r1 = min(r0 + (long long)MAX_TILE_ROWS, c_i1);
+                __syncwarp();
+                for (long long rr = r0 + lane; rr < r1; rr += 32) pbuf[rr - r0] = (float)c_p[rr];
+                __syncwarp();
+                c_win = win;
+            }
+            const float pv = pbuf[di - win * MAX_TILE_ROWS];
+            float c[4], x[4], xb[4];
+            if (on) {
+                if (i != c_last_ragged) {
+                    if (sizeof(TC) == 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(rst + lane * 16);
+                        c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
+                    } else {
+                        const uint2 t = *reinterpret_cast<const uint2*>(rst + lane * 8);
+                        c[0] = bf16_bits_to_f32(t.x & 0xffffu);
+                        c[1] = bf16_bits_to_f32(t.x >> 16);
+                        c[2] = bf16_bits_to_f32(t.y & 0xffffu);
+                        c[3] = bf16_bits_to_f32(t.y >> 16);
+                    }
+                } else {
+                    ldc4_tail<float>(c_C + i * c_ldc, c_n - j0, c);
+                }
+                const float4 tx = *reinterpret_cast<const float4*>(rst + STRIP * 4 + lane * 16);
+                x[0] = tx.x; x[1] = tx.y; x[2] = tx.z; x[3] = tx.w;
+                if (!first) {
+                    const float4 tb = *reinterpret_cast<const float4*>(rst + 2 * STRIP * 4 + lane * 16);
+                    xb[0] = tb.x; xb[1] = tb.y; xb[2] = tb.z; xb[3] = tb.w;
+                } else {
+                    xb[0] = xb[1] = xb[2] = xb[3] = 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; }
+            }
+            float xn[4], xbn[4], rs = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float Rc = (c[e] - pv) - qv[e];
+                float v = x[e] - tau * Rc;
+                v = v > 0.f ? v : 0.f;
+                v = valid[e] ? v : 0.f;
+                const float d = v - x[e];
+                dxa += d * d;
+                rs += v;
+                csa[e] += v;
+                xn[e] = v;
+                xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
+            }
+            if (on) {
+                st4(c_xn + di * c_ldx, xn);
+                st4(c_xbn + di * c_ldx, xbn);
+            }
+            rsv[r] = rs;
+        }
+        // The group's stage has been read: release it and refill it.
+        __syncwarp();
+        ++consumed;
+        if (p_tile < T) issue();
+        const float tot = rows4_sum(rsv, lane);
+        if ((lane & 7) == 0 && (lane >> 3) < ref.count) c_rowpart[ref.row0 + (lane >> 3)] = (double)tot;
+        rows_in_batch += ref.count;
+        if (rows_in_batch >= 8) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
+            dx2 += (double)dxa;
+            dxa = 0.f;
+            rows_in_batch = 0;
+        }
+    }
+    if (!failed) {
+        flush_tile();
+    } else if (lane == 0) {
+        const int t = refs[(int)(consumed % S)].tile;
+        atomicExch(&insts[tmap[t].inst].ctrl->status, ST_DEVICE);
+    }
     while (consumed < issued) {
         const int st = (int)(consumed % S);
         wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1));
@@ -622,9 +979,11 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
         // is the 1-based index of the attempted iteration plus one.
         const double om = S->omega;
         const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
-        const double t1 = (double)(S->total + 2);
-        const double a = (1.0 - pow(t1, -0.3)) * etabar;
-        const double b = (1.0 + pow(t1, -0.6)) * eta;
+        // The two schedule factors are heuristics; single precision is ample
+        // (GB300's FP64 transcendentals are slow on this serial path).
+        const float t1 = (float)(S->total + 2);
+        const double a = (1.0 - (double)powf(t1, -0.3f)) * etabar;
+        const double b = (1.0 + (double)powf(t1, -0.6f)) * eta;
         const double eta_next = a < b ? a : b;
         accept = eta <= etabar;
         S->last_etabar = etabar;
@@ -677,10 +1036,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* 
     const long long e = (long long)lvt * VE + lane;
     const bool row = e < m, col = !row && e < m + n;
     const long long idx = row ? e : e - m;
-    // One uniform call (it synchronises the block): rows reduce strip partials,
-    // columns reduce chunk partials.
-    const double s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
-                               row || col, sgrp);
+    // Independent loads first, so their latencies overlap the partial sums.
     const double sigma = S->sigma;
     const long long k = S->k;
     const bool first = k == 0;
@@ -689,23 +1045,35 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* 
     double* Vn = slot_v(I, S->nxt);
     const double* Vb = slot_v(I, S->bar);
     double* Vbn = slot_v(I, S->barn);
-    double a[3] = {0.0, 0.0, 0.0};   // ||dy||^2, dy^T A dx, ||dX||^2 (tile slice)
+    const long long yo = row ? idx : m + idx;                   // p_i or q_j
+    const long long so = row ? m + n + idx : 2 * m + n + idx;   // r_i or c_j
+    double b = 0.0, r = 0.0, y = 0.0, ybar = 0.0;
     if (grp == 0 && (row || col)) {
-        const long long yo = row ? idx : m + idx;               // p_i or q_j
-        const long long so = row ? m + n + idx : 2 * m + n + idx;   // r_i or c_j
-        const double b = row ? I.f[idx] : I.g[idx];
-        const double r = Vc[so], y = Vc[yo];
+        b = row ? I.f[idx] : I.g[idx];
+        r = Vc[so];
+        y = Vc[yo];
+        if (!first) ybar = Vb[yo];
+    }
+    double a2 = 0.0;   // ||dX||^2 over this vector tile's slice of plan tiles
+    {
+        const long long T = I.ntiles;
+        const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+        for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) a2 += I.tpart[t * TP + 0];
+    }
+    // One uniform call (it synchronises the block): rows reduce strip partials,
+    // columns reduce chunk partials.
+    const double s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
+                               row || col, sgrp);
+    double a[3] = {0.0, 0.0, a2};   // ||dy||^2, dy^T A dx, ||dX||^2 (tile slice)
+    if (grp == 0 && (row || col)) {
         const double yn = y + sigma * (b - (2.0 * s - r));
         Vn[yo] = yn;
         Vn[so] = s;
-        Vbn[yo] = first ? yn : Vb[yo] + w * (yn - Vb[yo]);
+        Vbn[yo] = first ? yn : ybar + w * (yn - ybar);
         const double dy = yn - y;
         a[0] = dy * dy;
         a[1] = dy * (s - r);
     }
-    const long long T = I.ntiles;
-    const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
-    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) a[2] += I.tpart[t * TP + 0];
     block_sum<3>(a, red);
     if (threadIdx.x == 0) {
         double* vp = I.vpart + (long long)lvt * VP;
@@ -735,25 +1103,21 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* 
 
 __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                              const int* __restrict__ NVp, unsigned* wctr) {
+    // One CTA per vector tile (no work queue): the grid covers the tile count.
     __shared__ double red[(VT / 32) * 3];
     __shared__ double sgrp[VG * 32];
-    __shared__ int s_t, s_last;
-    const int wc = wc_index(WC_DUAL, 0);
+    __shared__ int s_last;
     pdl_enter();
-    reset_other_counters(wctr, wc);
+    // No work counter of its own, but it still resets the others for the
+    // kernels that follow (block 0, before any early exit).
+    reset_other_counters(wctr, wc_index(WC_DUAL, 0));
     const int NV = *NVp;
-    for (;;) {
-        if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= NV) break;
-        const TileRef tr = vmap[t];
-        const Inst& I = insts[tr.inst];
-        Ctrl* S = I.ctrl;
-        if (S->status != ST_RUNNING) continue;
-        dual_tile(I, S, tr.local, red, sgrp, &s_last);
-    }
+    if ((int)blockIdx.x >= NV) return;
+    const TileRef tr = vmap[blockIdx.x];
+    const Inst& I = insts[tr.inst];
+    Ctrl* S = I.ctrl;
+    if (S->status != ST_RUNNING) return;
+    dual_tile(I, S, tr.local, red, sgrp, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -1096,25 +1460,21 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
 
 __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                                  const int* __restrict__ NVp, unsigned* wctr, int mode) {
+    // One CTA per vector tile (no work queue): the grid covers the tile count.
     __shared__ double red[(VT / 32) * VP];
     __shared__ double sgrp[VG * 32];
-    __shared__ int s_t, s_last;
-    const int wc = wc_index(WC_CHECK, 0);
+    __shared__ int s_last;
     pdl_enter();
-    reset_other_counters(wctr, wc);
+    // No work counter of its own, but it still resets the others for the
+    // kernels that follow (block 0, before any early exit).
+    reset_other_counters(wctr, wc_index(WC_CHECK, 0));
     const int NV = *NVp;
-    for (;;) {
-        if (threadIdx.x == 0) s_t = (int)atomicAdd(&wctr[wc], 1u);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= NV) break;
-        const TileRef tr = vmap[t];
-        const Inst& I = insts[tr.inst];
-        Ctrl* S = I.ctrl;
-        if (S->status != ST_RUNNING) continue;
-        checkvec_tile(I, S, tr.local, mode, red, sgrp, &s_last);
-    }
+    if ((int)blockIdx.x >= NV) return;
+    const TileRef tr = vmap[blockIdx.x];
+    const Inst& I = insts[tr.inst];
+    Ctrl* S = I.ctrl;
+    if (S->status != ST_RUNNING) return;
+    checkvec_tile(I, S, tr.local, mode, red, sgrp, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -1195,6 +1555,8 @@ static int launch_k(bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned bl
 
 constexpr int BULK_S = 8;
 constexpr int bulk_smem() { return TWARPS * bulk::warp_smem_bytes<BULK_S>(); }
+constexpr int GROUP_S = 2;   // stages of 4 rows: 8 rows in flight per warp
+constexpr int group_smem() { return TWARPS * bulk::warp_smem_bytes_g<4, GROUP_S>(); }
 
 int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream, int wc_override) {
@@ -1202,6 +1564,13 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
     const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
     const bool pdl = cfg.pdl != 0;
     const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
+    if (cfg.pass_bulk == 2 && ttype != TT_F64) {
+        if (ttype == TT_BF16)
+            return launch_k(pdl, k_pass_group<unsigned short, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc);
+        return launch_k(pdl, k_pass_group<float, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st, d_insts,
+                        d_tmap, T, wctr, wc);
+    }
     if (cfg.pass_bulk && ttype != TT_F64) {
         if (ttype == TT_BF16)
             return launch_k(pdl, k_pass_bulk<unsigned short, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st,
@@ -1222,7 +1591,8 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
 }
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream) {
-    int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
+    // nv_hint: an upper bound of the vector-tile count (one CTA each).
+    int blocks = nv_hint;
     if (blocks < 1) blocks = 1;
     return launch_k(cfg.pdl != 0, k_dual, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV, wctr);
 }
@@ -1243,7 +1613,7 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
 }
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream) {
-    int blocks = nv_hint < cfg.vec_blocks ? nv_hint : cfg.vec_blocks;
+    int blocks = nv_hint;
     if (blocks < 1) blocks = 1;
     return launch_k(cfg.pdl != 0, k_checkvec, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV,
                     wctr, mode);
@@ -1288,6 +1658,20 @@ int occupancy_tile_blocks_per_sm(int ttype) {
     if (d < r) r = d;
     return r;
 }
+int setup_group_pass() {
+    const int bytes = group_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_pass_group<float, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         bytes);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_pass_group<unsigned short, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_group<float, GROUP_S>, TWARPS * 32, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_group<unsigned short, GROUP_S>, TWARPS * 32, bytes);
+    const int r = a < b ? a : b;
+    return -(r > 0 ? r : 1);
+}
+
 int setup_bulk_pass() {
     const int bytes = bulk_smem();
     cudaError_t e = cudaFuncSetAttribute(k_pass_bulk<float, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
