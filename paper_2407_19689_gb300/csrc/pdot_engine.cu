@@ -196,6 +196,8 @@ struct pdot_handle {
 
     BatchEngine* batch = nullptr;
     int l2_hint = 0;             // L2 eviction-priority hints in the bulk pass (measured slower; opt-in)
+    int coop = 0;                // 1: single FP32-plan solves run one cooperative launch per chunk (opt-in: measured slower)
+    GridBar* d_gb = nullptr;
     long long l2_bytes = 0;
 };
 
@@ -294,7 +296,8 @@ int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kerne
     // each (the last wave of a dynamic queue would leave a tail), as tall as
     // that allows (fewer column partials).
     const long long blocks = ttype == TT_F64 ? h->cfg.tile_blocks_f64
-                             : kernel == 1   ? h->cfg.bulk_blocks
+                             : kernel == 1   ? (h->coop && h->cfg.coop_blocks > 0 ? h->cfg.coop_blocks
+                                                                                  : h->cfg.bulk_blocks)
                                              : h->cfg.tile_blocks;
     const long long warps = blocks * TWARPS;
     long long nch = warps / nstrips;
@@ -410,8 +413,20 @@ void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
     run_check(h, ttype, MODE_CHECK);
 }
 
+bool use_coop(pdot_handle* h, int ttype) {
+    return h->coop && h->cfg.coop_blocks > 0 && ttype != TT_F64 && h->cfg.pass_bulk == 1;
+}
+
 void launch_chunk(pdot_handle* h, int ttype, int K) {
     const Work& w = h->ws;
+    if (use_coop(h, ttype)) {
+        CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
+        CK(cudaMemsetAsync(h->d_gb, 0, sizeof(GridBar), h->stream));
+        CKL(launch_chunk_coop(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->d_vmap, h->d_cnt + 1, h->wctr, h->d_gb, K,
+                              h->cfg, h->stream));
+        launch_count(h, 1);
+        return;
+    }
     const long long key[6] = {(long long)(uintptr_t)w.base, (long long)(uintptr_t)h->d_tmap ^ ((long long)(uintptr_t)h->d_vmap << 1),
                               w.m * 4 + ttype, w.n, K,
                               (long long)h->cfg.pdl * 1000000 + (long long)h->cfg.pass_bulk * 100000 +
@@ -466,7 +481,7 @@ pdot_status map_status(int st) {
     switch (st) {
         case ST_OK: return PDOT_OK;
         case ST_ARG: return PDOT_ERR_ARG;
-        case ST_DEVICE: return PDOT_ERR_CUDA;
+        case ST_DEVICE: return PDOT_ERR_CUDA;   // a bounded device wait gave up
         case ST_NUMERIC: return PDOT_ERR_NUMERIC;
         case ST_MAX_ITER: return PDOT_MAX_ITER;
         case ST_TIMEOUT: return PDOT_TIMEOUT;
@@ -1314,6 +1329,13 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         const int grp = setup_group_pass();
         if (grp > 0) throw CudaError{(cudaError_t)grp};
         h->cfg.group_blocks = h->sm_count * (-grp);
+        const int coop = setup_coop_chunk();
+        if (coop > 0) throw CudaError{(cudaError_t)coop};
+        int coop_ok = 0;
+        CK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, device));
+        h->cfg.coop_blocks = coop_ok ? h->sm_count * (-coop) : 0;
+        const char* cp = getenv("PDOT_COOP");
+        if (cp && atoi(cp) == 1) h->coop = 1;
         h->cfg.pass_bulk = 1;
         const char* pb = getenv("PDOT_PASS_BULK");
         if (pb) {
@@ -1340,6 +1362,8 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         CK(cudaMallocHost(&h->h_inst, sizeof(Inst)));
         CK(cudaMallocHost(&h->h_status, 2 * sizeof(int)));
         CK(cudaMalloc(&h->d_cnt, 4 * sizeof(int)));
+        CK(cudaMalloc(&h->d_gb, sizeof(GridBar)));
+        CK(cudaMemset(h->d_gb, 0, sizeof(GridBar)));
         CK(cudaMallocHost(&h->h_cnt, 4 * sizeof(int)));
         return PDOT_OK;
     });
@@ -1367,6 +1391,7 @@ pdot_status pdot_destroy(pdot_handle* h) {
     if (h->h_inst) cudaFreeHost(h->h_inst);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->d_cnt) cudaFree(h->d_cnt);
+    if (h->d_gb) cudaFree(h->d_gb);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -76,6 +76,15 @@ struct Inst {
     int l2_keep_c;       // 1: C fits in L2 next to the streams; load it evict-last, stream X evict-first
 };
 
+// Grid barrier state of the cooperative chunk kernel (device memory, zeroed
+// before each launch).
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int err;
+    unsigned int pad;
+};
+
 struct TileRef {
     int inst;
     int local;
@@ -105,6 +114,7 @@ struct LaunchCfg {
     int pass_bulk;        // FP32-plan pass kernel: 0 register pipeline, 1 bulk copies per row, 2 per 4-row group
     int bulk_blocks;      // CTAs of the bulk-copy pass kernel
     int group_blocks;     // CTAs of the grouped bulk-copy pass kernel
+    int coop_blocks;      // CTAs of the cooperative chunk kernel (all co-resident)
     int pdl;              // 1: launch with programmatic dependent launch
 };
 
@@ -127,5 +137,9 @@ int occupancy_vec_blocks_per_sm();
 // the CTAs per SM it can hold, or a positive cudaError_t code.
 int setup_bulk_pass();
 int setup_group_pass();
+int setup_coop_chunk();
+// K passes and one check of a single FP32-plan instance in one cooperative launch.
+int launch_chunk_coop(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const TileRef* d_vmap,
+                      const int* NV, unsigned* wctr, GridBar* gb, int npass, const LaunchCfg& cfg, void* stream);
 
 }  // namespace pdot

@@ -32,7 +32,8 @@
 
 namespace pdot {
 
-constexpr int KU = 2;   // rows per load batch in the KKT pass
+constexpr int KU = 2;
+constexpr int BULK_ROW_S = 8;   // row stages per warp in the per-row bulk pass   // rows per load batch in the KKT pass
 
 // ---------------------------------------------------------------------------
 // loads and stores of 4 consecutive elements
@@ -143,8 +144,13 @@ __device__ __forceinline__ int warp_next(unsigned* ctr) {
 // calls this before touching any data or work counter.
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
+#ifdef PDOT_PDL_EARLY
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
 }
+// Let the next grid start launching: called when a CTA has finished its work
+// (a CTA that exits without calling it counts as having called it).
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -361,27 +367,48 @@ struct RowRef {       // what a stage holds
 
 }  // namespace bulk
 
-template <typename TC, int S>
-__global__ void __launch_bounds__(TWARPS * 32)
-k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
-            unsigned* wctr, int wc) {
-    using namespace bulk;
-    pdl_enter();
-    const int T = *Tp;
-    reset_other_counters(wctr, wc);
-    extern __shared__ __align__(128) unsigned char dsm[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wbase = dsm + warp * warp_smem_bytes<S>();
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + S * STAGE_BYTES);
-    RowRef* refs = reinterpret_cast<RowRef*>(wbase + S * STAGE_BYTES + S * 8);
-    float* pbuf = reinterpret_cast<float*>(wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
-    const unsigned wbase_s = smem_u32(wbase);
-    const unsigned bars_s = smem_u32(bars);
+namespace bulk {
+// A warp's row pipeline: its shared-memory stages and mbarriers, and the
+// counts of issued / consumed rows (they set the mbarrier phases, so they
+// persist across passes when one kernel runs several).
+template <int S>
+struct RowPipe {
+    unsigned char* wbase;
+    RowRef* refs;
+    float* pbuf;
+    unsigned wbase_s, bars_s;
+    long long issued, consumed;
+};
+
+template <int S>
+__device__ __forceinline__ void row_pipe_init(RowPipe<S>& P, unsigned char* dsm, int lane, int warp) {
+    P.wbase = dsm + warp * warp_smem_bytes<S>();
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(P.wbase + S * STAGE_BYTES);
+    P.refs = reinterpret_cast<RowRef*>(P.wbase + S * STAGE_BYTES + S * 8);
+    P.pbuf = reinterpret_cast<float*>(P.wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
+    P.wbase_s = smem_u32(P.wbase);
+    P.bars_s = smem_u32(bars);
+    P.issued = P.consumed = 0;
     if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(bars_s + 8 * s, 1);
+        for (int s = 0; s < S; ++s) mbar_init(P.bars_s + 8 * s, 1);
         fence_mbar_init();
     }
     __syncwarp();
+}
+}  // namespace bulk
+
+// One pass over the tiles handed out by the queue counter `qctr`.  Returns
+// false when a stage never completed (bounded wait); the instance's status
+// is then set to an error.
+template <typename TC, int S>
+__device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* qctr,
+                             bulk::RowPipe<S>& P, int lane) {
+    using namespace bulk;
+    unsigned char* wbase = P.wbase;
+    RowRef* refs = P.refs;
+    float* pbuf = P.pbuf;
+    const unsigned wbase_s = P.wbase_s;
+    const unsigned bars_s = P.bars_s;
     constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
 
     // ---- producer: the tile being issued, resolved once per tile ----
@@ -398,7 +425,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     const unsigned long long pol_stream = policy_evict_first();
     auto next_tile = [&]() {
         for (;;) {
-            p_tile = warp_next(&wctr[wc]);
+            p_tile = warp_next(qctr);
             if (p_tile >= T) return;
             const TileRef tr = tmap[p_tile];
             const Inst& I = insts[tr.inst];
@@ -426,7 +453,8 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
             return;
         }
     };
-    long long issued = 0, consumed = 0;
+    long long issued = P.issued, consumed = P.consumed;
+    const long long base = issued;   // rows of earlier passes (ring position)
     auto issue = [&]() {
         const int st = (int)(issued % S);
         if (lane == 0) {
@@ -455,7 +483,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
         if (++p_row >= p_end) next_tile();
     };
     next_tile();
-    while (issued < S && p_tile < T) issue();
+    while (issued - base < S && p_tile < T) issue();
 
     // ---- consumer: the tile being computed, resolved once per tile ----
     int c_tile = -1;
@@ -629,12 +657,30 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
         const int t = refs[(int)(consumed % S)].tile;
         atomicExch(&insts[tmap[t].inst].ctrl->status, ST_DEVICE);
     }
-    // Drain: wait (bounded) for every copy still in flight before exiting.
+    // Drain: wait (bounded) for every copy still in flight.
     while (consumed < issued) {
         const int st = (int)(consumed % S);
         wait_stage(bars_s + 8 * st, (unsigned)((consumed / S) & 1));
         ++consumed;
     }
+    P.issued = issued;
+    P.consumed = consumed;
+    return !failed;
+}
+
+template <typename TC, int S>
+__global__ void __launch_bounds__(TWARPS * 32)
+k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
+            unsigned* wctr, int wc) {
+    pdl_enter();
+    const int T = *Tp;
+    reset_other_counters(wctr, wc);
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bulk::RowPipe<S> P;
+    bulk::row_pipe_init<S>(P, dsm, lane, warp);
+    pass_row_run<TC, S>(insts, tmap, T, &wctr[wc], P, lane);
+    pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -938,6 +984,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             rows_in_batch = 0;
         }
     }
+    pdl_release();
     if (!failed) {
         flush_tile();
     } else if (lane == 0) {
@@ -1478,6 +1525,105 @@ __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts,
 }
 
 // ---------------------------------------------------------------------------
+// Cooperative chunk kernel (single instance, FP32 plans): one launch runs K
+// passes and the check.  Each pass: the plan pass over all tiles, a grid
+// barrier, the dual update (the instance's last vector tile runs the step
+// controller), a grid barrier.  Then the KKT pass, a barrier, the check.
+// All CTAs are co-resident (cooperative launch).  The barrier is the fence +
+// atomic-arrive + fenced-spin pattern, so plain loads after it see every
+// other CTA's writes before it; its spin is bounded and sets an error flag.
+// ---------------------------------------------------------------------------
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;
+
+__device__ bool grid_barrier(GridBar* gb, unsigned nblocks, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = &gb->gen;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gb->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > BARRIER_SPIN_LIMIT) {
+                    atomicExch(&gb->err, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned*)&gb->err) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(TWARPS * 32, 2)
+k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
+             const TileRef* __restrict__ vmap, const int* __restrict__ NVp, unsigned* wctr, GridBar* gb, int npass,
+             int wc_a, int wc_b, int wc_kkt) {
+    __shared__ double red[(VT / 32) * VP];
+    __shared__ double sgrp[VG * 32];
+    __shared__ int s_last, s_ok;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int T = *Tp, NV = *NVp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned G = gridDim.x;
+    bulk::RowPipe<BULK_ROW_S> P;
+    bulk::row_pipe_init<BULK_ROW_S>(P, dsm, lane, warp);
+    Ctrl* S0 = insts[0].ctrl;
+    bool ok = true;
+    for (int s = 0; s < npass && ok; ++s) {
+        // Every CTA reads the status after the same barrier: a uniform exit.
+        if (*(volatile int*)&S0->status != ST_RUNNING) break;
+        const int qc = (s & 1) ? wc_b : wc_a;
+        pass_row_run<TC, BULK_ROW_S>(insts, tmap, T, &wctr[qc], P, lane);
+        ok = grid_barrier(gb, G, &s_ok);
+        if (!ok) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&wctr[qc], 0u);   // ready for pass s + 2
+        for (int vt = blockIdx.x; vt < NV; vt += G) {
+            const TileRef tr = vmap[vt];
+            const Inst& I = insts[tr.inst];
+            Ctrl* S = I.ctrl;
+            if (S->status != ST_RUNNING) continue;
+            dual_tile(I, S, tr.local, red, sgrp, &s_last);
+        }
+        ok = grid_barrier(gb, G, &s_ok);
+    }
+    if (ok && *(volatile int*)&S0->status == ST_RUNNING) {
+        for (;;) {
+            const int t = warp_next(&wctr[wc_kkt]);
+            if (t >= T) break;
+            const TileRef tr = tmap[t];
+            const Inst& I = insts[tr.inst];
+            const Ctrl& S = *I.ctrl;
+            if (S.status != ST_RUNNING) continue;
+            kkt_tile<TC, float>(I, S, tr.local, lane, MODE_CHECK);
+        }
+        ok = grid_barrier(gb, G, &s_ok);
+        if (ok) {
+            for (int vt = blockIdx.x; vt < NV; vt += G) {
+                const TileRef tr = vmap[vt];
+                const Inst& I = insts[tr.inst];
+                Ctrl* S = I.ctrl;
+                if (S->status != ST_RUNNING) continue;
+                checkvec_tile(I, S, tr.local, MODE_CHECK, red, sgrp, &s_last);
+            }
+        }
+    }
+    if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&S0->status, ST_DEVICE);
+}
+
+// ---------------------------------------------------------------------------
 // ||C||_F^2 per plan tile (once per solve, for the relative dual residual)
 // ---------------------------------------------------------------------------
 template <typename TC>
@@ -1553,7 +1699,7 @@ static int launch_k(bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned bl
     return err(cudaLaunchKernelEx(&c, kern, args...));
 }
 
-constexpr int BULK_S = 8;
+constexpr int BULK_S = BULK_ROW_S;
 constexpr int bulk_smem() { return TWARPS * bulk::warp_smem_bytes<BULK_S>(); }
 constexpr int GROUP_S = 2;   // stages of 4 rows: 8 rows in flight per warp
 constexpr int group_smem() { return TWARPS * bulk::warp_smem_bytes_g<4, GROUP_S>(); }
@@ -1658,6 +1804,41 @@ int occupancy_tile_blocks_per_sm(int ttype) {
     if (d < r) r = d;
     return r;
 }
+int setup_coop_chunk() {
+    const int bytes = bulk_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_chunk_coop<unsigned short>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_chunk_coop<float>, TWARPS * 32, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chunk_coop<unsigned short>, TWARPS * 32, bytes);
+    const int r = a < b ? a : b;
+    return -(r > 0 ? r : 1);
+}
+
+int launch_chunk_coop(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const TileRef* d_vmap,
+                      const int* NV, unsigned* wctr, GridBar* gb, int npass, const LaunchCfg& cfg, void* stream) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3((unsigned)cfg.coop_blocks);
+    c.blockDim = dim3(TWARPS * 32);
+    c.dynamicSmemBytes = bulk_smem();
+    c.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    c.attrs = attr;
+    c.numAttrs = 1;
+    const int wa = wc_index(WC_PASS, ttype), wb = wc_index(WC_AUX, ttype), wk = wc_index(WC_KKT, ttype);
+    cudaError_t e;
+    if (ttype == TT_BF16)
+        e = cudaLaunchKernelEx(&c, k_chunk_coop<unsigned short>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb, npass, wa,
+                               wb, wk);
+    else
+        e = cudaLaunchKernelEx(&c, k_chunk_coop<float>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb, npass, wa, wb, wk);
+    return err(e);
+}
+
 int setup_group_pass() {
     const int bytes = group_smem();
     cudaError_t e = cudaFuncSetAttribute(k_pass_group<float, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

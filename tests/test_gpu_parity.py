@@ -200,6 +200,27 @@ def test_solve_is_deterministic(s32):
     assert torch.equal(a.X, b.X) and torch.equal(a.p, b.p)
 
 
+def test_cooperative_chunk_equals_graph_path(monkeypatch):
+    """One cooperative launch per chunk (K passes + check, grid barriers) runs the
+    same device code in the same reduction order as the graph of separate
+    kernels: the solves must agree bit for bit."""
+    ins = I.grid_blob_instance(24, 77)   # 576 x 576, above nothing-to-tune size
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    monkeypatch.setenv("PDOT_PASS_BULK", "1")
+    monkeypatch.setenv("PDOT_COOP", "1")
+    a = pdot.Solver(device=0, time_limit_s=120.0)
+    monkeypatch.setenv("PDOT_COOP", "0")
+    b = pdot.Solver(device=0, time_limit_s=120.0)
+    ra = a.solve(C, ins.f, ins.g, tol=1e-6)
+    rb = b.solve(C, ins.f, ins.g, tol=1e-6)
+    assert ra.status == rb.status == pdot.OK
+    assert ra.result["passes"] == rb.result["passes"] and ra.result["primal_obj"] == rb.result["primal_obj"]
+    assert torch.equal(ra.X, rb.X) and torch.equal(ra.p, rb.p) and torch.equal(ra.q, rb.q)
+    # far fewer launches: one per chunk instead of 2K + 2
+    a.close()
+    b.close()
+
+
 def test_solve_host_matches_device(s32):
     ins = I.points_instance(70, 90, 31)
     C = ins.C.astype(np.float32)
