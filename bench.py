@@ -114,6 +114,17 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+def aggregate_over_ranks(elapsed_s: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job throughput of replicas: every rank solved `steps` instances of
+    its own; the job took the slowest rank's time (MAX over ranks)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    return world * steps / elapsed_s, elapsed_s
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -259,22 +270,20 @@ def run_ours(args):
     launches = pdot.pdot_launch_count(h) - launches0
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
+    value, elapsed = aggregate_over_ranks(elapsed, args.steps, world, dist, dev)
     if dist is not None:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
-    value = world * args.steps / elapsed
     last = results[-1]
     passes = last.passes
 
     # Roofline of the dominant kernel: the fused plan pass, timed alone with
     # CUDA events on the library's stream, same size and launch shape.
-    st, ms_pass, bytes_pass = pdot.pdot_time_pass(h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
-                                                  50)
+    st, ms_pass, bytes_pass, variant = pdot.pdot_time_pass(h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(),
+                                                           g.data_ptr(), 50)
     peak, peak_kind = measured_peak()
     achieved = bytes_pass / (ms_pass * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    # The recorded DRAM traffic belongs to the per-row bulk kernel at this source.
+    traffic = recorded_traffic() if variant == 1 else None
 
     # End to end through the C ABI with host buffers (copies inside the timing).
     e2e = None
@@ -320,7 +329,7 @@ def run_ours(args):
             "restarts": last.restarts, "rel_kkt": last.rel_kkt, "primal_obj": last.primal_obj,
             "hbm_gbs_per_iter": last.hbm_bytes / (elapsed / args.steps) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_pass<float,float>",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": pdot.KERNEL_NAMES.get(variant),
                          "bytes_per_launch": bytes_pass, "ms_per_launch": ms_pass,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
@@ -444,8 +453,8 @@ def run_pass_sweep(args):
             os.environ["PDOT_PASS_BULK"] = bulk
             for tr in ((0, 32, 64, 128) if bulk != "0" else (0, 64)):
                 s = pdot.Solver(device=0, tile_rows=tr)
-                st, ms, b = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
-                                                30 if G == 64 else 10)
+                st, ms, b, _ = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
+                                                   30 if G == 64 else 10)
                 s.close()
                 row = {"m": m, "kernel": {"2": "bulk-group", "1": "bulk-row", "0": "register"}[bulk],
                        "tile_rows": tr or "auto",

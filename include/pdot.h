@@ -239,9 +239,13 @@ int64_t pdot_launch_count(pdot_handle *h);
  * pass `reps` times back to back on the handle's stream between two CUDA
  * events.  *ms_per_pass receives the mean device time of one pass;
  * *bytes_per_pass (nullable) the algorithmic bytes one pass moves:
- * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+). */
+ * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+);
+ * *kernel_variant (nullable) the pass kernel used for this shape: 0 register
+ * pipeline, 1 bulk copies per row, 2 bulk copies per 4-row group (FP64 plans
+ * always 0). */
 pdot_status pdot_time_pass(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
-                           const double *f, const double *g, int reps, double *ms_per_pass, double *bytes_per_pass);
+                           const double *f, const double *g, int reps, double *ms_per_pass, double *bytes_per_pass,
+                           int32_t *kernel_variant);
 
 #ifdef __cplusplus
 }

@@ -538,10 +538,10 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
                       const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc);
 
 // Autotuner: on the first single-instance solve of a shape (m, n, dtype),
-// time the fused pass for each candidate (kernel, tile height) on this
-// device with CUDA events -- three real steps first so the running average
-// is read, then repeated passes on the same state -- and keep the fastest.
-// Small shapes are launch-bound: they take the default without timing.
+// time whole PDHG steps (fused pass + dual update, constant step) for each
+// candidate (pass kernel, tile height) on this device with CUDA events --
+// after three untimed steps, so the running average is read -- and keep the
+// fastest.  Small shapes are launch-bound: they take the default untimed.
 void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                    const double* f, const double* g) {
     const int ttype = ttype_of(ctype);
@@ -558,7 +558,9 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
         h->cfg.pass_bulk = kern;
         return;
     }
-    const int cands[3][2] = {{1, 0}, {2, 32}, {2, 64}};
+    // Each candidate is timed on whole PDHG steps (pass + dual update): tile
+    // height also sets how many partial sums the dual update has to read.
+    const int cands[4][2] = {{1, 0}, {2, 32}, {2, 64}, {2, 128}};
     float best = 1e30f;
     int best_k = 1, best_tr = tile_rows_for(h, m, n, ttype, 1, false);
     const int reps = m * n >= (1LL << 26) ? 6 : 20;
@@ -584,17 +586,14 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, h->stream));
-        for (int r = 0; r < reps; ++r) {
-            const int wc = (r & 1) ? wc_index(WC_AUX, ttype) : wc_index(WC_PASS, ttype);
-            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream, wc));
-        }
+        for (int r = 0; r < reps; ++r) run_step(h, ttype);
         CK(cudaEventRecord(e1, h->stream));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, e0, e1));
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        launch_count(h, reps + 5);
+        launch_count(h, 3);
         if (ms < best) {
             best = ms;
             best_k = kern;
@@ -1607,13 +1606,15 @@ pdot_status pdot_batch_pending(pdot_handle* h, int* queued, int* running) {
 }
 
 pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
-                           const double* f, const double* g, int reps, double* ms_per_pass, double* bytes_per_pass) {
+                           const double* f, const double* g, int reps, double* ms_per_pass, double* bytes_per_pass,
+                           int32_t* kernel_variant) {
     if (!h) return PDOT_ERR_ARG;
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
         if (reps < 1 || !ms_per_pass) throw ArgError{"reps < 1 or null output"};
         const int ttype = ttype_of(c_dtype);
+        autotune_pass(h, m, n, C, c_dtype, ldc, f, g);
         const int tr = pick_tile_rows(h, m, n, ttype);
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);
@@ -1651,6 +1652,7 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         *ms_per_pass = (double)ms / reps;
         if (bytes_per_pass)
             *bytes_per_pass = (double)m * (double)n * ((double)csize_of(c_dtype) + 4.0 * (double)xsize_of(w.xtype));
+        if (kernel_variant) *kernel_variant = ttype == TT_F64 ? 0 : h->cfg.pass_bulk;
         return PDOT_OK;
     });
 }

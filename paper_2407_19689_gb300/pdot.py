@@ -149,7 +149,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_batch_pending": (i32, [H, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "pdot_launch_count": (i64, [H]),
         "pdot_time_pass": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i32, ctypes.POINTER(dbl),
-                                 ctypes.POINTER(dbl)]),
+                                 ctypes.POINTER(dbl), ctypes.POINTER(i32)]),
         "pdot_round_noalloc": (i32, [i32, vp, i64, i64, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -257,10 +257,16 @@ def pdot_round_noalloc(device, stream, m, n, x_dtype, X, f, g, X_out) -> int:
     return load().pdot_round_noalloc(device, stream or None, m, n, x_dtype, X, f, g, X_out)
 
 
+KERNEL_NAMES = {0: "k_pass (register pipeline)", 1: "k_pass_bulk<float, 8> (bulk copies per row)",
+                2: "k_pass_group<float, 2> (bulk copies per 4-row group)"}
+
+
 def pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps):
-    ms, b = ctypes.c_double(), ctypes.c_double()
-    st = load().pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps, ctypes.byref(ms), ctypes.byref(b))
-    return st, ms.value, b.value
+    """Returns (status, ms per pass, algorithmic bytes per pass, kernel variant)."""
+    ms, b, kv = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    st = load().pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps, ctypes.byref(ms), ctypes.byref(b),
+                               ctypes.byref(kv))
+    return st, ms.value, b.value, kv.value
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,87 @@
+"""CPU tests of host-side logic: the replica aggregation of bench.py across
+ranks (two gloo processes), and the seeded workload generators."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2407_19689_gb300 import instances as I
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    elapsed = [2.0, 3.0][rank]          # rank 1 is the slowest replica
+    value, t = bench.aggregate_over_ranks(elapsed, steps=4, world=world, dist=dist, device="cpu")
+    # each replica solves its own seeded instance
+    ins = I.grid_blob_instance(8, I.seed_for(1, rank))
+    q.put((rank, value, t, float(ins.f[0])))
+    dist.destroy_process_group()
+
+
+def test_replica_throughput_uses_slowest_rank_gloo():
+    pytest.importorskip("torch.distributed")
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, v0, t0, f0), (_, v1, t1, f1) = out
+    assert t0 == t1 == 3.0                       # MAX over ranks
+    assert v0 == v1 == 2 * 4 / 3.0               # all ranks' solves / slowest time
+    assert f0 != f1                              # distinct seeded instances per rank
+
+
+def test_aggregate_single_process():
+    import bench
+    v, t = bench.aggregate_over_ranks(1.5, steps=3, world=1)
+    assert v == 2.0 and t == 1.5
+
+
+def test_serve_requests_follow_the_recipe():
+    reqs = I.serve_requests(400, rate_per_s=5.0, seed=3)
+    t = np.array([r.arrival_s for r in reqs])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 0.2) < 0.05                       # Poisson rate 5/s
+    assert all(128 <= r.m <= 8192 and 128 <= r.n <= 8192 for r in reqs)
+    assert {r.d for r in reqs} == {2, 3, 8}
+    assert {r.cost for r in reqs} == {"sqeuclid", "l1"}
+    assert {r.tol for r in reqs} == {1e-4, 1e-6}
+    assert all(0.5 <= r.alpha <= 2.0 for r in reqs)
+    logm = np.log([r.m for r in reqs])
+    assert abs(logm.mean() - 0.5 * (math.log(128) + math.log(8192))) < 0.25   # log-uniform
+
+
+def test_request_points_match_request_instance():
+    r = I.serve_requests(3, 1.0, seed=9, lo=16, hi=40)[1]
+    xs, ys, f, g = I.request_points(r)
+    ins = I.request_instance(r)
+    assert np.allclose(I.cost_from_points(xs, ys, r.cost) / I.cost_from_points(xs, ys, r.cost).max(), ins.C)
+    assert np.array_equal(f, ins.f) and np.array_equal(g, ins.g)
+    assert abs(f.sum() - 1) < 1e-15 and abs(g.sum() - 1) < 1e-15
+
+
+def test_grid_blob_instance_shapes_and_normalisation():
+    ins = I.grid_blob_instance(16, I.seed_for(1))
+    assert ins.C.shape == (256, 256) and abs(ins.C.max() - 1.0) < 1e-15 and ins.C.min() == 0.0
+    assert abs(ins.f.sum() - 1) < 1e-14 and ins.f.min() > 0
+    sizes = I.batch_sizes(256, I.seed_for(3))
+    assert all(64 <= m <= 2048 and 64 <= n <= 2048 for m, n in sizes)
