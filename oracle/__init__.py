@@ -66,6 +66,8 @@ def _load():
         lib.ora_solve.restype = ctypes.c_int
         lib.ora_round.argtypes = [i64, i64, d, d, d, d]
         lib.ora_exact_transport.argtypes = [i64, i64, d, d, d, d, d, d, d]
+        lib.ora_points_cost.argtypes = [i64, i64, ctypes.c_int, d, d, ctypes.c_int, ctypes.c_double, d]
+        lib.ora_points_cost.restype = ctypes.c_int
         lib.ora_exact_transport.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -262,3 +264,19 @@ def exact_transport(C, f, g):
     if rc != 0:
         raise RuntimeError(f"exact_transport failed (code {rc})")
     return obj.value, X, p, q
+
+
+POINT_DISTANCES = {"sqeuclid": 0, "l1": 1, "l2": 2, "linf": 3}
+
+
+def points_cost(xs, ys, dist: str = "sqeuclid", divisor: float = 1.0):
+    """C_ij = dist(xs_i, ys_j) / divisor in FP64 (the cost-on-the-fly input)."""
+    xs, ys = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(ys))
+    m, d = xs.shape
+    n = ys.shape[0]
+    assert ys.shape[1] == d
+    C = np.empty((m, n))
+    rc = _load().ora_points_cost(m, n, d, _p(xs), _p(ys), POINT_DISTANCES[dist], float(divisor), _p(C))
+    if rc != 0:
+        raise ValueError("points_cost: bad arguments")
+    return C

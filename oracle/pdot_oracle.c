@@ -31,6 +31,10 @@
  *   ora_exact_transport          exact optimum of Eq. (1) by successive shortest
  *                                paths with node potentials (not in the paper:
  *                                the plain definition of the LP optimum).
+ *   ora_points_cost              C_ij = dist(x_i, y_j) / divisor for the
+ *                                distances the paper's grid costs use (Sec. 5.1:
+ *                                l1, l2, l_inf; squared l2 for the squared grid
+ *                                distance), the input of cost-on-the-fly solves.
  *
  * Readings of passages the paper leaves open are listed beside the code that
  * takes them (C1..C16 in the project notes use the same numbering).
@@ -560,4 +564,30 @@ int ora_exact_transport(int64_t m, int64_t n, const double *C, const double *f, 
     *obj = o;
     free(pi); free(dist); free(prev); free(done); free(sup); free(dem);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cost matrix from point coordinates (Sec. 5.1 defines the grid costs as      */
+/* distances between pixel coordinates).  xs is m x d, ys is n x d, row-major. */
+/* kind: 0 squared Euclidean, 1 l1, 2 l2 (Euclidean), 3 l_inf.                 */
+/* C_ij = dist(x_i, y_j) / divisor, every step in FP64.                        */
+/* ------------------------------------------------------------------------- */
+int ora_points_cost(int64_t m, int64_t n, int d, const double *xs, const double *ys, int kind, double divisor,
+                    double *C)
+{
+    if (d < 1 || kind < 0 || kind > 3 || !(divisor > 0.0)) return ORA_ERR_ARG;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double t = xs[i * d + k] - ys[j * d + k];
+                if (kind == 0 || kind == 2) acc += t * t;
+                else if (kind == 1) acc += fabs(t);
+                else if (fabs(t) > acc) acc = fabs(t);
+            }
+            if (kind == 2) acc = sqrt(acc);
+            C[i * n + j] = acc / divisor;
+        }
+    }
+    return ORA_OK;
 }

@@ -304,3 +304,40 @@ def test_rounding_keeps_feasible_plan(ora):
     ins = I.points_instance(6, 9, 141)
     obj, X, p, q = ora.exact_transport(ins.C, ins.f, ins.g)
     np.testing.assert_allclose(ora.round_plan(X, ins.f, ins.g), X, atol=1e-16)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.1: costs defined from point (pixel) coordinates
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [1, 2, 3, 8])
+def test_points_cost_matches_scipy_cdist(ora, d):
+    """The cost-on-the-fly input, C_ij = dist(x_i, y_j) / divisor, against
+    scipy's pairwise-distance routine for each distance the paper uses."""
+    cdist = pytest.importorskip("scipy.spatial.distance").cdist
+    rng = np.random.default_rng(100 + d)
+    xs, ys = rng.random((13, d)), rng.random((9, d))
+    for dist, metric in [("sqeuclid", "sqeuclidean"), ("l1", "cityblock"), ("l2", "euclidean"),
+                         ("linf", "chebyshev")]:
+        np.testing.assert_allclose(ora.points_cost(xs, ys, dist, 3.0), cdist(xs, ys, metric) / 3.0,
+                                   rtol=1e-14, atol=1e-16)
+
+
+def test_points_cost_grid_invariants(ora):
+    """Pixel grid against itself: symmetric, zero diagonal, integer squared
+    distances before scaling, and l_inf <= l2 <= l1 <= d l_inf, sqeuclid = l2^2."""
+    G = 6
+    P = np.array([(a, b) for a in range(G) for b in range(G)], dtype=np.float64)
+    sq = ora.points_cost(P, P, "sqeuclid")
+    l1, l2, li = (ora.points_cost(P, P, k) for k in ("l1", "l2", "linf"))
+    assert np.array_equal(sq, sq.T) and not np.any(np.diag(sq))
+    assert np.array_equal(sq, np.round(sq)) and sq.max() == 2 * (G - 1) ** 2
+    assert np.all(li <= l2 + 1e-15) and np.all(l2 <= l1 + 1e-15) and np.all(l1 <= 2 * li + 1e-15)
+    np.testing.assert_allclose(l2 ** 2, sq, rtol=1e-14, atol=1e-14)
+    # the corner-to-corner distances
+    assert l1[0, -1] == 2 * (G - 1) and li[0, -1] == G - 1
+
+
+def test_points_cost_rejects_bad_arguments(ora):
+    with pytest.raises(ValueError):
+        ora.points_cost(np.zeros((2, 2)), np.zeros((2, 2)), "l1", 0.0)
