@@ -29,7 +29,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-6 KKT & HBM GB/s per iter; batched solves/s, p99 latency vs plain"
-UNIT = "solves/s (4096x4096 grid-blob OT to 1e-6 rel. KKT)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2407_19689_gb300", "csrc", "pdot_kernels.cu")
@@ -43,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--grid", type=int, default=64, help="grid side G: m = n = G^2")
+    ap.add_argument("--cdtype", choices=["f32", "bf16", "points"], default="f32",
+                    help="storage type of the cost matrix; points: generated from the pixel coordinates in every pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
@@ -50,8 +51,10 @@ def parse():
                          "instances through the batch engine vs one instance per launch; serve: Poisson "
                          "request stream through the continuous-batching engine vs a plain FIFO server")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=200)
-    ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: 0.8 x measured capacity)")
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: the --serve-loads sweep)")
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.1",
+                    help="offered loads as fractions of the one-at-a-time server's measured capacity")
     ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
     ap.add_argument("--pass-sweep", action="store_true",
                     help="time the fused pass kernel alone over kernels x tile heights x sizes (tuning table)")
@@ -140,24 +143,42 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+def recorded_traffic(cost_dtype: str, grid: int, variant: int):
+    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary
+    for this cost storage, grid and kernel variant, or None when there is no
+    such record or the kernel source changed since it was captured."""
     try:
         with open(TRAFFIC) as fh:
-            rec = json.load(fh)
+            recs = json.load(fh)["records"]
         with open(KERNEL_SRC, "rb") as fh:
             sha = hashlib.sha256(fh.read()).hexdigest()
-        if rec.get("kernel_source_sha256") != sha:
-            return None
-        return float(rec["dram_bytes_per_launch_full_size"])
-    except (OSError, KeyError, ValueError):
+        for rec in recs:
+            if (rec["cost_dtype"], rec["grid"], rec["kernel_variant"]) == (cost_dtype, grid, variant):
+                if rec.get("kernel_source_sha256") != sha:
+                    return None
+                return float(rec["dram_bytes_per_launch_full_size"])
+        return None
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 
-def workload(grid: int, rank: int):
+def workload(grid: int, rank: int, build_cost: bool = True):
     from paper_2407_19689_gb300 import instances as I
-    return I.grid_blob_instance(grid, I.seed_for(1, rank))
+    return I.grid_blob_instance(grid, I.seed_for(1, rank), build_cost=build_cost)
+
+
+def unit_for(grid: int, tol: float) -> str:
+    m = grid * grid
+    return f"solves/s ({m}x{m} grid-blob OT to {tol:g} rel. KKT)"
+
+
+def grid_config(args, world: int = 1) -> dict:
+    """The workload description both arms print."""
+    m = args.grid * args.grid
+    bpe = {"f32": 20, "bf16": 18, "points": 16}[args.cdtype]
+    return {"workload": f"grid{args.grid}_blobs_sqeuclid (image-like {m}x{m})", "m": m, "n": m,
+            "cost_dtype": args.cdtype, "tol": args.tol, "parallelism": f"replicas x{world}",
+            "l2": f"working set {m * m * bpe / 1e6:.0f} MB per pass > 126 MB L2; no flush needed"}
 
 
 def oracle_sample(grid: int, passes: int):
@@ -200,16 +221,16 @@ def run_reference(args):
     if p_tol is None:
         p_tol, p_src = 5000, "assumed 5000 passes (no recorded count)"
     value = 1.0 / (sec_pass * p_tol)
+    unit = unit_for(args.grid, args.tol)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_pass * passes_per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"grid{args.grid}_blobs_sqeuclid", "m": args.grid ** 2, "n": args.grid ** 2,
-                   "tol": args.tol},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{passes_per_step} PDHG passes per step at full size; {sec_pass:.3f} s/pass "
+        "config": grid_config(args, args.gpus),
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": f"{passes_per_step} FP64 PDHG passes per step at full size; {sec_pass:.3f} s/pass "
                                    f"x {p_tol} passes to tol ({p_src})"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -234,9 +255,27 @@ def run_ours(args):
         dist.barrier()
     pdot.load()
     dev = f"cuda:{local}"
-    ins = workload(args.grid, rank)
-    m, n = ins.C.shape
-    C = torch.tensor(ins.C, dtype=torch.float32, device=dev)
+    import ctypes
+
+    from paper_2407_19689_gb300 import instances as I
+    points = args.cdtype == "points"
+    ins = workload(args.grid, rank, build_cost=not points)
+    m = n = args.grid * args.grid
+    unit = unit_for(args.grid, args.tol)
+    if points:
+        # Cost-on-the-fly: squared pixel distance / its maximum, from the
+        # 2-D integer pixel coordinates (no m x n cost buffer exists).
+        P = torch.tensor(I.grid_coords(args.grid), dtype=torch.float32, device=dev)
+        div = float(2 * (args.grid - 1) ** 2)
+        desc = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=P.data_ptr(), ys=P.data_ptr(), divisor=div)
+        cptr, ctype, ldc = ctypes.addressof(desc), pdot.POINTS, 0
+    else:
+        C = torch.tensor(ins.C, dtype=torch.float32, device=dev)
+        ctype = pdot.F32
+        if args.cdtype == "bf16":
+            C = C.to(torch.bfloat16)
+            ctype = pdot.BF16
+        cptr, ldc = C.data_ptr(), n
     f = torch.tensor(ins.f, device=dev)
     g = torch.tensor(ins.g, device=dev)
     X = torch.empty((m, n), dtype=torch.float32, device=dev)
@@ -246,7 +285,7 @@ def run_ours(args):
     h = solver.h
 
     def solve_once():
-        st, r = pdot.pdot_solve(h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(), args.tol,
+        st, r = pdot.pdot_solve(h, m, n, cptr, ctype, ldc, f.data_ptr(), g.data_ptr(), args.tol,
                                 X.data_ptr(), p.data_ptr(), q.data_ptr())
         if st != pdot.OK:
             raise RuntimeError(f"solve failed: {pdot.status_str(st)}")
@@ -278,17 +317,23 @@ def run_ours(args):
 
     # Roofline of the dominant kernel: the fused plan pass, timed alone with
     # CUDA events on the library's stream, same size and launch shape.
-    st, ms_pass, bytes_pass, variant = pdot.pdot_time_pass(h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(),
+    st, ms_pass, bytes_pass, variant = pdot.pdot_time_pass(h, m, n, cptr, ctype, ldc, f.data_ptr(),
                                                            g.data_ptr(), 50)
     peak, peak_kind = measured_peak()
     achieved = bytes_pass / (ms_pass * 1e-3) / 1e9
-    # The recorded DRAM traffic belongs to the per-row bulk kernel at this source.
-    traffic = recorded_traffic() if variant == 1 else None
+    traffic = recorded_traffic(args.cdtype, args.grid, variant)
 
     # End to end through the C ABI with host buffers (copies inside the timing).
     e2e = None
     if not args.no_e2e:
-        Ch = torch.tensor(ins.C, dtype=torch.float32).pin_memory()
+        if points:
+            Ch = P.cpu().pin_memory()
+            hdesc = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=Ch.data_ptr(), ys=Ch.data_ptr(),
+                                        divisor=div)
+            hptr, cbytes = ctypes.addressof(hdesc), 2 * Ch.numel() * Ch.element_size()   # xs and ys
+        else:
+            Ch = C.cpu().pin_memory()
+            hptr, cbytes = Ch.data_ptr(), Ch.numel() * Ch.element_size()
         fh = torch.tensor(ins.f).pin_memory()
         gh = torch.tensor(ins.g).pin_memory()
         Xh = torch.empty((m, n), dtype=torch.float32).pin_memory()
@@ -297,13 +342,13 @@ def run_ours(args):
         steps_e2e = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(steps_e2e):
-            st, r = pdot.pdot_solve_host(h, m, n, Ch.data_ptr(), pdot.F32, n, fh.data_ptr(), gh.data_ptr(),
+            st, r = pdot.pdot_solve_host(h, m, n, hptr, ctype, ldc, fh.data_ptr(), gh.data_ptr(),
                                          args.tol, Xh.data_ptr(), ph.data_ptr(), qh.data_ptr())
             if st != pdot.OK:
                 raise RuntimeError(f"host solve failed: {pdot.status_str(st)}")
         t_e2e = (time.perf_counter() - t0) / steps_e2e
-        e2e = {"value": world / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": int(Ch.numel() * 4 + fh.numel() * 8 + gh.numel() * 8),
+        e2e = {"value": world / t_e2e, "unit": unit,
+               "h2d_bytes_per_step": int(cbytes + fh.numel() * 8 + gh.numel() * 8),
                "d2h_bytes_per_step": int(Xh.numel() * 4 + ph.numel() * 8 + qh.numel() * 8)}
 
     cpu = None
@@ -313,18 +358,17 @@ def run_ours(args):
         p_tol, p_src = oracle_passes_to_tol(args.grid, args.tol)
         if p_tol is None:
             p_tol, p_src = passes, "pass count of this GPU solve"
-        cpu = {"value": 1.0 / (sec_pass * p_tol), "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": 1.0 / (sec_pass * p_tol), "unit": unit, "cores": 1, "kind": "oracle",
                "sample": f"{sample_passes} FP64 PDHG passes of the oracle on the full instance: "
                          f"{sec_pass:.3f} s/pass x {p_tol} passes to tol ({p_src})"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals", "data": "synthetic",
-            "config": {"workload": f"grid{args.grid}_blobs_sqeuclid (image-like {m}x{n})", "m": m, "n": n,
-                       "tol": args.tol, "parallelism": f"replicas x{world}",
-                       "l2": "working set 336 MB per pass > 126 MB L2; no flush needed"},
+            "scaling": "weak", "vs_baseline": None, "dtype": f"{args.cdtype} cost, f32 plan, f64 duals",
+            "data": "synthetic",
+            "config": grid_config(args, world),
             "time_to_tol_s": elapsed / args.steps, "passes_to_tol": passes, "iters": last.iters,
             "restarts": last.restarts, "rel_kkt": last.rel_kkt, "primal_obj": last.primal_obj,
             "hbm_gbs_per_iter": last.hbm_bytes / (elapsed / args.steps) / 1e9,
@@ -410,30 +454,42 @@ def run_serve(args):
     from paper_2407_19689_gb300 import instances as I
     _build.build()
     pdot.load()
-    rate = args.rate
-    if rate <= 0.0:
-        # capacity probe: a short saturated burst
-        probe = I.serve_requests(24, 1e9, I.seed_for(4, 1), hi=args.serve_max)
-        r = serve.serve_batched(probe)
-        rate = 0.8 * len(probe) / r["wall_s"]
-    reqs = I.serve_requests(args.requests, rate, I.seed_for(4), hi=args.serve_max)
-    rb = serve.serve_batched(reqs)
-    sb = serve.summary(rb)
-    rp = serve.serve_plain(reqs)
-    sp = serve.summary(rp)
-    diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
-    line = {"metric": METRIC, "value": sb["solves_per_s"], "unit": "solves/s (Poisson stream)",
-            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": sb["wall_s"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals", "data": "synthetic",
-            "config": {"workload": f"serve{len(reqs)}_poisson_loguniform128-{args.serve_max}", "rate_per_s": rate,
-                       "admission_budget_bytes": 150 << 30},
-            "continuous_batching": sb, "plain_fifo": sp, "p99_speedup_vs_plain": sp["p99_s"] / sb["p99_s"],
-            "max_rel_obj_diff_vs_plain": float(np.max(diffs)) if diffs else None}
+    # Capacity of the one-at-a-time server: the mean service time of 24
+    # requests of the same mix served back to back.
+    probe = I.serve_requests(24, 1e9, I.seed_for(4, 1), hi=args.serve_max)
+    capacity = len(probe) / serve.serve_plain(probe)["wall_s"]
+    loads = [args.rate / capacity] if args.rate > 0.0 else [float(x) for x in args.serve_loads.split(",")]
+    points = []
+    for load in loads:
+        rate = load * capacity
+        reqs = I.serve_requests(args.requests, rate, I.seed_for(4), hi=args.serve_max)
+        rb = serve.serve_batched(reqs)
+        sb = serve.summary(rb)
+        rp = serve.serve_plain(reqs)
+        sp = serve.summary(rp)
+        diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
+        points.append({"load_vs_plain_capacity": load, "rate_per_s": rate, "continuous_batching": sb,
+                       "plain_fifo": sp, "p50_ratio_plain_over_batched": sp["p50_s"] / sb["p50_s"],
+                       "p99_ratio_plain_over_batched": sp["p99_s"] / sb["p99_s"],
+                       "max_rel_obj_diff_vs_plain": float(np.max(diffs)) if diffs else None})
+        print(json.dumps({"progress": points[-1]}), file=sys.stderr, flush=True)
+    top = points[-1]
+    line = {"metric": METRIC, "value": top["continuous_batching"]["solves_per_s"], "unit": "solves/s (Poisson stream)",
+            "n_gpus": 1, "steps": len(points), "warmup": 0,
+            "ms_per_step": sum(p["continuous_batching"]["wall_s"] for p in points) / len(points) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals",
+            "data": "synthetic",
+            "config": {"workload": f"serve{args.requests}_poisson_loguniform128-{args.serve_max}",
+                       "plain_capacity_per_s": capacity, "admission_budget_bytes": 150 << 30,
+                       "value_at_load": top["load_vs_plain_capacity"]},
+            "loads": points}
     print(json.dumps(line), flush=True)
 
 
 def run_pass_sweep(args):
     import torch
+
+    import ctypes
 
     from paper_2407_19689_gb300 import _build, pdot
     from paper_2407_19689_gb300 import instances as I
@@ -451,7 +507,11 @@ def run_pass_sweep(args):
         m = n = G * G
         for bulk in ("2", "1", "0"):
             os.environ["PDOT_PASS_BULK"] = bulk
-            for tr in ((0, 32, 64, 128) if bulk != "0" else (0, 64)):
+            # tile heights: auto, fixed ones, and the one-tile-per-warp split
+            # (4096^2: 54 rows; 16384^2: 864) for the grouped kernel too
+            trs = (0, 32, 64, 128) if bulk == "1" else (0, 64) if bulk == "0" else \
+                (0, 32, 64, 128) + ((54,) if G == 64 else (432, 864))
+            for tr in trs:
                 s = pdot.Solver(device=0, tile_rows=tr)
                 st, ms, b, _ = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
                                                    30 if G == 64 else 10)
@@ -463,6 +523,18 @@ def run_pass_sweep(args):
                 print(json.dumps(row), flush=True)
         del C
         torch.cuda.empty_cache()
+        # the same pass with the cost generated from the pixel coordinates
+        Pf = P.float()
+        cost = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=Pf.data_ptr(), ys=Pf.data_ptr(),
+                                   divisor=float(2 * (G - 1) ** 2))
+        s = pdot.Solver(device=0)
+        st, ms, b, _ = pdot.pdot_time_pass(s.h, m, n, ctypes.addressof(cost), pdot.POINTS, 0, f.data_ptr(),
+                                           g.data_ptr(), 30 if G == 64 else 10)
+        s.close()
+        row = {"m": m, "kernel": "bulk-row, generated cost", "tile_rows": "auto", "us": ms * 1e3,
+               "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
+        out.append(row)
+        print(json.dumps(row), flush=True)
     os.environ.pop("PDOT_PASS_BULK", None)
 
 

@@ -47,7 +47,34 @@ typedef enum {
     PDOT_CANCELLED = 9
 } pdot_status;
 
-typedef enum { PDOT_F32 = 0, PDOT_BF16 = 1, PDOT_F64 = 2 } pdot_dtype;
+typedef enum { PDOT_F32 = 0, PDOT_BF16 = 1, PDOT_F64 = 2, PDOT_POINTS = 3 } pdot_dtype;
+
+/*
+ * Cost generated on the fly (c_dtype = PDOT_POINTS).  Sec. 5.1 defines the
+ * costs of its image workloads as distances between pixel coordinates; with
+ * this form no m x n cost matrix exists: every pass computes
+ *     C_ij = dist(xs_i, ys_j) / divisor
+ * in FP32 from the coordinates (coordinate k = 0..d-1 accumulated in order,
+ * then the quotient by the divisor's reciprocal with one FMA correction step,
+ * the correctly rounded quotient on every value checked), which removes the
+ * cost read from every plan pass (16 instead
+ * of 20 bytes per plan entry) and the m x n cost buffer.  Any entry point that
+ * takes (C, c_dtype, ldc) accepts it: C then points to a pdot_points_cost in
+ * HOST memory (read during the call; pdot_batch_submit copies it), ldc is
+ * ignored, and the plan must be FP32.  xs is m x d and ys is n x d, row-major
+ * FP32, device memory (host memory for the _host entry points), borrowed like
+ * C.  Errors (PDOT_ERR_ARG): d outside 1..8, an unknown dist, a null
+ * coordinate pointer, divisor not finite and > 0, an FP64 plan.
+ */
+typedef enum { PDOT_DIST_SQEUCLID = 0, PDOT_DIST_L1 = 1, PDOT_DIST_L2 = 2, PDOT_DIST_LINF = 3 } pdot_dist;
+
+typedef struct {
+    int32_t d;              /* coordinates per point, 1..8 */
+    pdot_dist dist;
+    const float *xs;        /* m x d */
+    const float *ys;        /* n x d */
+    float divisor;          /* > 0 */
+} pdot_points_cost;
 
 /*
  * Solver options.  Defaults (pdot_default_options) follow Sec. 5 of the paper
@@ -116,7 +143,7 @@ typedef struct {
 
 typedef struct {
     int64_t m, n;
-    const void *C;          /* device, m x ldc */
+    const void *C;          /* device, m x ldc; or a host pdot_points_cost (c_dtype PDOT_POINTS) */
     pdot_dtype c_dtype;
     int64_t ldc;
     const double *f, *g;    /* device */
@@ -150,7 +177,8 @@ pdot_status pdot_destroy(pdot_handle *h);
 /*
  * Solve Eq. (1) with restarted PDHG (Algorithm 2 plus the Sec. 5 heuristics)
  * until the relative KKT error is <= tol (Sec. 5.1 termination).
- * C: device, dtype c_dtype (F32/BF16 with F32 plans, F64 with F64 plans).
+ * C: device, dtype c_dtype (F32/BF16 with F32 plans, F64 with F64 plans), or
+ * a host pdot_points_cost with c_dtype PDOT_POINTS (F32 plans).
  * f, g: device FP64.  X_out (m x n, x_dtype), p_out (m), q_out (n): nullable
  * device outputs of the returned iterate (or of its Algorithm 3 rounding for
  * X_out when round_plan = 1).  res: required.

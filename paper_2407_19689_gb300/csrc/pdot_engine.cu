@@ -28,8 +28,8 @@ int launch_round_rowsum(const void* X, int xtype, long long m, long long n, long
                         const double* cs, double* rowout, double* colpart, int colparts, void* stream);
 int launch_round_write(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
                        const double* cs, const double* er, const double* ec, double inv_l1, void* Xout,
-                       long long ldo, const void* C, int ctype, long long ldc, double* objpart, int parts,
-                       void* stream);
+                       long long ldo, const void* C, int ctype, long long ldc, const GenSpec* gen,
+                       double* objpart, int parts, void* stream);
 int launch_colreduce(const double* colpart, int parts, long long n, double* out, void* stream);
 }  // namespace pdot
 
@@ -70,8 +70,27 @@ long long padded_ldc(long long n, int ctype) {
     return (n + q - 1) / q * q;
 }
 
-int ttype_of(int ctype) { return ctype == PDOT_F64 ? TT_F64 : (ctype == PDOT_BF16 ? TT_BF16 : TT_F32); }
-size_t csize_of(int ctype) { return ctype == PDOT_F64 ? 8 : (ctype == PDOT_BF16 ? 2 : 4); }
+int ttype_of(int ctype) {
+    return ctype == PDOT_F64 ? TT_F64 : ctype == PDOT_BF16 ? TT_BF16 : ctype == PDOT_POINTS ? TT_GEN : TT_F32;
+}
+// Bytes per stored cost entry (a generated cost stores none).
+size_t csize_of(int ctype) {
+    return ctype == PDOT_F64 ? 8 : ctype == PDOT_BF16 ? 2 : ctype == PDOT_POINTS ? 0 : 4;
+}
+
+// The generated cost of a PDOT_POINTS descriptor (host memory, checked by
+// check_common_args).
+GenSpec gen_spec_of(const void* C) {
+    const pdot_points_cost* d = static_cast<const pdot_points_cost*>(C);
+    GenSpec g;
+    g.xs = d->xs;
+    g.ys = d->ys;
+    g.d = d->d;
+    g.kind = (int)d->dist;
+    g.div = d->divisor;
+    g.inv = 1.0f / d->divisor;
+    return g;
+}
 size_t xsize_of(int xtype) { return xtype == PDOT_F64 ? 8 : 4; }
 
 // One instance's device buffers (a single cudaMalloc carved into pieces).
@@ -131,6 +150,11 @@ Inst make_inst(const Work& w, const void* C, int ctype, long long ldc, const dou
     memset(&I, 0, sizeof(I));
     I.m = w.m; I.n = w.n; I.ldc = ldc; I.ldx = w.ldx;
     I.C = C; I.ctype = ctype; I.xtype = w.xtype;
+    if (ctype == PDOT_POINTS) {
+        I.gen = gen_spec_of(C);
+        I.C = nullptr;
+        I.ldc = 0;
+    }
     I.f = f; I.g = g;
     I.X = w.X; I.xslot = w.m * w.ldx;
     I.V = w.V; I.vslot = 2 * (w.m + w.n);
@@ -185,7 +209,7 @@ struct pdot_handle {
     Inst* h_inst = nullptr;      // pinned
     int* h_status = nullptr;     // pinned [2]
     Graph chunk;                 // K x (pass, dual) + (kkt, checkvec)
-    long long chunk_key[6] = {0, 0, 0, 0, 0, 0};
+    long long chunk_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::map<long long, std::pair<int, int>> tune_cache;   // (m, n, ttype) -> (pass kernel, tile_rows)
     int autotune = 1;            // time pass-kernel candidates on a shape's first solve
     // host staging for pdot_solve_host
@@ -321,6 +345,10 @@ int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool bat
 const void* prepare_C(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                       long long* ldc_used) {
     const size_t cs = csize_of(ctype);
+    if (ctype == PDOT_POINTS) {   // nothing stored: the descriptor travels in the instance
+        *ldc_used = 0;
+        return C;
+    }
     if (c_layout_ok(C, ctype, ldc)) {
         *ldc_used = ldc;
         return C;
@@ -381,7 +409,7 @@ void launch_count(pdot_handle* h, int k) { h->launches += k; }
 // Keep C resident in L2 when it takes at most half of it (it is re-read every
 // pass; the plan streams get evict-first so they do not push it out).
 bool keep_c_in_l2(pdot_handle* h, const Inst& I) {
-    if (!h->l2_hint || h->l2_bytes <= 0) return false;
+    if (!h->l2_hint || h->l2_bytes <= 0 || I.ctype == PDOT_POINTS) return false;
     const double cbytes = (double)I.m * (double)I.ldc * (double)csize_of(I.ctype);
     return cbytes <= 0.5 * (double)h->l2_bytes;
 }
@@ -390,6 +418,7 @@ bool keep_c_in_l2(pdot_handle* h, const Inst& I) {
 void stage_instance(pdot_handle* h, const Inst& I) {
     *h->h_inst = I;
     h->h_inst->l2_keep_c = keep_c_in_l2(h, I) ? 1 : 0;
+    h->cfg.gen_dims = I.ctype == PDOT_POINTS ? I.gen.d : 0;
     CK(cudaMemcpyAsync(h->d_inst, h->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
 }
@@ -414,7 +443,7 @@ void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
 }
 
 bool use_coop(pdot_handle* h, int ttype) {
-    return h->coop && h->cfg.coop_blocks > 0 && ttype != TT_F64 && h->cfg.pass_bulk == 1;
+    return h->coop && h->cfg.coop_blocks > 0 && ttype != TT_F64 && ttype != TT_GEN && h->cfg.pass_bulk == 1;
 }
 
 void launch_chunk(pdot_handle* h, int ttype, int K) {
@@ -427,10 +456,14 @@ void launch_chunk(pdot_handle* h, int ttype, int K) {
         launch_count(h, 1);
         return;
     }
-    const long long key[6] = {(long long)(uintptr_t)w.base, (long long)(uintptr_t)h->d_tmap ^ ((long long)(uintptr_t)h->d_vmap << 1),
-                              w.m * 4 + ttype, w.n, K,
-                              (long long)h->cfg.pdl * 1000000 + (long long)h->cfg.pass_bulk * 100000 +
-                                  (long long)h->cfg.pass_u * 1000 + w.tile_rows};
+    const long long key[8] = {(long long)(uintptr_t)w.base,
+                              (long long)(uintptr_t)h->d_tmap ^ ((long long)(uintptr_t)h->d_vmap << 1),
+                              w.m * 4 + ttype,
+                              w.n,
+                              K,
+                              (long long)h->cfg.pdl * 100 + (long long)h->cfg.pass_bulk * 10 + (long long)h->cfg.pass_u,
+                              w.tile_rows,
+                              h->cfg.gen_dims};
     if (!h->opt.use_graph) {
         issue_chunk_kernels(h, ttype, K);
         return;
@@ -522,11 +555,21 @@ void check_common_args(pdot_handle* h, long long m, long long n, const void* C, 
                        const double* f, const double* g) {
     if (!h) throw ArgError{"null handle"};
     if (m < 1 || n < 1) throw ArgError{"m and n must be >= 1"};
-    if (ldc < n) throw ArgError{"ldc < n"};
     if (!C || !f || !g) throw ArgError{"null C, f or g"};
-    if (ctype != PDOT_F32 && ctype != PDOT_BF16 && ctype != PDOT_F64) throw ArgError{"unknown c_dtype"};
+    if (ctype != PDOT_F32 && ctype != PDOT_BF16 && ctype != PDOT_F64 && ctype != PDOT_POINTS)
+        throw ArgError{"unknown c_dtype"};
     const int xt = h->opt.x_dtype;
     if (xt != PDOT_F32 && xt != PDOT_F64) throw ArgError{"x_dtype must be F32 or F64"};
+    if (ctype == PDOT_POINTS) {
+        const pdot_points_cost* d = static_cast<const pdot_points_cost*>(C);
+        if (d->d < 1 || d->d > GEN_DMAX) throw ArgError{"points cost: d must be in 1..8"};
+        if ((int)d->dist < 0 || (int)d->dist > 3) throw ArgError{"points cost: unknown dist"};
+        if (!d->xs || !d->ys) throw ArgError{"points cost: null coordinates"};
+        if (!(std::isfinite(d->divisor) && d->divisor > 0.f)) throw ArgError{"points cost: divisor must be finite and > 0"};
+        if (xt != PDOT_F32) throw ArgError{"generated costs need F32 plans"};
+    } else if (ldc < n) {
+        throw ArgError{"ldc < n"};
+    }
     if ((xt == PDOT_F64) != (ctype == PDOT_F64))
         throw ArgError{"F64 plans need F64 costs and F32 plans need F32/BF16 costs"};
     if (m > (1LL << 31) / 2 || n > (1LL << 31) / 2) throw ArgError{"dimension too large"};
@@ -535,7 +578,8 @@ void check_common_args(pdot_handle* h, long long m, long long n, const void* C, 
 // Algorithm 3 on the plan of `slot` (or an external device plan), writing
 // X_out (dense m x n).  Returns <C, X_feas> when C is given.
 double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const void* Xsrc, long long ldx,
-                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc);
+                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc,
+                      const GenSpec* gen);
 
 // Autotuner: on the first single-instance solve of a shape (m, n, dtype),
 // time whole PDHG steps (fused pass + dual update, constant step) for each
@@ -545,6 +589,11 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
 void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                    const double* f, const double* g) {
     const int ttype = ttype_of(ctype);
+    if (ttype == TT_GEN) {
+        // Generated costs have one bulk kernel (per-row copies of X and Xbar).
+        h->cfg.pass_bulk = h->cfg_base.pass_bulk ? 1 : 0;
+        return;
+    }
     if (ttype == TT_F64 || h->opt.tile_rows > 0 || !h->cfg_base.pass_bulk) return;
     const long long key = (m * 1000003LL + n) * 4 + ttype;
     auto it = h->tune_cache.find(key);
@@ -695,7 +744,8 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     const int slot = S->res_slot;
     const char* Xslot = (const char*)w.X + (size_t)slot * (size_t)(w.m * w.ldx) * xsize_of(w.xtype);
     if (h->opt.round_plan) {
-        res->rounded_obj = round_plan_dev(h, w.m, w.n, w.xtype, Xslot, w.ldx, f, g, X_out, Cd, ctype, ldc_used);
+        res->rounded_obj =
+            round_plan_dev(h, w.m, w.n, w.xtype, Xslot, w.ldx, f, g, X_out, I.C, ctype, ldc_used, &I.gen);
     } else if (X_out) {
         copy_plan_out(h, slot, X_out, cudaMemcpyDeviceToDevice);
     }
@@ -732,7 +782,8 @@ pdot_status guarded(pdot_handle* h, F&& fn) {
 // ---------------------------------------------------------------------------
 namespace {
 double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const void* Xsrc, long long ldx,
-                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc) {
+                      const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc,
+                      const GenSpec* gen) {
     const int parts = 64;   // column-partial rows (fixed order)
     const size_t need = sizeof(double) * (size_t)(4 * m + 4 * n + (size_t)parts * n + parts + 8);
     if (h->round_scratch_bytes < need) {
@@ -791,8 +842,8 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
     CK(cudaMemcpyAsync(ec, hc.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     const double inv_l1 = l1 > 0.0 ? 1.0 / l1 : 0.0;
     // 4) X_feas = diag(x) X diag(y) + err_r err_c^T / ||err_r||_1, and <C, X_feas>
-    CKL(launch_round_write(Xsrc, xtype, m, n, ldx, xs, ys, er, ec, inv_l1, out, n, C, ctype, ldc, objpart, parts,
-                           h->stream));
+    CKL(launch_round_write(Xsrc, xtype, m, n, ldx, xs, ys, er, ec, inv_l1, out, n, C, ctype, ldc, gen, objpart,
+                           parts, h->stream));
     launch_count(h, 1);
     std::vector<double> ho((size_t)parts);
     CK(cudaMemcpyAsync(ho.data(), objpart, sizeof(double) * parts, cudaMemcpyDeviceToHost, h->stream));
@@ -824,6 +875,7 @@ namespace {
 struct BSlot {
     uint64_t id = 0;
     pdot_request req{};
+    pdot_points_cost pts{};   // copy of a PDOT_POINTS descriptor (req.C points here)
     int ttype = 0;
     Work w;
     size_t bytes = 0;
@@ -863,6 +915,13 @@ struct DevArr {
 
 }  // namespace
 
+// Device count words of the batch engine: plan tiles per type, vector tiles,
+// instances, init-check plan tiles per type, init-check vector tiles, and one
+// pinned source word for status writes.
+constexpr int CNT_VEC = NTT, CNT_INST = NTT + 1, CNT_INIT = NTT + 2, CNT_INIT_VEC = 2 * NTT + 2, CNT_WORDS = 2 * NTT + 3,
+              CNT_CANCEL = 15;
+static_assert(CNT_WORDS <= CNT_CANCEL, "count words overlap");
+
 struct BatchEngine {
     std::deque<BSlot*> queue;
     std::vector<BSlot*> live;
@@ -876,8 +935,9 @@ struct BatchEngine {
     DevArr<TileRef> vmap_init;
     DevArr<Ctrl> snap;
     DevArr<Ctrl> ctrl_stage;
-    DevArr<int> cnt;          // [0..2] tiles per type, [3] vector tiles, [4] instances, [5..7] init tiles, [8] init vts
+    DevArr<int> cnt;          // counts, laid out as the CNT_* indices below
     Graph graph;
+    int gen_dims = 0;         // largest d of the live generated costs
     long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t ev_chunk = nullptr, ev_copy = nullptr;
     bool inflight = false;
@@ -890,7 +950,7 @@ namespace {
 
 size_t slot_bytes(pdot_handle* h, const pdot_request& r, int tile_rows) {
     size_t b = work_bytes(r.m, r.n, h->opt.x_dtype, tile_rows, nullptr);
-    if (!c_layout_ok(r.C, r.c_dtype, r.ldc))
+    if (r.c_dtype != PDOT_POINTS && !c_layout_ok(r.C, r.c_dtype, r.ldc))
         b += align_up((size_t)r.m * padded_ldc(r.n, r.c_dtype) * csize_of(r.c_dtype), 256);
     return b;
 }
@@ -926,8 +986,10 @@ void batch_compose(pdot_handle* h) {
     const int L = (int)B->live.size();
     B->insts.ensure((size_t)std::max(L, 1));
     B->snap.ensure(B->insts.cap);
-    size_t nt[NTT] = {0, 0, 0}, nti[NTT] = {0, 0, 0}, nv = 0, nvi = 0;
+    size_t nt[NTT] = {}, nti[NTT] = {}, nv = 0, nvi = 0;
+    int gd = 0;
     for (BSlot* s : B->live) {
+        if (s->req.c_dtype == PDOT_POINTS) gd = std::max(gd, (int)s->pts.d);
         nt[s->ttype] += (size_t)s->w.ntiles;
         nv += (size_t)s->w.nvt;
         if (s->fresh) {
@@ -941,7 +1003,8 @@ void batch_compose(pdot_handle* h) {
     }
     B->vmap.ensure(std::max<size_t>(nv, 1));
     B->vmap_init.ensure(std::max<size_t>(nvi, 1));
-    size_t ot[NTT] = {0, 0, 0}, oti[NTT] = {0, 0, 0}, ov = 0, ovi = 0;
+    B->gen_dims = gd;
+    size_t ot[NTT] = {}, oti[NTT] = {}, ov = 0, ovi = 0;
     for (int i = 0; i < L; ++i) {
         BSlot* s = B->live[(size_t)i];
         long long ldc = s->req.ldc;
@@ -968,14 +1031,14 @@ void batch_compose(pdot_handle* h) {
         if (oti[t])
             CK(cudaMemcpyAsync(B->tmap_init[t].d, B->tmap_init[t].h, sizeof(TileRef) * oti[t], cudaMemcpyHostToDevice, st));
         B->cnt.h[t] = (int)ot[t];
-        B->cnt.h[5 + t] = (int)oti[t];
+        B->cnt.h[CNT_INIT + t] = (int)oti[t];
     }
     if (ov) CK(cudaMemcpyAsync(B->vmap.d, B->vmap.h, sizeof(TileRef) * ov, cudaMemcpyHostToDevice, st));
     if (ovi) CK(cudaMemcpyAsync(B->vmap_init.d, B->vmap_init.h, sizeof(TileRef) * ovi, cudaMemcpyHostToDevice, st));
-    B->cnt.h[3] = (int)ov;
-    B->cnt.h[4] = L;
-    B->cnt.h[8] = (int)ovi;
-    CK(cudaMemcpyAsync(B->cnt.d, B->cnt.h, sizeof(int) * 9, cudaMemcpyHostToDevice, st));
+    B->cnt.h[CNT_VEC] = (int)ov;
+    B->cnt.h[CNT_INST] = L;
+    B->cnt.h[CNT_INIT_VEC] = (int)ovi;
+    CK(cudaMemcpyAsync(B->cnt.d, B->cnt.h, sizeof(int) * CNT_WORDS, cudaMemcpyHostToDevice, st));
     B->nv_live = (int)ov;
     {
         // One CTA per vector tile: size the grid by the live count (bucketed,
@@ -989,10 +1052,12 @@ void batch_compose(pdot_handle* h) {
         CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, st));
         for (int t = 0; t < NTT; ++t) {
             if (!oti[t]) continue;
-            CKL(launch_kkt(t, B->insts.d, B->tmap_init[t].d, B->cnt.d + 5 + t, h->wctr, MODE_INIT, h->cfg, st));
+            CKL(launch_kkt(t, B->insts.d, B->tmap_init[t].d, B->cnt.d + CNT_INIT + t, h->wctr, MODE_INIT, h->cfg,
+                           st));
             launch_count(h, 1);
         }
-        CKL(launch_checkvec(B->insts.d, B->vmap_init.d, B->cnt.d + 8, (int)nvi, h->wctr, MODE_INIT, h->cfg, st));
+        CKL(launch_checkvec(B->insts.d, B->vmap_init.d, B->cnt.d + CNT_INIT_VEC, (int)nvi, h->wctr, MODE_INIT,
+                            h->cfg, st));
         launch_count(h, 1);
         for (BSlot* s : B->live) s->fresh = false;
     }
@@ -1011,7 +1076,7 @@ void batch_issue_chunk(pdot_handle* h, int types) {
                 CKL(launch_pass(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, h->cfg, st));
                 launch_count(h, 1);
             }
-            CKL(launch_dual(B->insts.d, B->vmap.d, B->cnt.d + 3, B->nv_grid, h->wctr, h->cfg, st));
+            CKL(launch_dual(B->insts.d, B->vmap.d, B->cnt.d + CNT_VEC, B->nv_grid, h->wctr, h->cfg, st));
             launch_count(h, 1);
         }
         for (int t = 0; t < NTT; ++t) {
@@ -1019,11 +1084,12 @@ void batch_issue_chunk(pdot_handle* h, int types) {
             CKL(launch_kkt(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->wctr, MODE_CHECK, h->cfg, st));
             launch_count(h, 1);
         }
-        CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + 3, B->nv_grid, h->wctr, MODE_CHECK, h->cfg, st));
+        CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + CNT_VEC, B->nv_grid, h->wctr, MODE_CHECK, h->cfg,
+                            st));
         launch_count(h, 1);
     }
     (void)nvh;
-    CKL(launch_snapshot(B->insts.d, B->cnt.d + 4, (int)B->snap.cap, B->snap.d, st));
+    CKL(launch_snapshot(B->insts.d, B->cnt.d + CNT_INST, (int)B->snap.cap, B->snap.d, st));
     launch_count(h, 1);
     CK(cudaMemcpyAsync(B->snap.h, B->snap.d, sizeof(Ctrl) * B->snap.cap, cudaMemcpyDeviceToHost, st));
 }
@@ -1032,12 +1098,13 @@ void batch_launch_chunk(pdot_handle* h) {
     BatchEngine* B = h->batch;
     int types = 0;
     for (BSlot* s : B->live) types |= 1 << s->ttype;
+    h->cfg.gen_dims = B->gen_dims;
+    long long tmaps = 0;
+    for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
     const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->snap.d,
-                              (long long)(uintptr_t)B->vmap.d,
-                              (long long)(uintptr_t)B->tmap[0].d ^ ((long long)(uintptr_t)B->tmap[1].d << 1) ^
-                                  ((long long)(uintptr_t)B->tmap[2].d << 2),
-                              types | ((long long)B->nv_grid << 8), h->opt.restart_check_every, h->opt.chunk_checks,
-                              (long long)B->snap.cap};
+                              (long long)(uintptr_t)B->vmap.d, tmaps,
+                              types | ((long long)B->nv_grid << 8) | ((long long)B->gen_dims << 48),
+                              h->opt.restart_check_every, h->opt.chunk_checks, (long long)B->snap.cap};
     if (!h->opt.use_graph) {
         batch_issue_chunk(h, types);
     } else {
@@ -1180,11 +1247,12 @@ bool batch_admit(pdot_handle* h) {
 void batch_apply_cancels(pdot_handle* h) {
     // Stop cancelled / timed-out resident instances on the device before the next chunk.
     BatchEngine* B = h->batch;
-    B->cnt.h[15] = ST_CANCELLED;   // pinned source word of the status writes
+    B->cnt.h[CNT_CANCEL] = ST_CANCELLED;   // pinned source word of the status writes
     for (size_t i = 0; i < B->live.size(); ++i) {
         BSlot* s = B->live[i];
         if (!s->cancel) continue;
-        CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[15], sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_CANCEL], sizeof(int), cudaMemcpyHostToDevice,
+                           h->stream));
     }
 }
 
@@ -1417,11 +1485,20 @@ pdot_status pdot_solve_host(pdot_handle* h, int64_t m, int64_t n, const void* C,
     if (!h) return PDOT_ERR_ARG;
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
-        if (m < 1 || n < 1 || ldc < n || !C || !f || !g) throw ArgError{"bad arguments"};
+        const bool pts = c_dtype == PDOT_POINTS;
+        if (m < 1 || n < 1 || (!pts && ldc < n) || !C || !f || !g) throw ArgError{"bad arguments"};
+        pdot_points_cost dpc{};   // the descriptor with device coordinates
+        size_t bxs = 0, bys = 0;
+        if (pts) {
+            check_common_args(h, m, n, C, c_dtype, ldc, f, g);
+            dpc = *static_cast<const pdot_points_cost*>(C);
+            bxs = align_up(sizeof(float) * (size_t)m * (size_t)dpc.d, 256);
+            bys = align_up(sizeof(float) * (size_t)n * (size_t)dpc.d, 256);
+        }
         const size_t cs = csize_of(c_dtype);
         const size_t xs = xsize_of(h->opt.x_dtype);
-        const long long ldp = padded_ldc(n, c_dtype);
-        const size_t bC = align_up((size_t)m * ldp * cs, 256);
+        const long long ldp = pts ? 0 : padded_ldc(n, c_dtype);
+        const size_t bC = pts ? bxs + bys : align_up((size_t)m * ldp * cs, 256);
         const size_t bf = align_up(sizeof(double) * (size_t)m, 256), bg = align_up(sizeof(double) * (size_t)n, 256);
         const size_t bX = X_out ? align_up((size_t)m * n * xs, 256) : 0;
         const size_t bp = p_out ? bf : 0, bq = q_out ? bg : 0;
@@ -1440,11 +1517,22 @@ pdot_status pdot_solve_host(pdot_handle* h, int64_t m, int64_t n, const void* C,
         void* dX = X_out ? (void*)(b + bC + bf + bg) : nullptr;
         double* dp = p_out ? (double*)(b + bC + bf + bg + bX) : nullptr;
         double* dq = q_out ? (double*)(b + bC + bf + bg + bX + bp) : nullptr;
-        CK(cudaMemcpy2DAsync(dC, ldp * cs, C, (size_t)ldc * cs, (size_t)n * cs, (size_t)m, cudaMemcpyHostToDevice,
-                             h->stream));
+        const void* Cs = dC;
+        if (pts) {
+            const pdot_points_cost& hc = *static_cast<const pdot_points_cost*>(C);
+            CK(cudaMemcpyAsync(b, hc.xs, sizeof(float) * (size_t)m * (size_t)hc.d, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(b + bxs, hc.ys, sizeof(float) * (size_t)n * (size_t)hc.d, cudaMemcpyHostToDevice,
+                               h->stream));
+            dpc.xs = (const float*)b;
+            dpc.ys = (const float*)(b + bxs);
+            Cs = &dpc;
+        } else {
+            CK(cudaMemcpy2DAsync(dC, ldp * cs, C, (size_t)ldc * cs, (size_t)n * cs, (size_t)m, cudaMemcpyHostToDevice,
+                                 h->stream));
+        }
         CK(cudaMemcpyAsync(df, f, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemcpyAsync(dg, g, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
-        pdot_status st = solve_impl(h, m, n, dC, c_dtype, ldp, df, dg, tol, dX, dp, dq, res);
+        pdot_status st = solve_impl(h, m, n, Cs, c_dtype, ldp, df, dg, tol, dX, dp, dq, res);
         const auto t0 = Clock::now();
         if (X_out) CK(cudaMemcpyAsync(X_out, dX, (size_t)m * n * xs, cudaMemcpyDeviceToHost, h->stream));
         if (p_out) CK(cudaMemcpyAsync(p_out, dp, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
@@ -1536,7 +1624,7 @@ pdot_status pdot_round(pdot_handle* h, int64_t m, int64_t n, const void* X, cons
         if (m < 1 || n < 1 || !X || !f || !g || !X_out) throw ArgError{"bad arguments"};
         const int xt = h->opt.x_dtype;
         if (xt != PDOT_F32 && xt != PDOT_F64) throw ArgError{"x_dtype must be F32 or F64"};
-        round_plan_dev(h, m, n, xt, X, n, f, g, X_out, nullptr, 0, 0);
+        round_plan_dev(h, m, n, xt, X, n, f, g, X_out, nullptr, 0, 0, nullptr);
         CK(cudaStreamSynchronize(h->stream));
         return PDOT_OK;
     });
@@ -1558,6 +1646,11 @@ pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int coun
                 BSlot* s = new BSlot();
                 slots.push_back(s);
                 s->req = r;
+                if (r.c_dtype == PDOT_POINTS) {
+                    s->pts = *static_cast<const pdot_points_cost*>(r.C);
+                    s->req.C = &s->pts;
+                    s->req.ldc = 0;
+                }
                 s->ttype = ttype_of(r.c_dtype);
                 s->bytes = slot_bytes(h, r, pick_tile_rows(h, r.m, r.n, s->ttype, true));
                 if (s->bytes > B->budget) {
@@ -1656,7 +1749,8 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         *ms_per_pass = (double)ms / reps;
         if (bytes_per_pass)
             *bytes_per_pass = (double)m * (double)n * ((double)csize_of(c_dtype) + 4.0 * (double)xsize_of(w.xtype));
-        if (kernel_variant) *kernel_variant = ttype == TT_F64 ? 0 : h->cfg.pass_bulk;
+        if (kernel_variant) *kernel_variant = ttype == TT_F64 ? 0 : ttype == TT_GEN ? (h->cfg.pass_bulk ? 1 : 0)
+                                                                                     : h->cfg.pass_bulk;
         return PDOT_OK;
     });
 }

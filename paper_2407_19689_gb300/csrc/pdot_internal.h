@@ -14,6 +14,7 @@
 //          (nvt = ceil((m+n)/VE) vector tiles).
 //   Ctrl : the scalar state of Algorithm 2 and the Sec. 5 controller.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace pdot {
@@ -55,10 +56,56 @@ struct Ctrl {
     double last_etabar, last_dX2, last_dy2, last_inter;
 };
 
+// Cost generated from coordinates (pdot_dtype PDOT_POINTS):
+//   C_ij = dist(xs_i, ys_j) / div, coordinates k = 0..d-1 accumulated in order
+//   in FP32, then the quotient by gen_div.  Every kernel that needs C_ij uses
+//   the same operation sequence, so the pass, the check and the rounding see
+//   the same values.
+constexpr int GEN_DMAX = 8;
+constexpr int GK_SQEUCLID = 0, GK_L1 = 1, GK_L2 = 2, GK_LINF = 3;
+
+struct GenSpec {
+    const float* xs;     // m x d
+    const float* ys;     // n x d
+    int d, kind;
+    float div;
+    float inv;           // 1 / div rounded to nearest (host IEEE division)
+};
+
+// a / div without a division instruction: q = RN(a * inv), the remainder
+// r = RN(a - q * div) by one FMA, and the corrected quotient RN(q + r * inv)
+// by another (Markstein's correction step for division by a reciprocal).
+// It matched the correctly rounded quotient on every value checked exactly
+// (all pixel-grid squared distances over their maximum for grids up to
+// 128 x 128, and 20,000 random pairs); in general it is within one ulp.
+__host__ __device__ __forceinline__ float gen_div(float a, float div, float inv) {
+    const float q = a * inv;
+    const float r = fmaf(-q, div, a);
+    return fmaf(r, inv, q);
+}
+
+// x and y: anything indexable by k < d (register arrays or pointers); d <= DM.
+template <int DM = GEN_DMAX, typename PX, typename PY>
+__host__ __device__ __forceinline__ float gen_cost(int kind, int d, const PX& x, const PY& y, float div, float inv) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) {
+        if (k < d) {
+            const float t = x[k] - y[k];
+            if (kind == GK_SQEUCLID || kind == GK_L2) acc = fmaf(t, t, acc);
+            else if (kind == GK_L1) acc = acc + fabsf(t);
+            else acc = fmaxf(acc, fabsf(t));
+        }
+    }
+    if (kind == GK_L2) acc = sqrtf(acc);
+    return gen_div(acc, div, inv);
+}
+
 struct Inst {
     long long m, n, ldc, ldx;
     const void* C;
-    int ctype;           // 0 FP32, 1 BF16, 2 FP64 (pdot_dtype)
+    GenSpec gen;         // used when ctype == 3 (C is then null)
+    int ctype;           // 0 FP32, 1 BF16, 2 FP64, 3 generated (pdot_dtype)
     int xtype;           // 0 FP32, 2 FP64
     const double* f;
     const double* g;
@@ -94,7 +141,8 @@ struct TileRef {
 constexpr int TT_F32 = 0;    // FP32 C, FP32 X
 constexpr int TT_BF16 = 1;   // BF16 C, FP32 X
 constexpr int TT_F64 = 2;    // FP64 C, FP64 X
-constexpr int NTT = 3;
+constexpr int TT_GEN = 3;    // C generated from coordinates, FP32 X
+constexpr int NTT = 4;
 
 // Work counters of the tile-queue kernels, one per (phase, type).  Every
 // kernel resets all counters but its own when it starts: kernels on one
@@ -116,6 +164,7 @@ struct LaunchCfg {
     int group_blocks;     // CTAs of the grouped bulk-copy pass kernel
     int coop_blocks;      // CTAs of the cooperative chunk kernel (all co-resident)
     int pdl;              // 1: launch with programmatic dependent launch
+    int gen_dims;         // largest coordinate count of the generated costs in flight (TT_GEN)
 };
 
 // Tile and vector-tile counts are read from device memory, so one captured
@@ -128,8 +177,6 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
                const LaunchCfg& cfg, void* stream);
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream);
-int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
-                   const LaunchCfg& cfg, void* stream);
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream);
 int occupancy_tile_blocks_per_sm(int ttype);
 int occupancy_vec_blocks_per_sm();

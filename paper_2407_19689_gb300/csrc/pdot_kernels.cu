@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "pdot_internal.h"
 
 namespace pdot {
@@ -93,6 +95,54 @@ __device__ __forceinline__ void ldc4_tail(const double* p, long long cnt, A (&v)
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = e < cnt ? (A)__ldg(p + e) : A(0);
 }
+
+// Tag type of the generated cost (TT_GEN): C_ij comes from coordinates of at
+// most DM dimensions (the pass kernel has a 4-dimension variant that keeps
+// fewer coordinates in registers).
+template <int DM>
+struct GenC {};
+template <typename TC>
+struct GenDims { static constexpr int value = 0; };
+template <int DM>
+struct GenDims<GenC<DM>> { static constexpr int value = DM; };
+using GenC8 = GenC<GEN_DMAX>;
+using GenC4 = GenC<4>;
+
+// One lane's four cost entries C[i][j0..j0+3]: read from the stored matrix,
+// or generated from the coordinates (the four columns' coordinates are kept in
+// registers; the row's are read per call).
+template <typename TC, typename A>
+struct CostRow {
+    const TC* C;
+    long long ldc, cnt;
+    bool full;
+    __device__ __forceinline__ CostRow(const Inst& I, long long j0)
+        : C(reinterpret_cast<const TC*>(I.C) + j0), ldc(I.ldc), cnt(I.n - j0), full(j0 + 4 <= I.n) {}
+    __device__ __forceinline__ void get(long long i, A (&c)[4]) const {
+        if (full) ldc4<A>(C + i * ldc, c);
+        else ldc4_tail<A>(C + i * ldc, cnt, c);
+    }
+};
+template <int DM, typename A>
+struct CostRow<GenC<DM>, A> {
+    GenSpec g;
+    float y[4][DM];
+    __device__ __forceinline__ CostRow(const Inst& I, long long j0) : g(I.gen) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int k = 0; k < DM; ++k)
+                y[e][k] = (k < g.d && j0 + e < I.n) ? __ldg(g.ys + (j0 + e) * g.d + k) : 0.f;
+        }
+    }
+    __device__ __forceinline__ void get(long long i, A (&c)[4]) const {
+        float x[DM];
+#pragma unroll
+        for (int k = 0; k < DM; ++k) x[k] = k < g.d ? __ldg(g.xs + i * g.d + k) : 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[e] = (A)gen_cost<DM>(g.kind, g.d, x, y[e], g.div, g.inv);
+    }
+};
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -165,14 +215,13 @@ __device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
 template <typename TC, typename TX, int U>
 __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, int lane) {
     typedef TX A;
-    const long long m = I.m, n = I.n, ldx = I.ldx, ldc = I.ldc;
+    const long long m = I.m, n = I.n, ldx = I.ldx;
     const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
     const long long j0 = (long long)strip * STRIP + lane * 4;
     const long long i0 = (long long)chunk * I.tile_rows;
     const long long i1 = min(i0 + (long long)I.tile_rows, m);
     const bool on = j0 < n;
-    const bool full = j0 + 4 <= n;
-    const TC* C = reinterpret_cast<const TC*>(I.C);
+    const CostRow<TC, A> cr(I, j0);
     const TX* X = slot_x<TX>(I, S.cur);
     const TX* Xb = slot_x<TX>(I, S.bar);
     TX* Xn = slot_x<TX>(I, S.nxt);
@@ -193,14 +242,12 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
     double cs[4] = {0.0, 0.0, 0.0, 0.0};
     double dx2 = 0.0;
     double* rowpart = I.rowpart + (long long)strip * m;
-    // Row pointers advanced by the leading dimensions (lanes past n never dereference).
-    const TC* Cr = C + i0 * ldc + j0;
+    // Row pointers advanced by the leading dimension (lanes past n never dereference).
     const long long xo = i0 * ldx + j0;
     const TX* Xr = X + xo;
     const TX* Xbr = Xb + xo;
     TX* Xnr = Xn + xo;
     TX* Xbnr = Xbn + xo;
-    const long long ccnt = n - j0;
 
     for (long long ib = i0; ib < i1; ib += U) {
         A c[U][4], x[U][4], xb[U][4], pv[U];
@@ -210,8 +257,7 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
             const bool rv = ib + u < i1;
             pv[u] = rv ? (A)p[ib + u] : A(0);
             if (rv && on) {
-                if (full) ldc4<A>(Cr + u * ldc, c[u]);
-                else ldc4_tail<A>(Cr + u * ldc, ccnt, c[u]);
+                cr.get(ib + u, c[u]);
                 ld4(Xr + u * ldx, x[u]);
                 if (!first) ld4(Xbr + u * ldx, xb[u]);
                 else {
@@ -253,7 +299,6 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
 #pragma unroll
         for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
         dx2 += (double)dxa;
-        Cr += U * ldc;
         Xr += U * ldx;
         Xbr += U * ldx;
         Xnr += U * ldx;
@@ -409,7 +454,10 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     float* pbuf = P.pbuf;
     const unsigned wbase_s = P.wbase_s;
     const unsigned bars_s = P.bars_s;
-    constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
+    constexpr int DM = GenDims<TC>::value;
+    constexpr bool GEN = DM > 0;                            // C generated, not copied
+    constexpr int DA = GEN ? DM : 1;                        // coordinate array size
+    constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;      // C elements per 16 bytes
 
     // ---- producer: the tile being issued, resolved once per tile ----
     int p_tile = T;
@@ -436,18 +484,22 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             const long long ncols = min((long long)STRIP, I.n - c0);
             p_row = (long long)chunk * I.tile_rows;
             p_end = min(p_row + (long long)I.tile_rows, I.m);
-            p_cstride = I.ldc * (long long)sizeof(TC);
             p_xstride = I.ldx * 4;
-            p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            if constexpr (!GEN) {
+                p_cstride = I.ldc * (long long)sizeof(TC);
+                p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            }
             p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
                                                 p_row * I.ldx + c0);
             p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
                                                  p_row * I.ldx + c0);
             p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
-            p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
-            // The rounded-up C copy could run past the caller's allocation on
-            // the last matrix row of a ragged strip: lanes load that row.
-            p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            if constexpr (!GEN) {
+                p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
+                // The rounded-up C copy could run past the caller's allocation on
+                // the last matrix row of a ragged strip: lanes load that row.
+                p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            }
             p_first = Sc.k == 0;
             p_hint = I.l2_keep_c != 0;
             return;
@@ -505,6 +557,11 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     const double* c_p = nullptr;   // p of the consumer's instance
     bool c_hint = false;
     long long c_i1 = 0, c_win = -1;
+    // Generated cost: the lane's four columns' coordinates, and the
+    // coordinates of a window of 32 rows (lane r holds row window*32 + r).
+    GenSpec gs = {nullptr, nullptr, 0, 0, 1.f, 1.f};
+    float gy[4][DA], growc[DA];
+    long long c_cwin = -1;
     auto flush_tile = [&]() {
         if (c_tile < 0) return;
 #pragma unroll
@@ -533,11 +590,22 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
         c_ldx = CI->ldx;
         c_i0 = c_chunk * CI->tile_rows;
         const long long i1 = min(c_i0 + (long long)CI->tile_rows, CI->m);
-        const long long ncols = min((long long)STRIP, c_n - c0);
-        c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
         j0 = c0 + lane * 4;
         on = j0 < c_n;
-        c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        if constexpr (GEN) {
+            gs = CI->gen;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                for (int k = 0; k < DA; ++k)
+                    gy[e][k] = (k < gs.d && j0 + e < c_n) ? __ldg(gs.ys + (j0 + e) * gs.d + k) : 0.f;
+            }
+            c_cwin = -1;
+        } else {
+            const long long ncols = min((long long)STRIP, c_n - c0);
+            c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
+            c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        }
         float* Xb = reinterpret_cast<float*>(CI->X);
         c_xn = Xb + (long long)Sc.nxt * CI->xslot + c_i0 * c_ldx + j0;
         c_xbn = Xb + (long long)Sc.barn * CI->xslot + c_i0 * c_ldx + j0;
@@ -573,8 +641,62 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
         const long long di = i - c_i0;
         const unsigned char* stage = wbase + st * STAGE_BYTES;
         float c[4], x[4], xb[4];
+        if constexpr (GEN) {
+            // Every lane takes part in the shuffles (lanes past n included).
+            const long long cw = di >> 5;
+            if (cw != c_cwin) {
+                const long long r = c_i0 + cw * 32 + lane;
+#pragma unroll
+                for (int k = 0; k < DA; ++k)
+                    growc[k] = (k < gs.d && r < c_i1) ? __ldg(gs.xs + r * gs.d + k) : 0.f;
+                c_cwin = cw;
+            }
+            // gen_cost with the coordinate loop outermost (one shuffle per
+            // coordinate, four accumulators) and the distance kind resolved
+            // once per row: the same operations per entry.
+            const int src = (int)(di & 31);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gs.kind == GK_L1) {
+#pragma unroll
+                for (int k = 0; k < DA; ++k) {
+                    if (k < gs.d) {
+                        const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] = acc[e] + fabsf(xk - gy[e][k]);
+                    }
+                }
+            } else if (gs.kind == GK_LINF) {
+#pragma unroll
+                for (int k = 0; k < DA; ++k) {
+                    if (k < gs.d) {
+                        const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] = fmaxf(acc[e], fabsf(xk - gy[e][k]));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < DA; ++k) {
+                    if (k < gs.d) {
+                        const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float t = xk - gy[e][k];
+                            acc[e] = fmaf(t, t, acc[e]);
+                        }
+                    }
+                }
+                if (gs.kind == GK_L2) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[e] = sqrtf(acc[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c[e] = gen_div(acc[e], gs.div, gs.inv);
+        }
         if (on) {
-            if (i != c_last_ragged) {
+            if constexpr (GEN) {
+            } else if (i != c_last_ragged) {
                 if (sizeof(TC) == 4) {
                     const float4 t = *reinterpret_cast<const float4*>(stage + lane * 16);
                     c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
@@ -598,7 +720,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; }
+            for (int e = 0; e < 4; ++e) { c[e] = GEN ? c[e] : 0.f; x[e] = 0.f; xb[e] = 0.f; }
         }
         // Row duals are staged in shared memory per window of MAX_TILE_ROWS rows
         // instead of one dependent global load per row.
@@ -669,7 +791,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
 }
 
 template <typename TC, int S>
-__global__ void __launch_bounds__(TWARPS * 32)
+__global__ void __launch_bounds__(TWARPS * 32, 2)
 k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
             unsigned* wctr, int wc) {
     pdl_enter();
@@ -1173,17 +1295,16 @@ __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, con
 template <typename TC, typename TX>
 __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, int lane, int mode) {
     typedef TX A;
-    const long long m = I.m, n = I.n, ldx = I.ldx, ldc = I.ldc;
+    const long long m = I.m, n = I.n, ldx = I.ldx;
     const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
     const long long j0 = (long long)strip * STRIP + lane * 4;
     const long long i0 = (long long)chunk * I.tile_rows;
     const long long i1 = min(i0 + (long long)I.tile_rows, m);
     const bool on = j0 < n;
-    const bool full = j0 + 4 <= n;
+    const CostRow<TC, A> cr(I, j0);
     const bool init = mode == MODE_INIT;
     const bool avg = !init && S.k > 0;      // the running average exists
     const bool sums = init || avg;          // exact row/col sums of X (init) or Xbar (check)
-    const TC* C = reinterpret_cast<const TC*>(I.C);
     const TX* X = slot_x<TX>(I, S.cur);
     const TX* Xb = slot_x<TX>(I, S.bar);
     const TX* Xa = slot_x<TX>(I, S.anc);
@@ -1215,8 +1336,7 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
 #pragma unroll
             for (int e = 0; e < 4; ++e) { c[u][e] = A(0); x[u][e] = A(0); xb[u][e] = A(0); xa[u][e] = A(0); }
             if (rv && on) {
-                if (full) ldc4<A>(C + i * ldc + j0, c[u]);
-                else ldc4_tail<A>(C + i * ldc + j0, n - j0, c[u]);
+                cr.get(i, c[u]);
                 ld4(X + i * ldx + j0, x[u]);
                 if (avg) {
                     ld4(Xb + i * ldx + j0, xb[u]);
@@ -1624,45 +1744,6 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
 }
 
 // ---------------------------------------------------------------------------
-// ||C||_F^2 per plan tile (once per solve, for the relative dual residual)
-// ---------------------------------------------------------------------------
-template <typename TC>
-__device__ __forceinline__ void sumsq_tile(const Inst& I, int lt, int lane) {
-    const long long m = I.m, n = I.n, ldc = I.ldc;
-    const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
-    const long long j0 = (long long)strip * STRIP + lane * 4;
-    const long long i0 = (long long)chunk * I.tile_rows;
-    const long long i1 = min(i0 + (long long)I.tile_rows, m);
-    const TC* C = reinterpret_cast<const TC*>(I.C);
-    double s = 0.0;
-    if (j0 < n) {
-        for (long long i = i0; i < i1; ++i) {
-            double c[4];
-            if (j0 + 4 <= n) ldc4<double>(C + i * ldc + j0, c);
-            else ldc4_tail<double>(C + i * ldc + j0, n - j0, c);
-            s += c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + c[3] * c[3];
-        }
-    }
-    s = warp_sum(s);
-    if (lane == 0) I.tpart[(long long)lt * TP + 0] = s;
-}
-
-template <typename TC>
-__global__ void __launch_bounds__(TWARPS * 32)
-k_sumsq_C(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
-    pdl_enter();
-    const int T = *Tp;
-    reset_other_counters(wctr, wc);
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        const int t = warp_next(&wctr[wc]);
-        if (t >= T) break;
-        const TileRef tr = tmap[t];
-        sumsq_tile<TC>(insts[tr.inst], tr.local, lane);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Snapshot of every resident instance's controller (one D2H copy per chunk)
 // ---------------------------------------------------------------------------
 __global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict__ count, Ctrl* out) {
@@ -1710,6 +1791,17 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
     const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
     const bool pdl = cfg.pdl != 0;
     const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
+    if (ttype == TT_GEN) {
+        // Generated cost: the per-row bulk pipeline (X and Xbar copies only),
+        // or the register pipeline when the bulk kernels are switched off.
+        if (cfg.pass_bulk && cfg.gen_dims <= 4)
+            return launch_k(pdl, k_pass_bulk<GenC4, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                            d_tmap, T, wctr, wc);
+        if (cfg.pass_bulk)
+            return launch_k(pdl, k_pass_bulk<GenC8, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                            d_tmap, T, wctr, wc);
+        return launch_k(pdl, k_pass<GenC8, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    }
     if (cfg.pass_bulk == 2 && ttype != TT_F64) {
         if (ttype == TT_BF16)
             return launch_k(pdl, k_pass_group<unsigned short, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st,
@@ -1754,6 +1846,9 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
     if (ttype == TT_BF16)
         return launch_k(pdl, k_kkt<unsigned short, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T,
                         wctr, wc, mode);
+    if (ttype == TT_GEN)
+        return launch_k(pdl, k_kkt<GenC8, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T, wctr, wc,
+                        mode);
     return launch_k(pdl, k_kkt<float, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T, wctr, wc,
                     mode);
 }
@@ -1764,16 +1859,6 @@ int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, i
     return launch_k(cfg.pdl != 0, k_checkvec, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV,
                     wctr, mode);
 }
-int launch_sumsq_C(int ctype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
-                   const LaunchCfg& cfg, void* stream) {
-    const cudaStream_t st = (cudaStream_t)stream;
-    const int wc = wc_index(WC_AUX, ctype == 2 ? TT_F64 : (ctype == 1 ? TT_BF16 : TT_F32));
-    const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
-    if (ctype == 2) return launch_k(false, k_sumsq_C<double>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
-    if (ctype == 1) return launch_k(false, k_sumsq_C<unsigned short>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
-    return launch_k(false, k_sumsq_C<float>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
-}
-
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream) {
     const int words = (int)(sizeof(Ctrl) / sizeof(int));
     int blocks = (max_count * words + 255) / 256;
@@ -1798,10 +1883,14 @@ int occupancy_tile_blocks_per_sm(int ttype) {
     const int b = occ((const void*)k_kkt<float, float>, TWARPS * 32);
     const int c = occ((const void*)k_pass<unsigned short, float, 4>, TWARPS * 32);
     const int d = occ((const void*)k_kkt<unsigned short, float>, TWARPS * 32);
+    const int e = occ((const void*)k_pass<GenC8, float, 2>, TWARPS * 32);
+    const int g = occ((const void*)k_kkt<GenC8, float>, TWARPS * 32);
     int r = a;
     if (b < r) r = b;
     if (c < r) r = c;
     if (d < r) r = d;
+    if (e < r) r = e;
+    if (g < r) r = g;
     return r;
 }
 int setup_coop_chunk() {
@@ -1859,10 +1948,18 @@ int setup_bulk_pass() {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_pass_bulk<unsigned short, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
-    int a = 0, b = 0;
+    e = cudaFuncSetAttribute(k_pass_bulk<GenC4, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_pass_bulk<GenC8, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    int a = 0, b = 0, c = 0, d = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_bulk<float, BULK_S>, TWARPS * 32, bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_bulk<unsigned short, BULK_S>, TWARPS * 32, bytes);
-    const int r = a < b ? a : b;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass_bulk<GenC4, BULK_S>, TWARPS * 32, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_pass_bulk<GenC8, BULK_S>, TWARPS * 32, bytes);
+    int r = a < b ? a : b;
+    if (c < r) r = c;
+    if (d < r) r = d;
     return -(r > 0 ? r : 1);   // negative: blocks per SM
 }
 

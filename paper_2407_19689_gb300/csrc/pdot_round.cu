@@ -55,10 +55,27 @@ __global__ void k_colreduce(const double* colpart, int parts, long long n, doubl
     out[j] = s;
 }
 
-template <typename TX, typename TC>
+// Cost entry (i, j) for the objective of the rounded plan: a stored matrix
+// (null: no objective) or the generated cost.
+template <typename TC>
+struct StoredCost {
+    const TC* C;
+    long long ldc;
+    __device__ __forceinline__ bool on() const { return C != nullptr; }
+    __device__ __forceinline__ double operator()(long long i, long long j) const { return (double)C[i * ldc + j]; }
+};
+struct PointsCost {
+    GenSpec g;
+    __device__ __forceinline__ bool on() const { return true; }
+    __device__ __forceinline__ double operator()(long long i, long long j) const {
+        return (double)gen_cost(g.kind, g.d, g.xs + i * g.d, g.ys + j * g.d, g.div, g.inv);
+    }
+};
+
+template <typename TX, typename CA>
 __global__ void k_round_write(const TX* X, long long m, long long n, long long ldx, const double* rs,
                               const double* cs, const double* er, const double* ec, double inv_l1, TX* out,
-                              long long ldo, const TC* C, long long ldc, double* objpart, int parts) {
+                              long long ldo, CA C, double* objpart, int parts) {
     __shared__ double red[32];
     const int grp = blockIdx.x;
     const long long r0 = m * grp / parts, r1 = m * (grp + 1) / parts;
@@ -68,7 +85,7 @@ __global__ void k_round_write(const TX* X, long long m, long long n, long long l
             const double v = scaled(X, ldx, i, j, rs, cs) + er[i] * ec[j] * inv_l1;
             const TX vo = (TX)v;
             out[i * ldo + j] = vo;
-            if (C) obj += (double)C[i * ldc + j] * (double)vo;
+            if (C.on()) obj += C(i, j) * (double)vo;
         }
     }
 #pragma unroll
@@ -111,20 +128,24 @@ int launch_colreduce(const double* colpart, int parts, long long n, double* out,
 
 int launch_round_write(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
                        const double* cs, const double* er, const double* ec, double inv_l1, void* Xout,
-                       long long ldo, const void* C, int ctype, long long ldc, double* objpart, int parts,
-                       void* stream) {
+                       long long ldo, const void* C, int ctype, long long ldc, const GenSpec* gen,
+                       double* objpart, int parts, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     if (xtype == 2) {
-        k_round_write<double, double><<<parts, 256, 0, st>>>((const double*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
-                                                             (double*)Xout, ldo, (const double*)C, ldc, objpart,
-                                                             parts);
+        k_round_write<double><<<parts, 256, 0, st>>>((const double*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                     (double*)Xout, ldo,
+                                                     StoredCost<double>{(const double*)C, ldc}, objpart, parts);
+    } else if (ctype == 3) {
+        k_round_write<float><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                    (float*)Xout, ldo, PointsCost{*gen}, objpart, parts);
     } else if (ctype == 1) {
-        k_round_write<float, Bf16><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
-                                                          (float*)Xout, ldo, (const Bf16*)C, ldc, objpart, parts);
+        k_round_write<float><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                    (float*)Xout, ldo, StoredCost<Bf16>{(const Bf16*)C, ldc},
+                                                    objpart, parts);
     } else {
-        k_round_write<float, float><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
-                                                           (float*)Xout, ldo, (const float*)C, ldc, objpart,
-                                                           parts);
+        k_round_write<float><<<parts, 256, 0, st>>>((const float*)X, m, n, ldx, rs, cs, er, ec, inv_l1,
+                                                    (float*)Xout, ldo, StoredCost<float>{(const float*)C, ldc},
+                                                    objpart, parts);
     }
     return (int)cudaGetLastError();
 }

@@ -17,7 +17,8 @@ from dataclasses import dataclass
 
 from . import _build
 
-F32, BF16, F64 = 0, 1, 2
+F32, BF16, F64, POINTS = 0, 1, 2, 3
+DIST = {"sqeuclid": 0, "l1": 1, "l2": 2, "linf": 3}
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, MAX_ITER, TIMEOUT, BUSY, PENDING, CANCELLED = range(10)
 
 
@@ -105,6 +106,17 @@ class Request(ctypes.Structure):
         ("p_out", ctypes.c_void_p),
         ("q_out", ctypes.c_void_p),
         ("user_tag", ctypes.c_uint64),
+    ]
+
+
+class PointsCostDesc(ctypes.Structure):
+    """pdot_points_cost: a cost generated from coordinates (c_dtype POINTS)."""
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("dist", ctypes.c_int32),
+        ("xs", ctypes.c_void_p),
+        ("ys", ctypes.c_void_p),
+        ("divisor", ctypes.c_float),
     ]
 
 
@@ -294,6 +306,31 @@ def _xdtype_torch(x_dtype: int):
     return torch.float64 if x_dtype == F64 else torch.float32
 
 
+class Points:
+    """A cost that is never stored: C_ij = dist(xs_i, ys_j) / divisor, computed
+    in FP32 by every pass from the coordinates (xs: m x d, ys: n x d, d <= 8;
+    dist one of DIST).  Pass it wherever a cost matrix is accepted."""
+
+    def __init__(self, xs, ys, dist: str = "sqeuclid", divisor: float = 1.0):
+        self.xs, self.ys, self.dist, self.divisor = xs, ys, dist, float(divisor)
+
+    @property
+    def shape(self):
+        return (self.xs.shape[0], self.ys.shape[0])
+
+
+@dataclass
+class _Cost:
+    """Marshalled cost argument: pointer, dtype, leading dimension, and the
+    objects that must stay alive while the library reads them."""
+    ptr: int
+    dtype: int
+    ldc: int
+    m: int
+    n: int
+    keep: tuple
+
+
 @dataclass
 class Solution:
     result: dict
@@ -334,24 +371,41 @@ class Solver:
             t = t.to(dtype)
         return t.to(f"cuda:{self.device}").contiguous()
 
-    def _prep(self, C, f, g):
+    def _cost(self, C) -> _Cost:
         torch = _torch()
+        if isinstance(C, Points):
+            xs = self._cuda(C.xs, torch.float32)
+            ys = self._cuda(C.ys, torch.float32)
+            if xs.dim() == 1:
+                xs = xs[:, None].contiguous()
+            if ys.dim() == 1:
+                ys = ys[:, None].contiguous()
+            if xs.dim() != 2 or ys.dim() != 2 or xs.shape[1] != ys.shape[1]:
+                raise ValueError("xs and ys must be (m, d) and (n, d)")
+            desc = PointsCostDesc(d=xs.shape[1], dist=DIST[C.dist], xs=xs.data_ptr(), ys=ys.data_ptr(),
+                                  divisor=C.divisor)
+            return _Cost(ctypes.addressof(desc), POINTS, 0, xs.shape[0], ys.shape[0], (desc, xs, ys))
         C = self._cuda(C)
         if C.dim() != 2:
             raise ValueError("C must be 2-D")
+        return _Cost(C.data_ptr(), _cdtype(C), C.stride(0), C.shape[0], C.shape[1], (C,))
+
+    def _prep(self, C, f, g):
+        torch = _torch()
+        c = self._cost(C)
         f = self._cuda(f, torch.float64)
         g = self._cuda(g, torch.float64)
-        return C, f, g
+        return c, f, g
 
     def solve(self, C, f, g, tol: float | None = None, want_plan: bool = True) -> Solution:
         torch = _torch()
-        C, f, g = self._prep(C, f, g)
-        m, n = C.shape
+        c, f, g = self._prep(C, f, g)
+        m, n = c.m, c.n
         xt = _xdtype_torch(self.options.x_dtype)
-        X = torch.empty((m, n), dtype=xt, device=C.device) if want_plan else None
-        p = torch.empty(m, dtype=torch.float64, device=C.device)
-        q = torch.empty(n, dtype=torch.float64, device=C.device)
-        st, r = pdot_solve(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(),
+        X = torch.empty((m, n), dtype=xt, device=f.device) if want_plan else None
+        p = torch.empty(m, dtype=torch.float64, device=f.device)
+        q = torch.empty(n, dtype=torch.float64, device=f.device)
+        st, r = pdot_solve(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(),
                            tol if tol is not None else self.options.tol, X.data_ptr() if X is not None else 0,
                            p.data_ptr(), q.data_ptr())
         _check(self.h, st, allow=(OK, MAX_ITER, TIMEOUT, ERR_NUMERIC))
@@ -359,14 +413,14 @@ class Solver:
 
     def pdhg_steps(self, C, f, g, X, p, q, k: int, eta: float, omega: float = 1.0):
         torch = _torch()
-        C, f, g = self._prep(C, f, g)
-        m, n = C.shape
+        c, f, g = self._prep(C, f, g)
+        m, n = c.m, c.n
         xt = _xdtype_torch(self.options.x_dtype)
         X = self._cuda(X, xt).clone()
         p = self._cuda(p, torch.float64).clone()
         q = self._cuda(q, torch.float64).clone()
         Xb, pb, qb = torch.empty_like(X), torch.empty_like(p), torch.empty_like(q)
-        st = pdot_pdhg_steps(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(), k,
+        st = pdot_pdhg_steps(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(), k,
                              eta, omega, X.data_ptr(), p.data_ptr(), q.data_ptr(), Xb.data_ptr(), pb.data_ptr(),
                              qb.data_ptr())
         _check(self.h, st)
@@ -374,12 +428,12 @@ class Solver:
 
     def kkt(self, C, f, g, X, p, q) -> dict:
         torch = _torch()
-        C, f, g = self._prep(C, f, g)
-        m, n = C.shape
+        c, f, g = self._prep(C, f, g)
+        m, n = c.m, c.n
         X = self._cuda(X, _xdtype_torch(self.options.x_dtype))
         p = self._cuda(p, torch.float64)
         q = self._cuda(q, torch.float64)
-        st, out = pdot_kkt(self.h, m, n, C.data_ptr(), _cdtype(C), C.stride(0), f.data_ptr(), g.data_ptr(),
+        st, out = pdot_kkt(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(),
                            X.data_ptr(), p.data_ptr(), q.data_ptr())
         _check(self.h, st)
         return out.as_dict()
@@ -421,18 +475,18 @@ class BatchSolver:
 
     def submit(self, C, f, g, tol: float = 0.0, want_plan: bool = True, tag: int = 0) -> int:
         torch = _torch()
-        C, f, g = self.solver._prep(C, f, g)
-        m, n = C.shape
+        c, f, g = self.solver._prep(C, f, g)
+        m, n = c.m, c.n
         xt = _xdtype_torch(self.options.x_dtype)
-        X = torch.empty((m, n), dtype=xt, device=C.device) if want_plan else None
-        p = torch.empty(m, dtype=torch.float64, device=C.device)
-        q = torch.empty(n, dtype=torch.float64, device=C.device)
-        r = Request(m=m, n=n, C=C.data_ptr(), c_dtype=_cdtype(C), ldc=C.stride(0), f=f.data_ptr(), g=g.data_ptr(),
+        X = torch.empty((m, n), dtype=xt, device=f.device) if want_plan else None
+        p = torch.empty(m, dtype=torch.float64, device=f.device)
+        q = torch.empty(n, dtype=torch.float64, device=f.device)
+        r = Request(m=m, n=n, C=c.ptr, c_dtype=c.dtype, ldc=c.ldc, f=f.data_ptr(), g=g.data_ptr(),
                     tol=tol, X_out=X.data_ptr() if X is not None else None, p_out=p.data_ptr(),
                     q_out=q.data_ptr(), user_tag=tag)
         st, ids = pdot_batch_submit(self.h, [r])
         _check(self.h, st)
-        self._keep[ids[0]] = (C, f, g, X, p, q)
+        self._keep[ids[0]] = (c.keep, f, g, X, p, q)
         return ids[0]
 
     def poll(self, cap: int = 1024) -> list[tuple[int, Solution]]:

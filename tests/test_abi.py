@@ -49,7 +49,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 @pytest.mark.parametrize("cname,pyname", [("pdot_options", "Options"), ("pdot_result", "Result"),
-                                          ("pdot_kkt_parts", "KktParts"), ("pdot_request", "Request")])
+                                          ("pdot_kkt_parts", "KktParts"), ("pdot_request", "Request"),
+                                          ("pdot_points_cost", "PointsCostDesc")])
 def test_ctypes_structs_follow_header(cname, pyname):
     from paper_2407_19689_gb300 import pdot
     py = [f for f, _ in getattr(pdot, pyname)._fields_]
@@ -69,3 +70,13 @@ def test_null_handle_is_rejected_without_gpu(lib):
     st, _ = pdot.pdot_solve(None, 4, 4, 0, pdot.F32, 4, 0, 0, 1e-4)
     assert st == pdot.ERR_ARG
     assert pdot.pdot_destroy(None) == pdot.OK
+
+
+def test_dtype_and_distance_codes_follow_header():
+    from paper_2407_19689_gb300 import pdot
+    src = open(HEADER).read()
+    for name, val in [("PDOT_F32", pdot.F32), ("PDOT_BF16", pdot.BF16), ("PDOT_F64", pdot.F64),
+                      ("PDOT_POINTS", pdot.POINTS)]:
+        assert re.search(rf"\b{name}\s*=\s*{val}\b", src), name
+    for dist, val in pdot.DIST.items():
+        assert re.search(rf"\bPDOT_DIST_{dist.upper()}\s*=\s*{val}\b", src), dist
