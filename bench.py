@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--serve-loads", default="0.5,0.8,1.1",
                     help="offered loads as fractions of the one-at-a-time server's measured capacity")
     ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
+    ap.add_argument("--step-probe", action="store_true",
+                    help="per-step time decomposition: the pass alone, pass + dual update (plain launches)")
     ap.add_argument("--pass-sweep", action="store_true",
                     help="time the fused pass kernel alone over kernels x tile heights x sizes (tuning table)")
     return ap.parse_args()
@@ -373,7 +375,7 @@ def run_ours(args):
             "restarts": last.restarts, "rel_kkt": last.rel_kkt, "primal_obj": last.primal_obj,
             "hbm_gbs_per_iter": last.hbm_bytes / (elapsed / args.steps) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": pdot.KERNEL_NAMES.get(variant),
+                         "frac": achieved / peak, "traffic": traffic, "kernel": pdot.kernel_name(variant, ctype),
                          "bytes_per_launch": bytes_pass, "ms_per_launch": ms_pass,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
@@ -454,18 +456,19 @@ def run_serve(args):
     from paper_2407_19689_gb300 import instances as I
     _build.build()
     pdot.load()
-    # Capacity of the one-at-a-time server: the mean service time of 24
-    # requests of the same mix served back to back.
-    probe = I.serve_requests(24, 1e9, I.seed_for(4, 1), hi=args.serve_max)
-    capacity = len(probe) / serve.serve_plain(probe)["wall_s"]
+    # Capacity of the one-at-a-time server: the same requests served back to
+    # back (all arrived at time 0).  Every request has a 120 s time limit.
+    lim = {"time_limit_s": 120.0}
+    burst = I.serve_requests(args.requests, 1e9, I.seed_for(4), hi=args.serve_max)
+    capacity = len(burst) / serve.serve_plain(burst, **lim)["wall_s"]
     loads = [args.rate / capacity] if args.rate > 0.0 else [float(x) for x in args.serve_loads.split(",")]
     points = []
     for load in loads:
         rate = load * capacity
         reqs = I.serve_requests(args.requests, rate, I.seed_for(4), hi=args.serve_max)
-        rb = serve.serve_batched(reqs)
+        rb = serve.serve_batched(reqs, **lim)
         sb = serve.summary(rb)
-        rp = serve.serve_plain(reqs)
+        rp = serve.serve_plain(reqs, **lim)
         sp = serve.summary(rp)
         diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
         points.append({"load_vs_plain_capacity": load, "rate_per_s": rate, "continuous_batching": sb,
@@ -524,6 +527,8 @@ def run_pass_sweep(args):
         del C
         torch.cuda.empty_cache()
         # the same pass with the cost generated from the pixel coordinates
+        # (default kernel choice: no override left over from the loop above)
+        os.environ.pop("PDOT_PASS_BULK", None)
         Pf = P.float()
         cost = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=Pf.data_ptr(), ys=Pf.data_ptr(),
                                    divisor=float(2 * (G - 1) ** 2))
@@ -538,8 +543,66 @@ def run_pass_sweep(args):
     os.environ.pop("PDOT_PASS_BULK", None)
 
 
+def run_step_probe(args):
+    """Device time per PDHG step at one size, split into the fused pass alone
+    (pdot_time_pass) and pass + dual update with plain stream launches
+    (pdot_pdhg_steps with k = 300 minus k = 0, CUDA events), for stored FP32
+    and generated costs.  A diagnostic, not a bench line."""
+    import ctypes
+    import math
+
+    import torch
+
+    from paper_2407_19689_gb300 import _build, pdot
+    from paper_2407_19689_gb300 import instances as I
+    _build.build()
+    pdot.load()
+    G = args.grid
+    ins = I.grid_blob_instance(G, I.seed_for(1), build_cost=False)
+    P = torch.tensor(I.grid_coords(G), device="cuda:0")
+    C = torch.cdist(P, P) ** 2
+    C = (C / C.max()).float()
+    Pf = P.float()
+    desc = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=Pf.data_ptr(), ys=Pf.data_ptr(),
+                               divisor=float(2 * (G - 1) ** 2))
+    m = n = G * G
+    f = torch.tensor(ins.f, device="cuda:0")
+    g = torch.tensor(ins.g, device="cuda:0")
+    eta = 0.5 / math.sqrt(m + n)
+    out = {"m": m, "n": n}
+    for name, cptr, ctype, ldc in (("f32", C.data_ptr(), pdot.F32, n), ("points", ctypes.addressof(desc), pdot.POINTS, 0)):
+        s = pdot.Solver(device=0)
+        st, ms, _, var = pdot.pdot_time_pass(s.h, m, n, cptr, ctype, ldc, f.data_ptr(), g.data_ptr(), 50)
+
+        def steps(k):
+            X = torch.zeros((m, n), device="cuda:0")
+            p = torch.zeros(m, dtype=torch.float64, device="cuda:0")
+            q = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            rc = pdot.pdot_pdhg_steps(s.h, m, n, cptr, ctype, ldc, f.data_ptr(), g.data_ptr(), k, eta, 1.0,
+                                      X.data_ptr(), p.data_ptr(), q.data_ptr(), 0, 0, 0)
+            e1.record()
+            torch.cuda.synchronize()
+            if rc != pdot.OK:
+                raise RuntimeError(pdot.status_str(rc))
+            return e0.elapsed_time(e1)
+
+        steps(10)
+        t0 = min(steps(0) for _ in range(3))
+        t1 = min(steps(300) for _ in range(3))
+        out[name] = {"pass_us": ms * 1e3, "kernel_variant": var, "step_us": (t1 - t0) / 300 * 1e3}
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.step_probe:
+        run_step_probe(args)
+        return
     if args.pass_sweep:
         run_pass_sweep(args)
         return

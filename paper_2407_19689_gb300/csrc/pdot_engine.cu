@@ -333,9 +333,17 @@ int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kerne
     return (int)tr;
 }
 
-int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool batch = false) {
+// Autotuner cache key: shape, cost type and (generated costs) coordinate count.
+long long tune_key(long long m, long long n, int ttype, int gen_d) {
+    return ((m * 1000003LL + n) * 4 + ttype) * 16 + gen_d;
+}
+int gen_dims_of(const void* C, int ctype) {
+    return ctype == PDOT_POINTS ? (int)static_cast<const pdot_points_cost*>(C)->d : 0;
+}
+
+int pick_tile_rows(pdot_handle* h, long long m, long long n, int ttype, bool batch = false, int gen_d = 0) {
     if (!batch && h->opt.tile_rows <= 0) {
-        const long long key = (m * 1000003LL + n) * 4 + ttype;
+        const long long key = tune_key(m, n, ttype, gen_d);
         auto it = h->tune_cache.find(key);
         if (it != h->tune_cache.end() && it->second.first == h->cfg.pass_bulk) return it->second.second;
     }
@@ -589,13 +597,14 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
 void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                    const double* f, const double* g) {
     const int ttype = ttype_of(ctype);
-    if (ttype == TT_GEN) {
-        // Generated costs have one bulk kernel (per-row copies of X and Xbar).
+    const int gen_d = gen_dims_of(C, ctype);
+    if (ttype == TT_GEN && gen_d > 4) {
+        // More than 4 coordinates: the per-row kernel is the only bulk one.
         h->cfg.pass_bulk = h->cfg_base.pass_bulk ? 1 : 0;
         return;
     }
     if (ttype == TT_F64 || h->opt.tile_rows > 0 || !h->cfg_base.pass_bulk) return;
-    const long long key = (m * 1000003LL + n) * 4 + ttype;
+    const long long key = tune_key(m, n, ttype, gen_d);
     auto it = h->tune_cache.find(key);
     if (it != h->tune_cache.end()) {
         h->cfg.pass_bulk = it->second.first;
@@ -668,7 +677,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     validate_marginals(h, m, n, f, g, false, &norm_b);
     const int ttype = ttype_of(ctype);
     autotune_pass(h, m, n, C, ctype, ldc, f, g);
-    const int tr = pick_tile_rows(h, m, n, ttype);
+    const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, ctype));
     ensure_work(h, m, n, h->opt.x_dtype, tr);
     ensure_maps(h);
     Work& w = h->ws;
@@ -1552,7 +1561,7 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
         if (k < 0 || !(eta > 0.0) || !(omega > 0.0) || !X || !p || !q) throw ArgError{"bad k, eta, omega or state"};
         const int ttype = ttype_of(c_dtype);
-        const int tr = pick_tile_rows(h, m, n, ttype);
+        const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, c_dtype));
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);
         Work& w = h->ws;
@@ -1593,7 +1602,7 @@ pdot_status pdot_kkt(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_d
         double norm_b = 0.0;
         validate_marginals(h, m, n, f, g, false, &norm_b);
         const int ttype = ttype_of(c_dtype);
-        const int tr = pick_tile_rows(h, m, n, ttype);
+        const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, c_dtype));
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);
         Work& w = h->ws;
@@ -1712,7 +1721,7 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         if (reps < 1 || !ms_per_pass) throw ArgError{"reps < 1 or null output"};
         const int ttype = ttype_of(c_dtype);
         autotune_pass(h, m, n, C, c_dtype, ldc, f, g);
-        const int tr = pick_tile_rows(h, m, n, ttype);
+        const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, c_dtype));
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);
         Work& w = h->ws;
@@ -1749,8 +1758,11 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         *ms_per_pass = (double)ms / reps;
         if (bytes_per_pass)
             *bytes_per_pass = (double)m * (double)n * ((double)csize_of(c_dtype) + 4.0 * (double)xsize_of(w.xtype));
-        if (kernel_variant) *kernel_variant = ttype == TT_F64 ? 0 : ttype == TT_GEN ? (h->cfg.pass_bulk ? 1 : 0)
-                                                                                     : h->cfg.pass_bulk;
+        if (kernel_variant) {
+            int v = ttype == TT_F64 ? 0 : h->cfg.pass_bulk;
+            if (ttype == TT_GEN && v == 2 && h->cfg.gen_dims > 4) v = 1;   // no grouped kernel beyond 4 coordinates
+            *kernel_variant = v;
+        }
         return PDOT_OK;
     });
 }

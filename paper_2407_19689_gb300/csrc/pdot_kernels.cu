@@ -865,6 +865,9 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         fence_mbar_init();
     }
     __syncwarp();
+    constexpr int DM = GenDims<TC>::value;
+    constexpr bool GEN = DM > 0;                         // C generated, not copied
+    constexpr int DA = GEN ? DM : 1;                     // coordinate array size
     constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
 
     // ---- producer ----
@@ -889,16 +892,20 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             const long long ncols = min((long long)STRIP, I.n - c0);
             p_row = (long long)chunk * I.tile_rows;
             p_end = min(p_row + (long long)I.tile_rows, I.m);
-            p_cstride = I.ldc * (long long)sizeof(TC);
             p_xstride = I.ldx * 4;
-            p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            if constexpr (!GEN) {
+                p_cstride = I.ldc * (long long)sizeof(TC);
+                p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+            }
             p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
                                                 p_row * I.ldx + c0);
             p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
                                                  p_row * I.ldx + c0);
             p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
-            p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
-            p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            if constexpr (!GEN) {
+                p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
+                p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            }
             p_first = Sc.k == 0;
             return;
         }
@@ -926,7 +933,9 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             const unsigned d = dst + r * STAGE_BYTES + arr * (STRIP * 4);
             fence_proxy_async();   // this lane's copy follows the warp's generic reads of the stage
             if (arr == 0) {
-                if (!(skip_c && p_row + r == p_last_ragged)) g2s(d, p_c + r * p_cstride, p_cbytes, bar);
+                if constexpr (!GEN) {
+                    if (!(skip_c && p_row + r == p_last_ragged)) g2s(d, p_c + r * p_cstride, p_cbytes, bar);
+                }
             } else if (arr == 1) {
                 g2s(d, p_x + r * p_xstride, p_xbytes, bar);
             } else if (!p_first) {
@@ -962,6 +971,11 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     int c_local = 0;
     const double* c_p = nullptr;
     long long c_i1 = 0, c_win = -1;
+    // Generated cost: the lane's four columns' coordinates, and a 32-row
+    // window of row coordinates (lane r holds row window * 32 + r).
+    GenSpec gs = {nullptr, nullptr, 0, 0, 1.f, 1.f};
+    float gy[4][DA], growc[DA];
+    long long c_cwin = -1;
     auto flush_tile = [&]() {
         if (c_tile < 0) return;
 #pragma unroll
@@ -990,11 +1004,22 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         c_ldx = CI->ldx;
         c_i0 = c_chunk * CI->tile_rows;
         c_i1 = min(c_i0 + (long long)CI->tile_rows, CI->m);
-        const long long ncols = min((long long)STRIP, c_n - c0);
-        c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
         j0 = c0 + lane * 4;
         on = j0 < c_n;
-        c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        if constexpr (GEN) {
+            gs = CI->gen;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                for (int k = 0; k < DA; ++k)
+                    gy[e][k] = (k < gs.d && j0 + e < c_n) ? __ldg(gs.ys + (j0 + e) * gs.d + k) : 0.f;
+            }
+            c_cwin = -1;
+        } else {
+            const long long ncols = min((long long)STRIP, c_n - c0);
+            c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
+            c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        }
         float* Xb = reinterpret_cast<float*>(CI->X);
         c_xn = Xb + (long long)Sc.nxt * CI->xslot + c_i0 * c_ldx + j0;
         c_xbn = Xb + (long long)Sc.barn * CI->xslot + c_i0 * c_ldx + j0;
@@ -1044,8 +1069,59 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             }
             const float pv = pbuf[di - win * MAX_TILE_ROWS];
             float c[4], x[4], xb[4];
+            if constexpr (GEN) {
+                // Same operations as gen_cost; every lane takes part in the shuffles.
+                const long long cw = di >> 5;
+                if (cw != c_cwin) {
+                    const long long rr = c_i0 + cw * 32 + lane;
+#pragma unroll
+                    for (int k = 0; k < DA; ++k)
+                        growc[k] = (k < gs.d && rr < c_i1) ? __ldg(gs.xs + rr * gs.d + k) : 0.f;
+                    c_cwin = cw;
+                }
+                const int src = (int)(di & 31);
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                if (gs.kind == GK_L1) {
+#pragma unroll
+                    for (int k = 0; k < DA; ++k) {
+                        if (k < gs.d) {
+                            const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[e] = acc[e] + fabsf(xk - gy[e][k]);
+                        }
+                    }
+                } else if (gs.kind == GK_LINF) {
+#pragma unroll
+                    for (int k = 0; k < DA; ++k) {
+                        if (k < gs.d) {
+                            const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[e] = fmaxf(acc[e], fabsf(xk - gy[e][k]));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < DA; ++k) {
+                        if (k < gs.d) {
+                            const float xk = __shfl_sync(0xffffffffu, growc[k], src);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float t = xk - gy[e][k];
+                                acc[e] = fmaf(t, t, acc[e]);
+                            }
+                        }
+                    }
+                    if (gs.kind == GK_L2) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] = sqrtf(acc[e]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) c[e] = gen_div(acc[e], gs.div, gs.inv);
+            }
             if (on) {
-                if (i != c_last_ragged) {
+                if constexpr (GEN) {
+                } else if (i != c_last_ragged) {
                     if (sizeof(TC) == 4) {
                         const float4 t = *reinterpret_cast<const float4*>(rst + lane * 16);
                         c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
@@ -1069,7 +1145,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; }
+                for (int e = 0; e < 4; ++e) { c[e] = GEN ? c[e] : 0.f; x[e] = 0.f; xb[e] = 0.f; }
             }
             float xn[4], xbn[4], rs = 0.f;
 #pragma unroll
@@ -1199,83 +1275,108 @@ __device__ __forceinline__ double group_sum(const double* part, long long stride
     return t;
 }
 
-__device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* red, double* sgrp, int* s_last) {
+// One vector tile (VE = 32 entries of [p; q]) per CTA.  All warps add the
+// FP64 partial sums of the tile's row or column sums (group g: partials g,
+// g + VG, ...); warp 0 combines the groups in order, updates the duals and
+// the averages, reduces the tile's step-size scalars with shuffles and takes
+// the instance's ticket; the last tile of an instance finishes the step.
+// Everything that does not depend on the partial sums is requested before
+// them, and only one block-wide barrier is on the path (FP64 is a narrow pipe
+// on this part: block-wide FP64 reductions cost more than they save).
+__device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
     const long long m = I.m, n = I.n;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const long long e = (long long)lvt * VE + lane;
     const bool row = e < m, col = !row && e < m + n;
     const long long idx = row ? e : e - m;
-    // Independent loads first, so their latencies overlap the partial sums.
-    const double sigma = S->sigma;
-    const long long k = S->k;
-    const bool first = k == 0;
-    const double w = 1.0 / (double)(k + 1);
-    const double* Vc = slot_v(I, S->cur);
-    double* Vn = slot_v(I, S->nxt);
-    const double* Vb = slot_v(I, S->bar);
-    double* Vbn = slot_v(I, S->barn);
     const long long yo = row ? idx : m + idx;                   // p_i or q_j
     const long long so = row ? m + n + idx : 2 * m + n + idx;   // r_i or c_j
-    double b = 0.0, r = 0.0, y = 0.0, ybar = 0.0;
-    if (grp == 0 && (row || col)) {
-        b = row ? I.f[idx] : I.g[idx];
-        r = Vc[so];
-        y = Vc[yo];
-        if (!first) ybar = Vb[yo];
-    }
-    double a2 = 0.0;   // ||dX||^2 over this vector tile's slice of plan tiles
-    {
-        const long long T = I.ntiles;
-        const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
-        for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) a2 += I.tpart[t * TP + 0];
-    }
-    // One uniform call (it synchronises the block): rows reduce strip partials,
-    // columns reduce chunk partials.
-    const double s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
-                               row || col, sgrp);
-    double a[3] = {0.0, 0.0, a2};   // ||dy||^2, dy^T A dx, ||dX||^2 (tile slice)
-    if (grp == 0 && (row || col)) {
-        const double yn = y + sigma * (b - (2.0 * s - r));
-        Vn[yo] = yn;
-        Vn[so] = s;
-        Vbn[yo] = first ? yn : ybar + w * (yn - ybar);
-        const double dy = yn - y;
-        a[0] = dy * dy;
-        a[1] = dy * (s - r);
-    }
-    block_sum<3>(a, red);
-    if (threadIdx.x == 0) {
-        double* vp = I.vpart + (long long)lvt * VP;
-        vp[0] = a[0]; vp[1] = a[1]; vp[2] = a[2];
-        __threadfence();
-        const unsigned old = atomicAdd(I.ticket, 1u);
-        *s_last = (old == (unsigned)(I.nvt - 1));
-    }
-    __syncthreads();
-    if (*s_last) {
-        __threadfence();
-        double b[3] = {0.0, 0.0, 0.0};
-        for (int v = threadIdx.x; v < I.nvt; v += blockDim.x) {
-            const double* vp = I.vpart + (long long)v * VP;
-            b[0] += __ldcg(vp + 0);
-            b[1] += __ldcg(vp + 1);
-            b[2] += __ldcg(vp + 2);
-        }
-        block_sum<3>(b, red);
-        if (threadIdx.x == 0) {
-            *I.ticket = 0u;
-            finalize_step(S, b[2], b[0], b[1]);
+    int status = ST_RUNNING;
+    double sigma = 0.0, b = 0.0, r = 0.0, y = 0.0, ybar = 0.0;
+    long long k = 0;
+    double* Vn = nullptr;
+    double* Vbn = nullptr;
+    if (grp == 0) {
+        status = S->status;
+        sigma = S->sigma;
+        k = S->k;
+        const double* Vc = slot_v(I, S->cur);
+        const double* Vb = slot_v(I, S->bar);
+        Vn = slot_v(I, S->nxt);
+        Vbn = slot_v(I, S->barn);
+        if (row || col) {
+            b = row ? I.f[idx] : I.g[idx];
+            r = Vc[so];
+            y = Vc[yo];
+            if (k != 0) ybar = Vb[yo];
         }
     }
+    double s = 0.0;
+    if (row || col) {
+        const double* part = row ? I.rowpart : I.colpart;
+        const long long stride = row ? m : I.ldx;
+        const int count = row ? I.nstrips : I.nchunks;
+#pragma unroll 8
+        for (int kk = grp; kk < count; kk += VG) s += part[(long long)kk * stride + idx];
+    }
+    sgrp[grp * 32 + lane] = s;
     __syncthreads();
+    if (grp == 0 && status == ST_RUNNING) {
+        double t = 0.0;
+#pragma unroll
+        for (int g2 = 0; g2 < VG; ++g2) t += sgrp[g2 * 32 + lane];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;   // ||dy||^2, dy^T A dx, ||dX||^2 (this tile's slice)
+        if (row || col) {
+            const double w = 1.0 / (double)(k + 1);
+            const double yn = y + sigma * (b - (2.0 * t - r));
+            Vn[yo] = yn;
+            Vn[so] = t;
+            Vbn[yo] = k == 0 ? yn : ybar + w * (yn - ybar);
+            const double dy = yn - y;
+            a0 = dy * dy;
+            a1 = dy * (t - r);
+        }
+        {
+            const long long T = I.ntiles;
+            const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+            for (long long tt = t0 + lane; tt < t1; tt += 32) a2 += I.tpart[tt * TP + 0];
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        unsigned old = 0;
+        if (lane == 0) {
+            double* vp = I.vpart + (long long)lvt * VP;
+            vp[0] = a0; vp[1] = a1; vp[2] = a2;
+            __threadfence();
+            old = atomicAdd(I.ticket, 1u);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old == (unsigned)(I.nvt - 1)) {
+            __threadfence();
+            double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+            for (int v = lane; v < I.nvt; v += 32) {
+                const double* vp = I.vpart + (long long)v * VP;
+                b0 += __ldcg(vp + 0);
+                b1 += __ldcg(vp + 1);
+                b2 += __ldcg(vp + 2);
+            }
+            b0 = warp_sum(b0);
+            b1 = warp_sum(b1);
+            b2 = warp_sum(b2);
+            if (lane == 0) {
+                *I.ticket = 0u;
+                finalize_step(S, b2, b0, b1);
+            }
+        }
+    }
+    __syncthreads();   // sgrp is reused by the caller's next tile
 }
 
 __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                              const int* __restrict__ NVp, unsigned* wctr) {
     // One CTA per vector tile (no work queue): the grid covers the tile count.
-    __shared__ double red[(VT / 32) * 3];
     __shared__ double sgrp[VG * 32];
-    __shared__ int s_last;
     pdl_enter();
     // No work counter of its own, but it still resets the others for the
     // kernels that follow (block 0, before any early exit).
@@ -1284,9 +1385,9 @@ __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, con
     if ((int)blockIdx.x >= NV) return;
     const TileRef tr = vmap[blockIdx.x];
     const Inst& I = insts[tr.inst];
-    Ctrl* S = I.ctrl;
-    if (S->status != ST_RUNNING) return;
-    dual_tile(I, S, tr.local, red, sgrp, &s_last);
+    // The instance's status is read inside (warp 0), next to the other
+    // controller fields; a finished instance's tile does nothing.
+    dual_tile(I, I.ctrl, tr.local, sgrp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1713,9 +1814,7 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         for (int vt = blockIdx.x; vt < NV; vt += G) {
             const TileRef tr = vmap[vt];
             const Inst& I = insts[tr.inst];
-            Ctrl* S = I.ctrl;
-            if (S->status != ST_RUNNING) continue;
-            dual_tile(I, S, tr.local, red, sgrp, &s_last);
+            dual_tile(I, I.ctrl, tr.local, sgrp);
         }
         ok = grid_barrier(gb, G, &s_ok);
     }
@@ -1792,8 +1891,12 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
     const bool pdl = cfg.pdl != 0;
     const unsigned tb = (unsigned)cfg.tile_blocks, th = TWARPS * 32;
     if (ttype == TT_GEN) {
-        // Generated cost: the per-row bulk pipeline (X and Xbar copies only),
-        // or the register pipeline when the bulk kernels are switched off.
+        // Generated cost: the bulk pipelines copy X and Xbar only (the grouped
+        // one for up to 4 coordinates), or the register pipeline when the
+        // bulk kernels are switched off.
+        if (cfg.pass_bulk == 2 && cfg.gen_dims <= 4)
+            return launch_k(pdl, k_pass_group<GenC4, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc);
         if (cfg.pass_bulk && cfg.gen_dims <= 4)
             return launch_k(pdl, k_pass_bulk<GenC4, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
                             d_tmap, T, wctr, wc);
@@ -1935,10 +2038,14 @@ int setup_group_pass() {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_pass_group<unsigned short, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return (int)e;
-    int a = 0, b = 0;
+    e = cudaFuncSetAttribute(k_pass_group<GenC4, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return (int)e;
+    int a = 0, b = 0, c = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_group<float, GROUP_S>, TWARPS * 32, bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_group<unsigned short, GROUP_S>, TWARPS * 32, bytes);
-    const int r = a < b ? a : b;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass_group<GenC4, GROUP_S>, TWARPS * 32, bytes);
+    int r = a < b ? a : b;
+    if (c < r) r = c;
     return -(r > 0 ? r : 1);
 }
 

@@ -273,6 +273,16 @@ KERNEL_NAMES = {0: "k_pass (register pipeline)", 1: "k_pass_bulk<float, 8> (bulk
                 2: "k_pass_group<float, 2> (bulk copies per 4-row group)"}
 
 
+def kernel_name(variant: int, c_dtype: int) -> str:
+    """Name of the pass kernel a variant code and cost type select."""
+    tc = {F32: "float", BF16: "unsigned short", F64: "double", POINTS: "GenC"}.get(c_dtype, "?")
+    if variant == 0:
+        return f"k_pass<{tc}, ...> (register pipeline)"
+    if variant == 1:
+        return f"k_pass_bulk<{tc}, 8> (bulk copies per row)"
+    return f"k_pass_group<{tc}, 2> (bulk copies per 4-row group)"
+
+
 def pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps):
     """Returns (status, ms per pass, algorithmic bytes per pass, kernel variant)."""
     ms, b, kv = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()

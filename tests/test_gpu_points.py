@@ -257,3 +257,43 @@ def test_points_fullsize_rect_l1_sampled_rows():
     q_expect = q2 + eta * (torch.tensor(g, device=DEV) - (2.0 * c3 - c2))
     assert (torch.linalg.norm(q3 - q_expect) / torch.linalg.norm(q_expect)).item() < 1e-5
     s.close()
+
+
+def test_points_grouped_kernel(monkeypatch):
+    """The grouped bulk kernel (4-row stages; the autotuner's pick for large
+    shapes) with generated costs: bit-identical to it with the stored cost on
+    a pixel grid, and k-step parity with the oracle on random points."""
+    monkeypatch.setenv("PDOT_PASS_BULK", "2")
+    G = 32
+    ins = I.grid_blob_instance(G, I.seed_for(1, 7))
+    P = _grid(G)
+    div = float(2 * (G - 1) ** 2)
+    a = pdot.Solver(device=0, time_limit_s=120.0)
+    b = pdot.Solver(device=0, time_limit_s=120.0)
+    ra = a.solve(torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g, tol=1e-6)
+    rb = b.solve(pdot.Points(P, P, "sqeuclid", div), ins.f, ins.g, tol=1e-6)
+    assert ra.status == pdot.OK and rb.status == pdot.OK
+    assert ra.result["passes"] == rb.result["passes"] and torch.equal(ra.X, rb.X) and torch.equal(ra.p, rb.p)
+    Pd = torch.tensor(P, device=DEV)
+    desc = pdot.PointsCostDesc(d=2, dist=0, xs=Pd.data_ptr(), ys=Pd.data_ptr(), divisor=div)
+    import ctypes
+    f = torch.tensor(ins.f, device=DEV)
+    g = torch.tensor(ins.g, device=DEV)
+    st, _, _, variant = pdot.pdot_time_pass(b.h, G * G, G * G, ctypes.addressof(desc), pdot.POINTS, 0,
+                                            f.data_ptr(), g.data_ptr(), 3)
+    assert st == pdot.OK and variant == 2
+    a.close()
+    b.close()
+    s = pdot.Solver(device=0)
+    m, n = 300, 517
+    xs, ys, f, g = _points(m, n, 3, 4242)
+    Co = oracle.points_cost(xs.astype(np.float64), ys.astype(np.float64), "l1", 3.0)
+    rng = np.random.default_rng(3)
+    X0 = (rng.random((m, n)) / (m * n)).astype(np.float32).astype(np.float64)
+    p0, q0 = rng.standard_normal(m) * 0.05, rng.standard_normal(n) * 0.05
+    eta = 0.5 / math.sqrt(m + n)
+    gp = s.pdhg_steps(pdot.Points(xs, ys, "l1", 3.0), f, g, X0, p0, q0, k=20, eta=eta, omega=1.7)
+    o = oracle.pdhg_steps(Co, f, g, X0, p0, q0, k=20, eta=eta, omega=1.7)
+    assert rel(_np(gp[0]), o[0]) < 1e-5 and rel(_np(gp[3]), o[3]) < 1e-5
+    assert rel(np.concatenate([_np(gp[1]), _np(gp[2])]), np.concatenate([o[1], o[2]])) < 1e-5
+    s.close()
