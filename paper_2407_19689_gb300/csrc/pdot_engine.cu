@@ -441,7 +441,7 @@ void run_check(pdot_handle* h, int ttype, int mode) {
 void run_step(pdot_handle* h, int ttype) {
     const Work& w = h->ws;
     CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream));
-    CKL(launch_dual(h->d_inst, h->d_vmap, h->d_cnt + 1, w.nvt, h->wctr, h->cfg, h->stream));
+    CKL(launch_dual(h->d_inst, h->d_vmap, h->d_cnt + 1, w.nvt, h->wctr, h->cfg, h->stream, true));
     launch_count(h, 2);
 }
 

@@ -172,7 +172,7 @@ struct LaunchCfg {
 int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream, int wc_override = -1);
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
-                const LaunchCfg& cfg, void* stream);
+                const LaunchCfg& cfg, void* stream, bool direct = false);
 int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,
                const LaunchCfg& cfg, void* stream);
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,

@@ -188,6 +188,28 @@ __device__ __forceinline__ int warp_next(unsigned* ctr) {
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
+// Tile queue of the plan kernels: a warp's first tile is its global warp
+// index (no atomic on the path to the first load); later tiles come from the
+// counter, after all first tiles.  Which warp runs a tile does not change its
+// arithmetic, so results do not depend on the assignment.
+__device__ __forceinline__ int tile_next(unsigned* ctr, bool& first) {
+    const int W = (int)(gridDim.x * (blockDim.x >> 5));
+    if (first) {
+        first = false;
+        return (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    }
+    return W + warp_next(ctr);
+}
+
+// Arrival on an instance's ticket: the atomic releases this thread's earlier
+// writes and, for the last arrival, acquires the others' (one acquire-release
+// atomic instead of two sequentially consistent fences).
+__device__ __forceinline__ unsigned ticket_arrive(unsigned* ctr) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    return old;
+}
+
 // Programmatic dependent launch: wait for the previous grid in the stream
 // (completion and memory visibility; a no-op without the launch attribute),
 // then let the next grid start launching its CTAs.  Every solve-loop kernel
@@ -320,8 +342,9 @@ k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const i
     const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
+    bool first = true;
     for (;;) {
-        const int t = warp_next(&wctr[wc]);
+        const int t = tile_next(&wctr[wc], first);
         if (t >= T) break;
         const TileRef tr = tmap[t];
         const Inst& I = insts[tr.inst];
@@ -471,9 +494,10 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     bool p_hint = false;                // keep this instance's C in L2 (it fits)
     const unsigned long long pol_keep = policy_evict_last();
     const unsigned long long pol_stream = policy_evict_first();
+    bool q_first = true;
     auto next_tile = [&]() {
         for (;;) {
-            p_tile = warp_next(qctr);
+            p_tile = tile_next(qctr, q_first);
             if (p_tile >= T) return;
             const TileRef tr = tmap[p_tile];
             const Inst& I = insts[tr.inst];
@@ -879,9 +903,10 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     long long p_cstride = 0, p_xstride = 0;
     unsigned p_cbytes = 0, p_xbytes = 0;
     bool p_first = true;
+    bool q_first = true;
     auto next_tile = [&]() {
         for (;;) {
-            p_tile = warp_next(&wctr[wc]);
+            p_tile = tile_next(&wctr[wc], q_first);
             if (p_tile >= T) return;
             const TileRef tr = tmap[p_tile];
             const Inst& I = insts[tr.inst];
@@ -1222,8 +1247,10 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
     if (S->adaptive_step) {
         // Sec. 5 step-size rule in the PDLP form (reading C6); the exponent base
         // is the 1-based index of the attempted iteration plus one.
+        // (w dX2 + dy2 / w) / (2 |inter|) with a single division (FP64
+        // divisions are long dependent chains on this serial path).
         const double om = S->omega;
-        const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
+        const double etabar = inter != 0.0 ? (om * om * dX2 + dy2) / (2.0 * om * fabs(inter)) : CUDART_INF;
         // The two schedule factors are heuristics; single precision is ample
         // (GB300's FP64 transcendentals are slow on this serial path).
         const float t1 = (float)(S->total + 2);
@@ -1348,12 +1375,11 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
         if (lane == 0) {
             double* vp = I.vpart + (long long)lvt * VP;
             vp[0] = a0; vp[1] = a1; vp[2] = a2;
-            __threadfence();
-            old = atomicAdd(I.ticket, 1u);
+            old = ticket_arrive(I.ticket);
         }
         old = __shfl_sync(0xffffffffu, old, 0);
+        __syncwarp();
         if (old == (unsigned)(I.nvt - 1)) {
-            __threadfence();
             double b0 = 0.0, b1 = 0.0, b2 = 0.0;
             for (int v = lane; v < I.nvt; v += 32) {
                 const double* vp = I.vpart + (long long)v * VP;
@@ -1374,16 +1400,24 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
 }
 
 __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
-                                             const int* __restrict__ NVp, unsigned* wctr) {
+                                             const int* __restrict__ NVp, unsigned* wctr, int direct) {
     // One CTA per vector tile (no work queue): the grid covers the tile count.
+    // direct: one instance whose vector tiles are exactly the grid (no map or
+    // count to read before the work).
     __shared__ double sgrp[VG * 32];
     pdl_enter();
     // No work counter of its own, but it still resets the others for the
     // kernels that follow (block 0, before any early exit).
     reset_other_counters(wctr, wc_index(WC_DUAL, 0));
-    const int NV = *NVp;
-    if ((int)blockIdx.x >= NV) return;
-    const TileRef tr = vmap[blockIdx.x];
+    TileRef tr;
+    if (direct) {
+        tr.inst = 0;
+        tr.local = (int)blockIdx.x;
+    } else {
+        const int NV = *NVp;
+        if ((int)blockIdx.x >= NV) return;
+        tr = vmap[blockIdx.x];
+    }
     const Inst& I = insts[tr.inst];
     // The instance's status is read inside (warp 0), next to the other
     // controller fields; a finished instance's tile does nothing.
@@ -1504,8 +1538,9 @@ k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const in
     const int T = *Tp;
     reset_other_counters(wctr, wc);
     const int lane = threadIdx.x & 31;
+    bool first = true;
     for (;;) {
-        const int t = warp_next(&wctr[wc]);
+        const int t = tile_next(&wctr[wc], first);
         if (t >= T) break;
         const TileRef tr = tmap[t];
         const Inst& I = insts[tr.inst];
@@ -1702,13 +1737,11 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
         double* vp = I.vpart + (long long)lvt * VP;
 #pragma unroll
         for (int k = 0; k < VP; ++k) vp[k] = a[k];
-        __threadfence();
-        const unsigned old = atomicAdd(I.ticket, 1u);
+        const unsigned old = ticket_arrive(I.ticket);
         *s_last = (old == (unsigned)(I.nvt - 1));
     }
     __syncthreads();
     if (*s_last) {
-        __threadfence();
         double b[VP];
 #pragma unroll
         for (int k = 0; k < VP; ++k) b[k] = 0.0;
@@ -1819,8 +1852,9 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         ok = grid_barrier(gb, G, &s_ok);
     }
     if (ok && *(volatile int*)&S0->status == ST_RUNNING) {
+        bool first = true;
         for (;;) {
-            const int t = warp_next(&wctr[wc_kkt]);
+            const int t = tile_next(&wctr[wc_kkt], first);
             if (t >= T) break;
             const TileRef tr = tmap[t];
             const Inst& I = insts[tr.inst];
@@ -1931,11 +1965,13 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
     return launch_k(pdl, k_pass<float, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
 }
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
-                const LaunchCfg& cfg, void* stream) {
-    // nv_hint: an upper bound of the vector-tile count (one CTA each).
+                const LaunchCfg& cfg, void* stream, bool direct) {
+    // nv_hint: an upper bound of the vector-tile count (one CTA each); with
+    // direct, exactly the count of the single instance's vector tiles.
     int blocks = nv_hint;
     if (blocks < 1) blocks = 1;
-    return launch_k(cfg.pdl != 0, k_dual, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV, wctr);
+    return launch_k(cfg.pdl != 0, k_dual, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV, wctr,
+                    direct ? 1 : 0);
 }
 int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,
                const LaunchCfg& cfg, void* stream) {
