@@ -942,14 +942,31 @@ struct BatchEngine {
     DevArr<TileRef> vmap;
     DevArr<TileRef> tmap_init[NTT];
     DevArr<TileRef> vmap_init;
-    DevArr<Ctrl> snap;
+    DevArr<Ctrl> snap[2];     // controller snapshots of the two chunks that can be in flight
     DevArr<Ctrl> ctrl_stage;
     DevArr<int> cnt;          // counts, laid out as the CNT_* indices below
     Graph graph;
     int gen_dims = 0;         // largest d of the live generated costs
     long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaEvent_t ev_chunk = nullptr, ev_copy = nullptr;
-    bool inflight = false;
+    // Chunks in flight (oldest first, at most two): each one's snapshot buffer
+    // and the instance ids in the order its snapshot lists them.
+    struct Flight {
+        int buf = 0;
+        std::vector<uint64_t> ids;
+    };
+    std::deque<Flight> flights;
+    cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+    int next_buf = 0;
+    // Pinned staging (instance table, maps, counts, controllers) is rewritten
+    // only after the copies that read it last have run.
+    cudaEvent_t ev_staged = nullptr;
+    bool staged_pending = false;
+    // Results whose output copies are queued behind a chunk still in flight.
+    struct Pending {
+        cudaEvent_t ev = nullptr;
+        std::vector<std::pair<uint64_t, pdot_result>> results;
+    };
+    std::deque<Pending> pending_done;
     int nv_live = 0;
     int nv_grid = 32;          // vector-kernel grid: live vector tiles rounded up to a power of two
     int64_t chunks = 0;
@@ -968,8 +985,9 @@ BatchEngine* batch_of(pdot_handle* h) {
     if (!h->batch) {
         BatchEngine* B = new BatchEngine();
         h->batch = B;
-        CK(cudaEventCreateWithFlags(&B->ev_chunk, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&B->ev_copy, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&B->ev_chunk[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&B->ev_chunk[1], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&B->ev_staged, cudaEventDisableTiming));
         if (h->opt.hbm_budget_bytes > 0) {
             B->budget = (size_t)h->opt.hbm_budget_bytes;
         } else {
@@ -994,7 +1012,6 @@ void batch_compose(pdot_handle* h) {
     BatchEngine* B = h->batch;
     const int L = (int)B->live.size();
     B->insts.ensure((size_t)std::max(L, 1));
-    B->snap.ensure(B->insts.cap);
     size_t nt[NTT] = {}, nti[NTT] = {}, nv = 0, nvi = 0;
     int gd = 0;
     for (BSlot* s : B->live) {
@@ -1098,9 +1115,6 @@ void batch_issue_chunk(pdot_handle* h, int types) {
         launch_count(h, 1);
     }
     (void)nvh;
-    CKL(launch_snapshot(B->insts.d, B->cnt.d + CNT_INST, (int)B->snap.cap, B->snap.d, st));
-    launch_count(h, 1);
-    CK(cudaMemcpyAsync(B->snap.h, B->snap.d, sizeof(Ctrl) * B->snap.cap, cudaMemcpyDeviceToHost, st));
 }
 
 void batch_launch_chunk(pdot_handle* h) {
@@ -1110,10 +1124,10 @@ void batch_launch_chunk(pdot_handle* h) {
     h->cfg.gen_dims = B->gen_dims;
     long long tmaps = 0;
     for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
-    const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->snap.d,
+    const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->cnt.d,
                               (long long)(uintptr_t)B->vmap.d, tmaps,
                               types | ((long long)B->nv_grid << 8) | ((long long)B->gen_dims << 48),
-                              h->opt.restart_check_every, h->opt.chunk_checks, (long long)B->snap.cap};
+                              h->opt.restart_check_every, h->opt.chunk_checks, 0};
     if (!h->opt.use_graph) {
         batch_issue_chunk(h, types);
     } else {
@@ -1139,8 +1153,21 @@ void batch_launch_chunk(pdot_handle* h) {
         CK(cudaGraphLaunch(B->graph.exec, h->stream));
         launch_count(h, B->graph.kernels);
     }
-    CK(cudaEventRecord(B->ev_chunk, h->stream));
-    B->inflight = true;
+    // Controller snapshot of this chunk into its own buffer (the other one may
+    // still belong to the chunk before it).
+    BatchEngine::Flight f;
+    f.buf = B->next_buf;
+    B->next_buf ^= 1;
+    DevArr<Ctrl>& snap = B->snap[f.buf];
+    snap.ensure(B->insts.cap);
+    const int L = (int)B->live.size();
+    CKL(launch_snapshot(B->insts.d, B->cnt.d + CNT_INST, L, snap.d, h->stream));
+    launch_count(h, 1);
+    CK(cudaMemcpyAsync(snap.h, snap.d, sizeof(Ctrl) * (size_t)L, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(B->ev_chunk[f.buf], h->stream));
+    f.ids.reserve((size_t)L);
+    for (BSlot* sl : B->live) f.ids.push_back(sl->id);
+    B->flights.push_back(std::move(f));
     B->chunks += 1;
 }
 
@@ -1156,16 +1183,27 @@ pdot_result batch_result(pdot_handle* h, const BSlot* s, int status) {
     return r;
 }
 
-// Retire finished / cancelled / timed-out instances; true if any left.
-bool batch_retire(pdot_handle* h) {
+// Retire the instances that finished (or were cancelled / timed out) by the
+// end of chunk `f`, whose snapshot lists them in f.ids order; their output
+// copies are queued behind every chunk still in flight and their results are
+// reported once those copies have run.  True if any instance left.
+bool batch_retire(pdot_handle* h, const BatchEngine::Flight& f) {
     BatchEngine* B = h->batch;
     bool changed = false;
+    std::map<uint64_t, size_t> pos;
+    for (size_t i = 0; i < f.ids.size(); ++i) pos[f.ids[i]] = i;
     std::vector<BSlot*> keep;
     keep.reserve(B->live.size());
+    std::vector<std::pair<uint64_t, pdot_result>> res;
     const double tlim = h->opt.time_limit_s;
     for (size_t i = 0; i < B->live.size(); ++i) {
         BSlot* s = B->live[i];
-        s->last = B->snap.h[i];
+        const auto it = pos.find(s->id);
+        if (it == pos.end()) {   // admitted after chunk f was launched
+            keep.push_back(s);
+            continue;
+        }
+        s->last = B->snap[f.buf].h[it->second];
         int stt = s->last.status;
         if (s->cancel) stt = ST_CANCELLED;
         else if (stt == ST_RUNNING && tlim > 0.0 &&
@@ -1194,11 +1232,18 @@ bool batch_retire(pdot_handle* h) {
                                    h->stream));
         }
         batch_free_slot(h, s);
-        B->done.emplace_back(s->id, batch_result(h, s, stt));
+        res.emplace_back(s->id, batch_result(h, s, stt));
         delete s;
         changed = true;
     }
     B->live.swap(keep);
+    if (!res.empty()) {
+        BatchEngine::Pending p;
+        CK(cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(p.ev, h->stream));
+        p.results = std::move(res);
+        B->pending_done.push_back(std::move(p));
+    }
     return changed;
 }
 
@@ -1265,21 +1310,63 @@ void batch_apply_cancels(pdot_handle* h) {
     }
 }
 
+void batch_retire_front(pdot_handle* h, bool& changed) {
+    BatchEngine* B = h->batch;
+    const BatchEngine::Flight& f = B->flights.front();
+    CK(cudaEventSynchronize(B->ev_chunk[f.buf]));
+    changed |= batch_retire(h, f);
+    B->flights.pop_front();
+}
+
+// Move results whose output copies have run to `done` (all of them, waiting,
+// when `wait`).
+void batch_collect(pdot_handle* h, bool wait) {
+    BatchEngine* B = h->batch;
+    while (!B->pending_done.empty()) {
+        BatchEngine::Pending& p = B->pending_done.front();
+        if (wait) {
+            CK(cudaEventSynchronize(p.ev));
+        } else {
+            const cudaError_t q = cudaEventQuery(p.ev);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) throw CudaError{q};
+        }
+        cudaEventDestroy(p.ev);
+        for (auto& r : p.results) B->done.push_back(r);
+        B->pending_done.pop_front();
+    }
+}
+
+// One poll: retire what finished, admit, and keep up to two chunks in flight
+// (the device runs chunk i+1 while the host retires chunk i and prepares
+// chunk i+2).
 pdot_status batch_poll(pdot_handle* h, uint64_t* ids, pdot_result* results, int cap, int* n_done) {
     BatchEngine* B = batch_of(h);
-    if (B->inflight) {
-        CK(cudaEventSynchronize(B->ev_chunk));
-        B->inflight = false;
-        batch_retire(h);
+    bool changed = false;
+    if (B->flights.size() >= 2) batch_retire_front(h, changed);
+    while (!B->flights.empty()) {
+        const cudaError_t q = cudaEventQuery(B->ev_chunk[B->flights.front().buf]);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) throw CudaError{q};
+        batch_retire_front(h, changed);
+    }
+    // The pinned staging buffers are rewritten below: the copies that read
+    // them for the previous chunk must have run.
+    if (B->staged_pending) {
+        CK(cudaEventSynchronize(B->ev_staged));
+        B->staged_pending = false;
     }
     batch_apply_cancels(h);
-    bool changed = batch_admit(h);
-    const bool had_done = !B->done.empty();
-    if (had_done) CK(cudaEventRecord(B->ev_copy, h->stream));
+    changed |= batch_admit(h);
     if (changed || B->chunks == 0) batch_compose(h);
-    else if (had_done) batch_compose(h);
-    if (!B->live.empty()) batch_launch_chunk(h);
-    if (had_done) CK(cudaEventSynchronize(B->ev_copy));
+    CK(cudaEventRecord(B->ev_staged, h->stream));
+    B->staged_pending = true;
+    if (!B->live.empty()) {
+        batch_launch_chunk(h);
+    } else {
+        while (!B->flights.empty()) batch_retire_front(h, changed);
+    }
+    batch_collect(h, B->live.empty() && B->flights.empty());
     int k = 0;
     const int take = std::min<int>(cap, (int)B->done.size());
     for (; k < take; ++k) {
@@ -1302,6 +1389,8 @@ void batch_destroy(pdot_handle* h) {
     for (BSlot* s : B->queue) delete s;
     if (h->stream) cudaStreamSynchronize(h->stream);
     B->graph.reset();
+    for (auto& p : B->pending_done) cudaEventDestroy(p.ev);
+    B->pending_done.clear();
     B->insts.release();
     for (int t = 0; t < NTT; ++t) {
         B->tmap[t].release();
@@ -1309,11 +1398,13 @@ void batch_destroy(pdot_handle* h) {
     }
     B->vmap.release();
     B->vmap_init.release();
-    B->snap.release();
+    B->snap[0].release();
+    B->snap[1].release();
     B->ctrl_stage.release();
     B->cnt.release();
-    if (B->ev_chunk) cudaEventDestroy(B->ev_chunk);
-    if (B->ev_copy) cudaEventDestroy(B->ev_copy);
+    for (int k = 0; k < 2; ++k)
+        if (B->ev_chunk[k]) cudaEventDestroy(B->ev_chunk[k]);
+    if (B->ev_staged) cudaEventDestroy(B->ev_staged);
     delete B;
     h->batch = nullptr;
 }
@@ -1706,8 +1797,11 @@ pdot_status pdot_cancel(pdot_handle* h, uint64_t ticket) {
 pdot_status pdot_batch_pending(pdot_handle* h, int* queued, int* running) {
     if (!h) return PDOT_ERR_ARG;
     BatchEngine* B = h->batch;
+    size_t waiting = 0;   // finished, results not yet reported
+    if (B)
+        for (const auto& p : B->pending_done) waiting += p.results.size();
     if (queued) *queued = B ? (int)B->queue.size() : 0;
-    if (running) *running = B ? (int)B->live.size() : 0;
+    if (running) *running = B ? (int)(B->live.size() + waiting) : 0;
     return PDOT_OK;
 }
 
