@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: the --serve-loads sweep)")
+    ap.add_argument("--active-mb", type=float, default=400.0,
+                    help="serving: per-pass plan megabytes the active-budget engine advances together")
     ap.add_argument("--serve-loads", default="0.5,0.8,1.1",
                     help="offered loads as fractions of the one-at-a-time server's measured capacity")
     ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
@@ -467,13 +469,19 @@ def run_serve(args):
         rate = load * capacity
         reqs = I.serve_requests(args.requests, rate, I.seed_for(4), hi=args.serve_max)
         rb = serve.serve_batched(reqs, **lim)
-        sb = serve.summary(rb)
+        sb = serve.summary(rb, reqs)
+        # the same engine with an active-bytes budget: the oldest solve keeps
+        # the bandwidth, small ones fill in beside it
+        ra = serve.serve_batched(reqs, batch_active_bytes=int(args.active_mb * 1e6), **lim)
+        sa = serve.summary(ra, reqs)
         rp = serve.serve_plain(reqs, **lim)
-        sp = serve.summary(rp)
+        sp = serve.summary(rp, reqs)
         diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
         points.append({"load_vs_plain_capacity": load, "rate_per_s": rate, "continuous_batching": sb,
-                       "plain_fifo": sp, "p50_ratio_plain_over_batched": sp["p50_s"] / sb["p50_s"],
+                       "continuous_batching_active_budget": sa, "plain_fifo": sp,
+                       "p50_ratio_plain_over_batched": sp["p50_s"] / sb["p50_s"],
                        "p99_ratio_plain_over_batched": sp["p99_s"] / sb["p99_s"],
+                       "p99_ratio_plain_over_active_budget": sp["p99_s"] / sa["p99_s"],
                        "max_rel_obj_diff_vs_plain": float(np.max(diffs)) if diffs else None})
         print(json.dumps({"progress": points[-1]}), file=sys.stderr, flush=True)
     top = points[-1]
@@ -484,6 +492,7 @@ def run_serve(args):
             "data": "synthetic",
             "config": {"workload": f"serve{args.requests}_poisson_loguniform128-{args.serve_max}",
                        "plain_capacity_per_s": capacity, "admission_budget_bytes": 150 << 30,
+                       "active_budget_bytes": int(args.active_mb * 1e6),
                        "value_at_load": top["load_vs_plain_capacity"]},
             "loads": points}
     print(json.dumps(line), flush=True)
@@ -533,10 +542,11 @@ def run_pass_sweep(args):
         cost = pdot.PointsCostDesc(d=2, dist=pdot.DIST["sqeuclid"], xs=Pf.data_ptr(), ys=Pf.data_ptr(),
                                    divisor=float(2 * (G - 1) ** 2))
         s = pdot.Solver(device=0)
-        st, ms, b, _ = pdot.pdot_time_pass(s.h, m, n, ctypes.addressof(cost), pdot.POINTS, 0, f.data_ptr(),
-                                           g.data_ptr(), 30 if G == 64 else 10)
+        st, ms, b, var = pdot.pdot_time_pass(s.h, m, n, ctypes.addressof(cost), pdot.POINTS, 0, f.data_ptr(),
+                                             g.data_ptr(), 30 if G == 64 else 10)
         s.close()
-        row = {"m": m, "kernel": "bulk-row, generated cost", "tile_rows": "auto", "us": ms * 1e3,
+        row = {"m": m, "kernel": "generated cost, " + {0: "register", 1: "bulk-row", 2: "bulk-group"}.get(var, "?"),
+               "tile_rows": "auto", "us": ms * 1e3,
                "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
         out.append(row)
         print(json.dumps(row), flush=True)

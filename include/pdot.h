@@ -110,6 +110,10 @@ typedef struct {
     uint64_t hbm_budget_bytes;     /* batch admission budget; 0: 90% of free memory at create */
     int32_t max_batch_slots;       /* most instances resident at once in the batch engine */
     int32_t chunk_checks;          /* check periods per batch chunk launch (serving granularity) */
+    uint64_t batch_active_bytes;   /* 0: every resident batch instance advances in every chunk.  Otherwise
+                                      a chunk advances the oldest resident instance, then younger ones in
+                                      admission order whose per-pass plan bytes still fit this budget
+                                      (large solves keep the bandwidth; small ones fill in beside them) */
 } pdot_options;
 
 typedef struct {

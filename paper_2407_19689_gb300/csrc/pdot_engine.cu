@@ -946,7 +946,8 @@ struct BatchEngine {
     DevArr<Ctrl> ctrl_stage;
     DevArr<int> cnt;          // counts, laid out as the CNT_* indices below
     Graph graph;
-    int gen_dims = 0;         // largest d of the live generated costs
+    int gen_dims = 0;         // largest d of the active generated costs
+    int types = 0;            // plan-kernel types of the active instances (bit mask)
     long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // Chunks in flight (oldest first, at most two): each one's snapshot buffer
     // and the instance ids in the order its snapshot lists them.
@@ -1012,12 +1013,33 @@ void batch_compose(pdot_handle* h) {
     BatchEngine* B = h->batch;
     const int L = (int)B->live.size();
     B->insts.ensure((size_t)std::max(L, 1));
+    // The instances the next chunk advances: all, or the oldest and then
+    // younger ones (admission order) whose per-pass plan bytes fit the
+    // active budget.  A paused instance keeps its state; its trajectory only
+    // depends on its own passes, which always come in whole check periods.
+    std::vector<char> active((size_t)L, 1);
+    if (h->opt.batch_active_bytes > 0) {
+        const double cap = (double)h->opt.batch_active_bytes;
+        double used = 0.0;
+        for (int i = 0; i < L; ++i) {
+            const BSlot* s = B->live[(size_t)i];
+            const double b = (double)s->req.m * (double)s->req.n *
+                             ((double)csize_of(s->req.c_dtype) + 4.0 * (double)xsize_of(h->opt.x_dtype));
+            active[(size_t)i] = (i == 0 || used + b <= cap) ? 1 : 0;
+            if (active[(size_t)i]) used += b;
+        }
+    }
     size_t nt[NTT] = {}, nti[NTT] = {}, nv = 0, nvi = 0;
     int gd = 0;
-    for (BSlot* s : B->live) {
-        if (s->req.c_dtype == PDOT_POINTS) gd = std::max(gd, (int)s->pts.d);
-        nt[s->ttype] += (size_t)s->w.ntiles;
-        nv += (size_t)s->w.nvt;
+    B->types = 0;
+    for (int i = 0; i < L; ++i) {
+        BSlot* s = B->live[(size_t)i];
+        if (active[(size_t)i]) {
+            B->types |= 1 << s->ttype;
+            if (s->req.c_dtype == PDOT_POINTS) gd = std::max(gd, (int)s->pts.d);
+            nt[s->ttype] += (size_t)s->w.ntiles;
+            nv += (size_t)s->w.nvt;
+        }
         if (s->fresh) {
             nti[s->ttype] += (size_t)s->w.ntiles;
             nvi += (size_t)s->w.nvt;
@@ -1041,12 +1063,13 @@ void batch_compose(pdot_handle* h) {
         }
         B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
         const int tt = s->ttype;
+        const bool act = active[(size_t)i] != 0;
         for (int t = 0; t < s->w.ntiles; ++t) {
-            B->tmap[tt].h[ot[tt]++] = TileRef{i, t};
+            if (act) B->tmap[tt].h[ot[tt]++] = TileRef{i, t};
             if (s->fresh) B->tmap_init[tt].h[oti[tt]++] = TileRef{i, t};
         }
         for (int t = 0; t < s->w.nvt; ++t) {
-            B->vmap.h[ov++] = TileRef{i, t};
+            if (act) B->vmap.h[ov++] = TileRef{i, t};
             if (s->fresh) B->vmap_init.h[ovi++] = TileRef{i, t};
         }
     }
@@ -1119,8 +1142,7 @@ void batch_issue_chunk(pdot_handle* h, int types) {
 
 void batch_launch_chunk(pdot_handle* h) {
     BatchEngine* B = h->batch;
-    int types = 0;
-    for (BSlot* s : B->live) types |= 1 << s->ttype;
+    const int types = B->types;
     h->cfg.gen_dims = B->gen_dims;
     long long tmaps = 0;
     for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
@@ -1358,7 +1380,8 @@ pdot_status batch_poll(pdot_handle* h, uint64_t* ids, pdot_result* results, int 
     }
     batch_apply_cancels(h);
     changed |= batch_admit(h);
-    if (changed || B->chunks == 0) batch_compose(h);
+    // With an active-bytes budget the advancing set can change every chunk.
+    if (changed || B->chunks == 0 || h->opt.batch_active_bytes > 0) batch_compose(h);
     CK(cudaEventRecord(B->ev_staged, h->stream));
     B->staged_pending = true;
     if (!B->live.empty()) {
@@ -1443,6 +1466,7 @@ void pdot_default_options(pdot_options* o) {
     o->hbm_budget_bytes = 0;
     o->max_batch_slots = 4096;
     o->chunk_checks = 4;
+    o->batch_active_bytes = 0;
 }
 
 const char* pdot_status_str(pdot_status s) {

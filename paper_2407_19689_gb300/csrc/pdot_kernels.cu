@@ -211,15 +211,9 @@ __device__ __forceinline__ unsigned ticket_arrive(unsigned* ctr) {
 }
 
 // Programmatic dependent launch: wait for the previous grid in the stream
-// (completion and memory visibility; a no-op without the launch attribute),
-// then let the next grid start launching its CTAs.  Every solve-loop kernel
-// calls this before touching any data or work counter.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-#ifdef PDOT_PDL_EARLY
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-#endif
-}
+// (completion and memory visibility; a no-op without the launch attribute).
+// Every solve-loop kernel calls this before touching any data or work counter.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 // Let the next grid start launching: called when a CTA has finished its work
 // (a CTA that exits without calling it counts as having called it).
 __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

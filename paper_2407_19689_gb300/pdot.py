@@ -54,6 +54,7 @@ class Options(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_uint64),
         ("max_batch_slots", ctypes.c_int32),
         ("chunk_checks", ctypes.c_int32),
+        ("batch_active_bytes", ctypes.c_uint64),
     ]
 
 
@@ -267,10 +268,6 @@ def pdot_round_noalloc(device, stream, m, n, x_dtype, X, f, g, X_out) -> int:
     """Algorithm 3 without a handle or any allocation (scratch lives in the
     library's static device array); see include/pdot.h for the limits."""
     return load().pdot_round_noalloc(device, stream or None, m, n, x_dtype, X, f, g, X_out)
-
-
-KERNEL_NAMES = {0: "k_pass (register pipeline)", 1: "k_pass_bulk<float, 8> (bulk copies per row)",
-                2: "k_pass_group<float, 2> (bulk copies per 4-row group)"}
 
 
 def kernel_name(variant: int, c_dtype: int) -> str:

@@ -56,7 +56,7 @@ def serve_batched(requests, device: int = 0, budget_bytes: int = 150 << 30, chun
             lat[k] = time.perf_counter() - ta
             status[k] = sol.status
             obj[k] = sol.result["primal_obj"]
-            iters[k] = sol.result["iters"]
+            iters[k] = sol.result["passes"]
             pending -= 1
     wall = time.perf_counter() - t0
     launches = b.solver.launch_count()
@@ -68,7 +68,7 @@ def serve_plain(requests, device: int = 0, time_scale: float = 1.0, **opts):
     """The same requests served one at a time in arrival order (pdot_solve)."""
     s = pdot.Solver(device=device, **opts)
     t0 = time.perf_counter()
-    lat, status, obj = {}, {}, {}
+    lat, status, obj, iters = {}, {}, {}, {}
     for k, r in enumerate(requests):
         ta = t0 + r.arrival_s * time_scale
         wait = ta - time.perf_counter()
@@ -79,14 +79,23 @@ def serve_plain(requests, device: int = 0, time_scale: float = 1.0, **opts):
         lat[k] = time.perf_counter() - ta
         status[k] = sol.status
         obj[k] = sol.result["primal_obj"]
+        iters[k] = sol.result["passes"]
     wall = time.perf_counter() - t0
     s.close()
-    return {"latency": lat, "status": status, "obj": obj, "wall_s": wall}
+    return {"latency": lat, "status": status, "obj": obj, "iters": iters, "wall_s": wall}
 
 
-def summary(res: dict) -> dict:
-    lat = np.array([res["latency"][k] for k in sorted(res["latency"])])
+def summary(res: dict, requests=None) -> dict:
+    keys = sorted(res["latency"])
+    lat = np.array([res["latency"][k] for k in keys])
     ok = sum(1 for v in res["status"].values() if v == pdot.OK)
-    return {"requests": int(lat.size), "ok": ok, "solves_per_s": lat.size / res["wall_s"],
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "wall_s": res["wall_s"]}
+    out = {"requests": int(lat.size), "ok": ok, "solves_per_s": lat.size / res["wall_s"],
+           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "mean_s": float(lat.mean()), "wall_s": res["wall_s"]}
+    if requests is not None:
+        # the three slowest requests: what sets the tail
+        slow = sorted(keys, key=lambda k: -res["latency"][k])[:3]
+        out["slowest"] = [{"index": k, "m": requests[k].m, "n": requests[k].n, "d": requests[k].d,
+                           "cost": requests[k].cost, "tol": requests[k].tol, "latency_s": res["latency"][k],
+                           "passes": res.get("iters", {}).get(k)} for k in slow]
+    return out

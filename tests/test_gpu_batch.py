@@ -100,3 +100,21 @@ def test_batch_rejects_bad_marginals_on_device():
     res = b.run()
     assert res[t_bad].status == pdot.ERR_ARG and res[t_ok].status == pdot.OK
     b.close()
+
+
+@pytest.mark.parametrize("active_bytes", [1, 3 << 20])
+def test_active_bytes_policy_keeps_results(active_bytes):
+    """With an active-bytes budget a chunk advances the oldest instance and the
+    younger ones that fit; paused instances resume later.  Each result still
+    equals the same request in an unrestricted batch (1 byte: one instance at
+    a time, in admission order)."""
+    free = pdot.BatchSolver(device=0, time_limit_s=120.0, chunk_checks=1)
+    pol = pdot.BatchSolver(device=0, time_limit_s=120.0, chunk_checks=1, batch_active_bytes=active_bytes)
+    insts = [_inst(k) for k in range(6)]
+    a = [free.submit(C, f, g, tol=1e-6) for C, f, g in insts]
+    b = [pol.submit(C, f, g, tol=1e-6) for C, f, g in insts]
+    ra, rb = free.run(), pol.run()
+    for ta, tb in zip(a, b):
+        _same(ra[ta], rb[tb])
+    free.close()
+    pol.close()

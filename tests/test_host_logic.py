@@ -85,3 +85,65 @@ def test_grid_blob_instance_shapes_and_normalisation():
     assert abs(ins.f.sum() - 1) < 1e-14 and ins.f.min() > 0
     sizes = I.batch_sizes(256, I.seed_for(3))
     assert all(64 <= m <= 2048 and 64 <= n <= 2048 for m, n in sizes)
+
+
+def _shard_main(rank, world, port, q):
+    """One rank of a row-sharded PDHG step (Algorithm 2): rows [r0, r1) of C,
+    X and p live on this rank; the primal step and p+ are row-local, the
+    column sums of 2X+ - X are the one exchange (an all-reduce), then q+ is
+    updated identically on every rank."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ins = I.points_instance(37, 23, 4321)
+    m, n = ins.C.shape
+    rng = np.random.default_rng(9)
+    X = rng.random((m, n)) / (m * n)
+    p, qv = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
+    tau, sigma = 0.3, 0.4
+    r0, r1 = m * rank // world, m * (rank + 1) // world
+    # row block: the oracle's step on the block gives X+ and p+ of these rows
+    Xb, pb, _ = oracle.pdhg_step(ins.C[r0:r1], ins.f[r0:r1], ins.g, X[r0:r1], p[r0:r1], qv, tau, sigma)
+    part = torch.tensor((2.0 * Xb - X[r0:r1]).sum(axis=0), dtype=torch.float64)
+    # fixed-order all-reduce: gather every rank's partial and add them in rank order
+    parts = [torch.zeros_like(part) for _ in range(world)]
+    dist.all_gather(parts, part)
+    colsum = parts[0].clone()
+    for t in parts[1:]:
+        colsum += t
+    qn = qv + sigma * (ins.g - colsum.numpy())
+    q.put((rank, Xb, pb, qn))
+    dist.destroy_process_group()
+
+
+def test_row_sharded_step_equals_unsharded_gloo():
+    """Design check of a row-sharded single instance (two gloo ranks): the
+    sharded step, with one all-reduce of the column sums, reproduces the
+    unsharded oracle step (X+ and p+ exactly, q+ up to the summation order)."""
+    pytest.importorskip("torch.distributed")
+    import multiprocessing as mp
+
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_main, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    ins = I.points_instance(37, 23, 4321)
+    m, n = ins.C.shape
+    rng = np.random.default_rng(9)
+    X = rng.random((m, n)) / (m * n)
+    p, qv = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
+    Xo, po, qo = oracle.pdhg_step(ins.C, ins.f, ins.g, X, p, qv, 0.3, 0.4)
+    np.testing.assert_array_equal(np.vstack([o[1] for o in out]), Xo)
+    np.testing.assert_array_equal(np.concatenate([o[2] for o in out]), po)
+    for o in out:
+        np.testing.assert_allclose(o[3], qo, rtol=1e-13, atol=1e-15)
