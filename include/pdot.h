@@ -271,7 +271,8 @@ int64_t pdot_launch_count(pdot_handle *h);
  * pass `reps` times back to back on the handle's stream between two CUDA
  * events.  *ms_per_pass receives the mean device time of one pass;
  * *bytes_per_pass (nullable) the algorithmic bytes one pass moves:
- * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+);
+ * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+; sizeof C
+ * is 0 for a generated cost);
  * *kernel_variant (nullable) the pass kernel used for this shape: 0 register
  * pipeline, 1 bulk copies per row, 2 bulk copies per 4-row group (FP64 plans
  * always 0). */
