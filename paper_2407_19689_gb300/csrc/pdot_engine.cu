@@ -1547,8 +1547,9 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         h->l2_bytes = l2;
         const char* lh = getenv("PDOT_L2HINT");
         if (lh && atoi(lh) == 1) h->l2_hint = 1;
+        // Programmatic dependent launch: on (PDOT_PDL=0 turns it off).
         const char* pp = getenv("PDOT_PDL");
-        h->cfg.pdl = (pp && atoi(pp) == 1) ? 1 : 0;
+        h->cfg.pdl = (pp && atoi(pp) == 0) ? 0 : 1;
         h->cfg_base = h->cfg;
         CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
         CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));

@@ -218,6 +218,19 @@ __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;
 // (a CTA that exits without calling it counts as having called it).
 __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Before the wait of a dependent launch: pull the warp's first tile reference
+// and its instance descriptor into L1.  Both are written by the host before
+// the launch, never by the preceding kernel, so this may run while that
+// kernel finishes.
+__device__ __forceinline__ void prefetch_first_tile(const Inst* insts, const TileRef* tmap, int T) {
+    const int t = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (t >= T || (threadIdx.x & 31) != 0) return;
+    const TileRef tr = tmap[t];
+    const char* ip = reinterpret_cast<const char*>(insts + tr.inst);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ip));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ip + 128));
+}
+
 __device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int c = 0; c < WC_N; ++c)
@@ -812,13 +825,16 @@ template <typename TC, int S>
 __global__ void __launch_bounds__(TWARPS * 32, 2)
 k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
             unsigned* wctr, int wc) {
-    pdl_enter();
+    // Setup that does not depend on the preceding kernel (tile count and maps
+    // are host-written; shared-memory barriers are local) runs before the wait.
     const int T = *Tp;
-    reset_other_counters(wctr, wc);
     extern __shared__ __align__(128) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bulk::RowPipe<S> P;
     bulk::row_pipe_init<S>(P, dsm, lane, warp);
+    prefetch_first_tile(insts, tmap, T);
+    pdl_enter();
+    reset_other_counters(wctr, wc);
     pass_row_run<TC, S>(insts, tmap, T, &wctr[wc], P, lane);
     pdl_release();
 }
@@ -867,8 +883,9 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
              unsigned* wctr, int wc) {
     using namespace bulk;
     constexpr int R = 4;
+    const int T = *Tp;   // host-written: read before the wait (see k_pass_bulk)
+    prefetch_first_tile(insts, tmap, T);
     pdl_enter();
-    const int T = *Tp;
     reset_other_counters(wctr, wc);
     extern __shared__ __align__(128) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1400,6 +1417,10 @@ __global__ void __launch_bounds__(VT) k_dual(const Inst* __restrict__ insts, con
     // count to read before the work).
     __shared__ double sgrp[VG * 32];
     pdl_enter();
+    // The next pass may start launching now: it waits for this grid to
+    // complete before it reads anything this grid writes, and its CTAs use
+    // the time to set up (a no-op without programmatic dependent launch).
+    pdl_release();
     // No work counter of its own, but it still resets the others for the
     // kernels that follow (block 0, before any early exit).
     reset_other_counters(wctr, wc_index(WC_DUAL, 0));

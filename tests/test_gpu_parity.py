@@ -350,3 +350,41 @@ def test_full_size_4096_solve_kkt_is_honest(s32, grid64):
     assert k.rel_kkt <= 1.01e-4
     assert abs(k.rel_kkt - sol.result["rel_kkt"]) <= 1e-3 * k.rel_kkt
     assert abs(k.cx - sol.result["primal_obj"]) <= 1e-6 * abs(k.cx)
+
+
+@pytest.mark.parametrize("xt", ["f32", "f64"])
+def test_scaling_by_a_power_of_two_is_exact(xt):
+    """Sec. 4.2's scaled problem: with (C, f, g) and the start (X, p, q) all
+    multiplied by 2^-7, k constant-step iterates are the unscaled ones times
+    2^-7 bit for bit (no constant in the kernels breaks the homogeneity)."""
+    m, n = 150, 275
+    ins = I.points_instance(m, n, 888)
+    s = pdot.Solver(device=0, x_dtype=pdot.F64 if xt == "f64" else pdot.F32)
+    dt = torch.float64 if xt == "f64" else torch.float32
+    C = torch.tensor(ins.C, dtype=dt, device=DEV)
+    X0, p0, q0 = _rand_state(m, n, 17)
+    if xt == "f32":
+        X0 = X0.astype(np.float32).astype(np.float64)
+    eta = 0.5 / math.sqrt(m + n)
+    h = 2.0 ** -7
+    a = s.pdhg_steps(C, ins.f, ins.g, X0, p0, q0, k=25, eta=eta, omega=1.3)
+    b = s.pdhg_steps(C * h, ins.f * h, ins.g * h, X0 * h, p0 * h, q0 * h, k=25, eta=eta, omega=1.3)
+    for u, v in zip(a, b):
+        assert torch.equal(u * h, v)
+    s.close()
+
+
+def test_theory_mode_identifies_support_on_gpu():
+    """Constant step 1/(2 sqrt(m+n)) with fixed-beta restarts (Eq. 6), FP64:
+    the solve reaches the optimum and X_ij is exactly 0 where the optimal
+    reduced cost is positive (Thm. 1's identification)."""
+    ins = I.points_instance(12, 10, 111)
+    opt, Xs, ps, qs = oracle.exact_transport(ins.C, ins.f, ins.g)
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0, adaptive_step=0, adaptive_restart=0,
+                    primal_weight_update=0, beta=0.2)
+    sol = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-9)
+    assert sol.status == pdot.OK
+    assert abs(sol.result["primal_obj"] - opt) / opt < 1e-7
+    N = (ins.C - ps[:, None] - qs[None, :]) > 1e-6
+    assert np.all(_np(sol.X)[N] == 0.0)
+    s.close()
