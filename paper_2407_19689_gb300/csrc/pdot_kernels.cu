@@ -1258,15 +1258,14 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
     if (S->adaptive_step) {
         // Sec. 5 step-size rule in the PDLP form (reading C6); the exponent base
         // is the 1-based index of the attempted iteration plus one.
-        // (w dX2 + dy2 / w) / (2 |inter|) with a single division (FP64
-        // divisions are long dependent chains on this serial path).
+        // The accept/reject decision is discrete: it is taken in FP64 with
+        // the same expression as the FP64 reference of the rule, so that
+        // both sides decide alike away from exact ties.
         const double om = S->omega;
-        const double etabar = inter != 0.0 ? (om * om * dX2 + dy2) / (2.0 * om * fabs(inter)) : CUDART_INF;
-        // The two schedule factors are heuristics; single precision is ample
-        // (GB300's FP64 transcendentals are slow on this serial path).
-        const float t1 = (float)(S->total + 2);
-        const double a = (1.0 - (double)powf(t1, -0.3f)) * etabar;
-        const double b = (1.0 + (double)powf(t1, -0.6f)) * eta;
+        const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
+        const double t1 = (double)(S->total + 2);
+        const double a = (1.0 - pow(t1, -0.3)) * etabar;
+        const double b = (1.0 + pow(t1, -0.6)) * eta;
         const double eta_next = a < b ? a : b;
         accept = eta <= etabar;
         S->last_etabar = etabar;

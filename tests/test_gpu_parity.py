@@ -388,3 +388,44 @@ def test_theory_mode_identifies_support_on_gpu():
     N = (ins.C - ps[:, None] - qs[None, :]) > 1e-6
     assert np.all(_np(sol.X)[N] == 0.0)
     s.close()
+
+
+def test_degenerate_instances():
+    """Degenerate cases of Eq. (1): one source (the only feasible plan is
+    X = g^T), one target (X = f), a constant cost (every feasible plan is
+    optimal, objective = the constant), and zero entries in f and g (those
+    rows and columns end with no mass)."""
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0)
+    rng = np.random.default_rng(12)
+    # one source / one target
+    for m, n in [(1, 57), (43, 1)]:
+        C = rng.random((m, n))
+        f = np.full(m, 1.0 / m) if m > 1 else np.ones(1)
+        g = rng.dirichlet(np.ones(n)) if n > 1 else np.ones(1)
+        if m > 1:
+            f = rng.dirichlet(np.ones(m))
+        sol = s.solve(torch.tensor(C, device=DEV), f, g, tol=1e-8)
+        assert sol.status == pdot.OK
+        X = _np(sol.X)
+        Xstar = np.outer(f, g)
+        np.testing.assert_allclose(X, Xstar, rtol=1e-6, atol=1e-9)
+        assert abs(sol.result["primal_obj"] - float(np.sum(C * Xstar))) <= 1e-6 * float(np.sum(C * Xstar))
+    # constant cost
+    m, n = 30, 20
+    f, g = rng.dirichlet(np.ones(m)), rng.dirichlet(np.ones(n))
+    sol = s.solve(torch.full((m, n), 0.37, dtype=torch.float64, device=DEV), f, g, tol=1e-8)
+    assert sol.status == pdot.OK and abs(sol.result["primal_obj"] - 0.37) <= 1e-7
+    # zero marginal entries: their rows / columns carry no mass
+    ins = I.points_instance(40, 35, 99)
+    f, g = ins.f.copy(), ins.g.copy()
+    f[[3, 17]] = 0.0
+    g[[0, 34]] = 0.0
+    f, g = f / f.sum(), g / g.sum()
+    opt, *_ = oracle.exact_transport(ins.C, f, g)
+    sol = s.solve(torch.tensor(ins.C, device=DEV), f, g, tol=1e-8)
+    assert sol.status == pdot.OK and abs(sol.result["primal_obj"] - opt) / opt < 1e-6
+    X = _np(sol.X)
+    # (the returned point may be the running average, which keeps a trace of
+    # the first iterates: the mass on those rows/columns is tolerance-small)
+    assert X[[3, 17], :].sum() <= 1e-7 and X[:, [0, 34]].sum() <= 1e-7
+    s.close()
