@@ -408,7 +408,9 @@ def test_degenerate_instances():
         assert sol.status == pdot.OK
         X = _np(sol.X)
         Xstar = np.outer(f, g)
-        np.testing.assert_allclose(X, Xstar, rtol=1e-6, atol=1e-9)
+        # relative KKT 1e-8 bounds the marginal residual, hence the distance
+        # to the only feasible plan, at that order
+        np.testing.assert_allclose(X, Xstar, rtol=0.0, atol=1e-7)
         assert abs(sol.result["primal_obj"] - float(np.sum(C * Xstar))) <= 1e-6 * float(np.sum(C * Xstar))
     # constant cost
     m, n = 30, 20
