@@ -217,6 +217,8 @@ struct pdot_handle {
     size_t stage_bytes = 0;
     double* round_scratch = nullptr;
     size_t round_scratch_bytes = 0;
+    double* d_sched = nullptr;   // step-size schedule factors (see Ctrl::sched)
+    long long sched_len = 0;
 
     BatchEngine* batch = nullptr;
     int l2_hint = 0;             // L2 eviction-priority hints in the bulk pass (measured slower; opt-in)
@@ -407,6 +409,8 @@ void init_ctrl(pdot_handle* h, Ctrl* S, long long m, long long n, double tol, do
     S->max_passes = o.max_iter > 0 ? o.max_iter : std::numeric_limits<long long>::max() / 4;
     S->norm_b = norm_b;
     S->norm_C = norm_C;
+    S->sched = h->d_sched;
+    S->sched_len = h->sched_len;
     S->cur = 0; S->anc = 0; S->bar = 1; S->nxt = 2; S->barn = 3;
     S->status = ST_RUNNING;
     S->res_slot = 0;
@@ -1553,6 +1557,20 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         h->cfg_base = h->cfg;
         CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
         CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));
+        {
+            // t^-0.3 and t^-0.6 for t = 2 .. SCHED + 1, by the C library's pow
+            // (the same function the FP64 reference of the rule calls).
+            constexpr long long SCHED = 1LL << 19;
+            std::vector<double> tab((size_t)(2 * SCHED));
+            for (long long i = 0; i < SCHED; ++i) {
+                const double t1 = (double)(i + 2);
+                tab[(size_t)(2 * i)] = std::pow(t1, -0.3);
+                tab[(size_t)(2 * i + 1)] = std::pow(t1, -0.6);
+            }
+            CK(cudaMalloc(&h->d_sched, sizeof(double) * tab.size()));
+            CK(cudaMemcpy(h->d_sched, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+            h->sched_len = SCHED;
+        }
         CK(cudaMalloc(&h->d_inst, sizeof(Inst)));
         CK(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
         CK(cudaMallocHost(&h->h_inst, sizeof(Inst)));
@@ -1582,6 +1600,7 @@ pdot_status pdot_destroy(pdot_handle* h) {
     if (h->d_inst) cudaFree(h->d_inst);
     if (h->wctr) cudaFree(h->wctr);
     if (h->round_scratch) cudaFree(h->round_scratch);
+    if (h->d_sched) cudaFree(h->d_sched);
     if (h->stage) cudaFree(h->stage);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->h_inst) cudaFreeHost(h->h_inst);

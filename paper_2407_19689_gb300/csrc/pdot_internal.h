@@ -54,6 +54,12 @@ struct Ctrl {
     double r_rp2, r_rd2, r_cx, r_dual, r_gap, r_kkt, r_rel_p, r_rel_d, r_rel_gap, r_rel;
     // diagnostics of the last pass
     double last_etabar, last_dX2, last_dy2, last_inter;
+    // Step-size schedule factors (t^-0.3, t^-0.6 for t = 2, 3, ...), FP64,
+    // computed on the host with the C library's pow (so the device does not
+    // run FP64 pow on its serial path); beyond the table the device computes
+    // them itself.
+    const double* sched;
+    long long sched_len;
 };
 
 // Cost generated from coordinates (pdot_dtype PDOT_POINTS):

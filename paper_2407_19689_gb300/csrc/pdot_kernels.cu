@@ -1248,7 +1248,24 @@ __device__ __forceinline__ void assign_free(Ctrl* S) {
 // ---------------------------------------------------------------------------
 // Dual step + PDLP step-size controller
 // ---------------------------------------------------------------------------
-__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
+// The schedule factors of attempted iteration t1 = total + 2 (reading C6).
+struct SchedFactors {
+    double f3, f6;   // t1^-0.3, t1^-0.6
+};
+__device__ __forceinline__ SchedFactors sched_factors(const Ctrl* S, long long total) {
+    SchedFactors r;
+    if (total < S->sched_len) {
+        r.f3 = __ldg(S->sched + 2 * total);
+        r.f6 = __ldg(S->sched + 2 * total + 1);
+    } else {
+        const double t1 = (double)(total + 2);
+        r.f3 = pow(t1, -0.3);
+        r.f6 = pow(t1, -0.6);
+    }
+    return r;
+}
+
+__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, SchedFactors fac) {
     S->passes += 1;
     S->last_dX2 = dX2;
     S->last_dy2 = dy2;
@@ -1263,9 +1280,8 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter) {
         // both sides decide alike away from exact ties.
         const double om = S->omega;
         const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
-        const double t1 = (double)(S->total + 2);
-        const double a = (1.0 - pow(t1, -0.3)) * etabar;
-        const double b = (1.0 + pow(t1, -0.6)) * eta;
+        const double a = (1.0 - fac.f3) * etabar;
+        const double b = (1.0 + fac.f6) * eta;
         const double eta_next = a < b ? a : b;
         accept = eta <= etabar;
         S->last_etabar = etabar;
@@ -1333,10 +1349,13 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
     long long k = 0;
     double* Vn = nullptr;
     double* Vbn = nullptr;
+    SchedFactors fac = {0.0, 0.0};
     if (grp == 0) {
         status = S->status;
         sigma = S->sigma;
         k = S->k;
+        // requested now, used only by the instance's last tile
+        if (S->adaptive_step) fac = sched_factors(S, S->total);
         const double* Vc = slot_v(I, S->cur);
         const double* Vb = slot_v(I, S->bar);
         Vn = slot_v(I, S->nxt);
@@ -1402,7 +1421,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
             b2 = warp_sum(b2);
             if (lane == 0) {
                 *I.ticket = 0u;
-                finalize_step(S, b2, b0, b1);
+                finalize_step(S, b2, b0, b1, fac);
             }
         }
     }
