@@ -280,6 +280,18 @@ pdot_status pdot_time_pass(pdot_handle *h, int64_t m, int64_t n, const void *C, 
                            const double *f, const double *g, int reps, double *ms_per_pass, double *bytes_per_pass,
                            int32_t *kernel_variant);
 
+/*
+ * Self-test of the failure path of the bulk-copy pass kernels: on `device`,
+ * one warp waits, with their bounded wait, for a transfer that is announced on
+ * a shared-memory barrier but never issued.  The wait gives up after `polls`
+ * polls (1 .. 2^24) and *device_status (host memory) receives the status a
+ * pass sets when a wait gives up: PDOT_ERR_CUDA (3).  Returns PDOT_OK when the
+ * self-test ran, PDOT_ERR_ARG for a bad device, poll count or null pointer,
+ * PDOT_ERR_CUDA on a CUDA error.  Nothing on the device traps or waits without
+ * bound, and the CUDA context stays usable.
+ */
+pdot_status pdot_watchdog_selftest(int device, int64_t polls, int32_t *device_status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1838,6 +1838,22 @@ pdot_status pdot_cancel(pdot_handle* h, uint64_t ticket) {
     return PDOT_ERR_ARG;
 }
 
+pdot_status pdot_watchdog_selftest(int device, int64_t polls, int32_t* device_status) {
+    if (!device_status || polls < 1 || polls > (1LL << 24)) return PDOT_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PDOT_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return PDOT_ERR_CUDA;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PDOT_ERR_CUDA;
+    int hs = -1;
+    bool ok = cudaMemset(d, 0xff, sizeof(int)) == cudaSuccess && launch_watchdog_selftest(polls, d, nullptr) == 0 &&
+              cudaMemcpy(&hs, d, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(d);
+    if (!ok) return PDOT_ERR_CUDA;
+    *device_status = hs;
+    return PDOT_OK;
+}
+
 pdot_status pdot_batch_pending(pdot_handle* h, int* queued, int* running) {
     if (!h) return PDOT_ERR_ARG;
     BatchEngine* B = h->batch;

@@ -184,6 +184,8 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream);
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream);
+// One warp's bounded wait on a transfer that never comes; *d_status <- ST_DEVICE.
+int launch_watchdog_selftest(long long limit, int* d_status, void* stream);
 int occupancy_tile_blocks_per_sm(int ttype);
 int occupancy_vec_blocks_per_sm();
 // Opt the bulk-copy pass kernel into its shared-memory size; returns minus

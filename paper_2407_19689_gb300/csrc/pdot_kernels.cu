@@ -423,8 +423,8 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 // Bounded wait: a copy that never lands must not hang the GPU.
 constexpr long long WAIT_LIMIT = 1LL << 24;
-__device__ __forceinline__ bool wait_stage(unsigned bar, unsigned parity) {
-    for (long long it = 0; it < WAIT_LIMIT; ++it)
+__device__ __forceinline__ bool wait_stage(unsigned bar, unsigned parity, long long limit = WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -1923,6 +1923,28 @@ __global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Watchdog self-test: one warp waits, with the pipelines' bounded wait, for a
+// 16-byte transfer that is announced on an mbarrier but never issued.  The
+// wait gives up after `limit` polls and the kernel reports the status a pass
+// would set (ST_DEVICE).  Nothing traps and nothing waits without bound; no
+// copy is in flight when the CTA exits.
+// ---------------------------------------------------------------------------
+__global__ void k_watchdog_selftest(long long limit, int* status) {
+    __shared__ __align__(8) unsigned long long bar_mem;
+    const unsigned bar = bulk::smem_u32(&bar_mem);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        bulk::mbar_init(bar, 1);
+        bulk::fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) bulk::mbar_expect_tx(bar, 16u);   // the arrival happens; the bytes never come
+    __syncwarp();
+    const bool done = bulk::wait_stage(bar, 0u, limit);
+    if (lane == 0) *status = done ? ST_OK : ST_DEVICE;
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static int err(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
@@ -2031,6 +2053,11 @@ int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, i
     return launch_k(cfg.pdl != 0, k_checkvec, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV,
                     wctr, mode);
 }
+int launch_watchdog_selftest(long long limit, int* d_status, void* stream) {
+    k_watchdog_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(limit, d_status);
+    return err(cudaGetLastError());
+}
+
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream) {
     const int words = (int)(sizeof(Ctrl) / sizeof(int));
     int blocks = (max_count * words + 255) / 256;

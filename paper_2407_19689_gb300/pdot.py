@@ -126,6 +126,7 @@ DECLARED = [
     "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
     "pdot_solve_host", "pdot_pdhg_steps", "pdot_kkt", "pdot_round", "pdot_batch_submit", "pdot_poll",
     "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass", "pdot_round_noalloc",
+    "pdot_watchdog_selftest",
 ]
 
 _LIB = None
@@ -164,6 +165,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_time_pass": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i32, ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl), ctypes.POINTER(i32)]),
         "pdot_round_noalloc": (i32, [i32, vp, i64, i64, i32, vp, vp, vp, vp]),
+        "pdot_watchdog_selftest": (i32, [i32, i64, ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,6 +280,13 @@ def kernel_name(variant: int, c_dtype: int) -> str:
     if variant == 1:
         return f"k_pass_bulk<{tc}, 8> (bulk copies per row)"
     return f"k_pass_group<{tc}, 2> (bulk copies per 4-row group)"
+
+
+def pdot_watchdog_selftest(device: int = 0, polls: int = 4096):
+    """Returns (status of the call, status the device reported)."""
+    out = ctypes.c_int32(-1)
+    st = load().pdot_watchdog_selftest(device, polls, ctypes.byref(out))
+    return st, out.value
 
 
 def pdot_time_pass(h, m, n, C, c_dtype, ldc, f, g, reps):

@@ -80,3 +80,13 @@ def test_dtype_and_distance_codes_follow_header():
         assert re.search(rf"\b{name}\s*=\s*{val}\b", src), name
     for dist, val in pdot.DIST.items():
         assert re.search(rf"\bPDOT_DIST_{dist.upper()}\s*=\s*{val}\b", src), dist
+
+
+def test_watchdog_selftest_rejects_bad_arguments_before_any_cuda_call(lib):
+    import ctypes
+    from paper_2407_19689_gb300 import pdot
+    out = ctypes.c_int32(-1)
+    assert lib.pdot_watchdog_selftest(0, 0, ctypes.byref(out)) == pdot.ERR_ARG
+    assert lib.pdot_watchdog_selftest(0, (1 << 24) + 1, ctypes.byref(out)) == pdot.ERR_ARG
+    assert lib.pdot_watchdog_selftest(0, 4096, None) == pdot.ERR_ARG
+    assert out.value == -1

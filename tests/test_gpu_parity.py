@@ -305,6 +305,20 @@ def test_argument_errors(s32):
     assert sol.status == pdot.OK
 
 
+@pytest.mark.parametrize("polls", [1, 4096])
+def test_bounded_wait_gives_up_with_an_error_status(polls):
+    """A bulk-copy wait whose bytes never arrive ends after its poll limit and
+    reports PDOT_ERR_CUDA; the context stays usable (a solve runs afterwards)."""
+    st, dev = pdot.pdot_watchdog_selftest(0, polls)
+    assert st == pdot.OK and dev == pdot.ERR_CUDA
+    torch.cuda.synchronize()
+    ins = I.points_instance(20, 30, 73)
+    s = pdot.Solver(device=0, time_limit_s=60.0)
+    sol = s.solve(torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g, tol=1e-4)
+    s.close()
+    assert sol.status == pdot.OK
+
+
 def test_max_iter_returns_candidate():
     ins = I.points_instance(100, 100, 71)
     s = pdot.Solver(device=0, max_iter=128)
