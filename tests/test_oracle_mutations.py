@@ -1,0 +1,90 @@
+"""Mutation check of the oracle's pins.
+
+Each case plants one plausible mistake (a dropped term, a wrong sign, a
+swapped step size, an off-by-one weight) in a copy of ``oracle/pdot_oracle.c``,
+builds it on the CPU, and runs ``tests/test_oracle_pins.py`` against it in a
+child process; at least one pin must fail.  No mistake changes an index or a
+buffer size, so every mutant stays memory-safe.
+
+Mistakes in the Sec. 5 heuristics (restart conditions, step-size schedule,
+primal-weight update) may survive: the paper prints no trajectory to pin
+them against, and a changed heuristic can still converge to the same
+optimum.  Those cases are marked xfail ("parity unpinned").  Some of them
+XPASS: the solve then no longer reaches its tolerance within the capped
+pass budget (20 times what the unmodified oracle needs), which the
+end-to-end pins report.
+"""
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pdot_oracle.c")
+UNPINNED = pytest.mark.xfail(reason="parity unpinned: a Sec. 5 heuristic", strict=False)
+
+# (id, text in the oracle, planted replacement)
+MUTANTS = [
+    ("At_sign", "Y[i * n + j] = p[i] + q[j];", "Y[i * n + j] = p[i] - q[j];"),
+    ("A_column_drops_row0", "c[j] += X[i * n + j];", "c[j] += X[i * n + j] * (double)(i > 0);"),
+    ("step_reduced_cost_sign", "double v = X[e] - tau * (C[e] - AtY[e]);",
+     "double v = X[e] - tau * (C[e] + AtY[e]);"),
+    ("step_no_projection", "Xn[e] = v > 0.0 ? v : 0.0;", "Xn[e] = v;"),
+    ("step_no_extrapolation", "E[e] = 2.0 * Xn[e] - X[e];", "E[e] = Xn[e];"),
+    ("step_p_uses_tau", "pn[i] = p[i] + sigma * (f[i] - rE[i]);", "pn[i] = p[i] + tau * (f[i] - rE[i]);"),
+    ("step_q_sign", "qn[j] = q[j] + sigma * (g[j] - cE[j]);", "qn[j] = q[j] - sigma * (g[j] - cE[j]);"),
+    ("kkt_drops_gap", "out->kkt = sqrt(rp2 + rd2 + (out->gap / R) * (out->gap / R));",
+     "out->kkt = sqrt(rp2 + rd2);"),
+    ("kkt_dual_residual_sign", "double v = p[i] + q[j] - C[i * n + j];", "double v = C[i * n + j] - p[i] - q[j];"),
+    ("kkt_drops_column_residual", "for (int64_t j = 0; j < n; ++j) rp2 += (c[j] - g[j]) * (c[j] - g[j]);", ";"),
+    ("kkt_rel_d_wrong_scale", "out->rel_d = sqrt(rd2) / den_d;", "out->rel_d = sqrt(rd2) / den_p;"),
+    ("kkt_rel_gap_drops_dual", "den_g = fabs(cx) + fabs(dual);", "den_g = fabs(cx);"),
+    ("solve_norm_C_squared", "norm_C = sqrt(norm_C);", ";"),
+    ("average_weight_off_by_one", "wn = 1.0 / (double)(k + 1);", "wn = 1.0 / (double)(k + 2);"),
+    ("round_no_rank_one", "if (l1 > 0.0)", "if (l1 < 0.0)"),
+    ("round_row_scale_uncapped", "if (xi > 1.0) xi = 1.0;", ";"),
+    ("round_stale_column_sums", "ora_apply_A(m, n, Xf, r, c);\n    for (int64_t j = 0; j < n; ++j) {\n        double yj",
+     "for (int64_t j = 0; j < n; ++j) {\n        double yj"),
+    ("exact_reverse_arc_cost_sign", "double rcost = -C[i * n + j] + pi[u] - pi[i];",
+     "double rcost = C[i * n + j] + pi[u] - pi[i];"),
+    ("exact_dual_sign", "p[i] = -pi[i];", "p[i] = pi[i];"),
+    ("exact_ignores_reverse_capacity", "if (cap < delta) delta = cap;", ";"),
+    ("points_sqrt_on_sqeuclid", "if (kind == 2) acc = sqrt(acc);", "if (kind == 0 || kind == 2) acc = sqrt(acc);"),
+    ("points_linf_sums", "else if (fabs(t) > acc) acc = fabs(t);", "else acc += fabs(t);"),
+    ("theory_step_too_large", "0.5 / sqrt((double)(m + n))", "1.0 / sqrt((double)(m + n))"),
+    pytest.param("candidate_tie_inverted", "use_avg = !(kc.kkt < ka.kkt);", "use_avg = (kc.kkt < ka.kkt);",
+                 marks=UNPINNED),
+    pytest.param("restart_sufficient_flipped", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
+                 "restart = (kk->kkt >= opt->beta_suff * kkt0)", marks=UNPINNED),
+    pytest.param("restart_artificial_dropped", "|| ((double)k >= opt->beta_art * (double)total);", ";",
+                 marks=UNPINNED),
+    pytest.param("eta_bar_drops_factor_two", "(2.0 * fabs(inter))", "(fabs(inter))", marks=UNPINNED),
+    pytest.param("eta_growth_exponent", "pow(t1, -0.6)", "pow(t1, -0.3)", marks=UNPINNED),
+    pytest.param("primal_weight_inverted", "log(dy / dX)", "log(dX / dy)", marks=UNPINNED),
+    pytest.param("adaptive_eta0_doubled", "eta = opt->adaptive_step ? 1.0 / sqrt", "eta = opt->adaptive_step ? 2.0 / sqrt",
+                 marks=UNPINNED),
+]
+
+
+def _failed_pins(out: str):
+    return sorted(set(re.findall(r"FAILED \S*::(\S+)", out)))
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=lambda v: v if isinstance(v, str) and " " not in v else "")
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name} is not unique"
+    base = str(tmp_path / "oracle_mutant")
+    with open(base + ".c", "w") as fh:
+        fh.write(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", base + ".so", base + ".c", "-lm"])
+    env = dict(os.environ, PDOT_ORACLE_MUTANT=base)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    out = r.stdout + r.stderr
+    assert r.returncode in (0, 1), out[-2000:]
+    assert r.returncode == 1, f"mutant {name} survived every pin"
+    assert _failed_pins(out), out[-2000:]

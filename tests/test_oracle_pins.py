@@ -85,12 +85,13 @@ def test_alg2_step_equals_alg1_with_explicit_A(ora, m, n):
     rng = np.random.default_rng(4)
     X = rng.random((m, n)) * 0.1
     p, q = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
-    eta = 0.5 / math.sqrt(m + n)
+    # tau != sigma (a primal weight omega = 0.6), so a swapped step size fails here
+    tau, sigma = 0.3 / math.sqrt(m + n), 0.5 / math.sqrt(m + n)
     A = _kron_A(m, n)
     for _ in range(5):
-        Xn, pn, qn = ora.pdhg_step(ins.C, ins.f, ins.g, X, p, q, eta, eta)
+        Xn, pn, qn = ora.pdhg_step(ins.C, ins.f, ins.g, X, p, q, tau, sigma)
         xn, yn = ora.lp_pdhg_step(A, np.concatenate([ins.f, ins.g]), ins.C.reshape(-1, order="F"),
-                                  X.reshape(-1, order="F"), np.concatenate([p, q]), eta, eta)
+                                  X.reshape(-1, order="F"), np.concatenate([p, q]), tau, sigma)
         np.testing.assert_allclose(Xn.reshape(-1, order="F"), xn, rtol=0, atol=1e-14)
         np.testing.assert_allclose(np.concatenate([pn, qn]), yn, rtol=0, atol=1e-14)
         X, p, q = Xn, pn, qn
@@ -151,6 +152,54 @@ def test_kkt_closed_forms(ora):
     obj, X, p, q = ora.exact_transport(C, f, g)
     ks = ora.kkt(C, f, g, X, p, q)
     assert ks.kkt < 1e-14 and ks.rel_kkt < 1e-13
+
+
+def test_relative_measures_closed_forms(ora):
+    """Reading C5 at points where each relative part reduces to a constant:
+    at the origin the primal residual is [f; g] itself (rel_p = 1, or
+    |b| / (1 + |b|) with the '1 +' denominators) and the duals are feasible
+    with a zero gap; at the product plan f g^T with zero duals the plan is
+    feasible and the whole objective is gap (rel_gap = 1, or <C,X> / (1 + <C,X>))."""
+    ins = _rand_instance(8, 5, 42)
+    C, f, g = ins.C, ins.f, ins.g
+    nb = math.sqrt(np.sum(f ** 2) + np.sum(g ** 2))
+    z = (np.zeros((8, 5)), np.zeros(8), np.zeros(5))
+    k0, k1 = ora.kkt(C, f, g, *z), ora.kkt(C, f, g, *z, rel_mode=1)
+    assert abs(k0.rel_p - 1.0) < 1e-15 and k0.rel_d == 0.0 and k0.rel_gap == 0.0 and k0.rel_kkt == k0.rel_p
+    assert abs(k1.rel_p - nb / (1.0 + nb)) < 1e-15 and k1.rel_d == 0.0 and k1.rel_gap == 0.0
+    P = np.outer(f, g)
+    cx = f @ C @ g
+    k0, k1 = ora.kkt(C, f, g, P, z[1], z[2]), ora.kkt(C, f, g, P, z[1], z[2], rel_mode=1)
+    assert k0.rel_p < 1e-15 and k0.rel_d == 0.0 and abs(k0.rel_gap - 1.0) < 1e-15
+    assert abs(k1.rel_gap - cx / (1.0 + cx)) < 1e-15 and abs(k0.rel_kkt - 1.0) < 1e-15
+    # X = 0 with a feasible dual p = t 1 (t <= min C): the whole dual objective t
+    # is gap and nothing else contributes to it (rel_gap = 1, or t / (1 + t)).
+    t = 0.5 * C.min()
+    assert t > 0.0
+    k0, k1 = ora.kkt(C, f, g, z[0], np.full(8, t), z[2]), ora.kkt(C, f, g, z[0], np.full(8, t), z[2], rel_mode=1)
+    assert k0.rd2 == 0.0 and abs(k0.rel_gap - 1.0) < 1e-15 and abs(k1.rel_gap - t / (1.0 + t)) < 1e-15
+
+
+def test_relative_measures_scale_with_their_own_data(ora):
+    """Reading C5: each relative part is measured against the data it refers
+    to -- the primal part against the marginals only, the dual part against the
+    cost only: rel_p does not move when C changes, rel_d does not move when
+    the marginals change, and doubling C (marginals) halves rel_d (rel_p)
+    when the residual itself is unchanged."""
+    ins, other = _rand_instance(8, 5, 43), _rand_instance(8, 5, 44)
+    rng = np.random.default_rng(45)
+    X = rng.random((8, 5)) * 0.05
+    p, q = rng.standard_normal(8) * 0.3, rng.standard_normal(5) * 0.3
+    for mode in (0, 1):
+        a = ora.kkt(ins.C, ins.f, ins.g, X, p, q, rel_mode=mode)
+        b = ora.kkt(other.C, ins.f, ins.g, X, p, q, rel_mode=mode)
+        c = ora.kkt(ins.C, other.f, other.g, X, p, q, rel_mode=mode)
+        assert a.rel_d > 0.0 and a.rel_p > 0.0
+        assert b.rel_p == a.rel_p and c.rel_d == a.rel_d
+    # C -> 2C with p, q -> 2p, 2q doubles the dual residual and ||C||_F alike.
+    a = ora.kkt(ins.C, ins.f, ins.g, X, p, q)
+    d = ora.kkt(2.0 * ins.C, ins.f, ins.g, X, 2.0 * p, 2.0 * q)
+    assert d.rel_d == a.rel_d and d.rd2 == 4.0 * a.rd2
 
 
 # --------------------------------------------------------------------------
@@ -253,6 +302,10 @@ def test_solve_reaches_exact_optimum(ora, m, n, seed):
     for tol, bound in [(1e-4, 5e-3), (1e-6, 1e-5), (1e-8, 1e-7)]:
         res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=tol))
         assert res.status == 0 and res.rel_kkt <= tol
+        # the measures the solve reports are those of the iterate it returns
+        k = ora.kkt(ins.C, ins.f, ins.g, res.X, res.p, res.q)
+        for part in ("rel_p", "rel_d", "rel_gap", "rel_kkt"):
+            assert abs(getattr(res, part) - getattr(k, part)) <= 1e-12 * getattr(k, part) + 1e-300, part
         assert abs(res.primal_obj - opt) / opt < bound
         lb = _certified_interval(ins.C, ins.f, ins.g, res.X, res.p, res.q)
         ub = ins.C.reshape(-1) @ ora.round_plan(res.X, ins.f, ins.g).reshape(-1)
@@ -269,8 +322,31 @@ def test_solve_theory_mode_identifies_support(ora):
     res = ora.solve(ins.C, ins.f, ins.g, opts)
     assert res.status == 0
     assert abs(res.primal_obj - opt) / opt < 1e-7
+    # the constant step is Theorem 1's 1 / (2 ||A||_2), ||A||_2 = sqrt(m + n) (Prop. 1)
+    assert abs(res.eta - 0.5 / math.sqrt(12 + 10)) < 1e-16
     N = (ins.C - ps[:, None] - qs[None, :]) > 1e-6
     assert np.all(res.X[N] == 0.0)
+
+
+def test_solve_average_is_the_uniform_mean_of_the_iterates(ora):
+    """Algorithm 2's running average (reading C7: uniform weights): with a
+    constant step and no restart (fixed-beta test with beta = 0 never fires),
+    the candidate the solve returns at its pass limit is the average, which
+    must equal the plain mean of the iterates of repeated Algorithm 2 steps."""
+    ins = _rand_instance(9, 7, 151)
+    eta, k = 0.4 / math.sqrt(16), 192
+    opts = ora.Options(tol=0.0, max_passes=k, check_every=64, adaptive_step=0, adaptive_restart=0,
+                       primal_weight_update=0, beta=0.0, eta0=eta)
+    res = ora.solve(ins.C, ins.f, ins.g, opts)
+    assert res.status == ora.STATUS_MAX_ITER and res.restarts == 0 and res.candidate_is_average == 1
+    X, p, q = np.zeros((9, 7)), np.zeros(9), np.zeros(7)
+    Xs, ps, qs = [], [], []
+    for _ in range(k):
+        X, p, q = ora.pdhg_step(ins.C, ins.f, ins.g, X, p, q, eta, eta)
+        Xs.append(X); ps.append(p); qs.append(q)
+    np.testing.assert_allclose(res.X, np.mean(Xs, axis=0), rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(res.p, np.mean(ps, axis=0), rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(res.q, np.mean(qs, axis=0), rtol=1e-12, atol=1e-16)
 
 
 def test_solve_rel_mode_one_plus(ora):
@@ -304,6 +380,23 @@ def test_rounding_keeps_feasible_plan(ora):
     ins = I.points_instance(6, 9, 141)
     obj, X, p, q = ora.exact_transport(ins.C, ins.f, ins.g)
     np.testing.assert_allclose(ora.round_plan(X, ins.f, ins.g), X, atol=1e-16)
+
+
+def test_rounding_closed_forms(ora):
+    """Algorithm 3 on two families with a closed-form result.  P is a feasible
+    plan.  (a) alpha P, 0 < alpha < 1: every row and column is short, both
+    scales are capped at 1, and the rank-one correction adds the missing mass
+    (1 - alpha) f g^T.  (b) diag(d) P with d >= 1: the row step alone restores
+    P, after which the columns are exact and nothing else changes."""
+    ins = I.points_instance(7, 11, 142, marginals="dirichlet")
+    f, g = ins.f, ins.g
+    _, P, _, _ = ora.exact_transport(ins.C, f, g)
+    P = 0.5 * P + 0.5 * np.outer(f, g)     # dense: every row and column carries mass
+    for alpha in (0.25, 0.9):
+        np.testing.assert_allclose(ora.round_plan(alpha * P, f, g), alpha * P + (1 - alpha) * np.outer(f, g),
+                                   rtol=1e-13, atol=1e-17)
+    d = np.random.default_rng(143).uniform(1.0, 3.0, 7)
+    np.testing.assert_allclose(ora.round_plan(d[:, None] * P, f, g), P, rtol=1e-13, atol=1e-17)
 
 
 # --------------------------------------------------------------------------
