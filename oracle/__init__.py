@@ -18,9 +18,12 @@ Each wrapper names the passage of the paper its C function follows:
 Parity status: the operators, the PDHG step, the KKT error, the rounding and
 the exact solver are pinned by the ``-m "not gpu"`` tests (closed forms,
 brute force, library LP/assignment solvers, invariants).  The adaptive
-heuristics inside ``solve`` (restart conditions, step-size schedule,
-primal-weight update) are "parity unpinned" individually; they are pinned only
-end to end, by the solve reaching the exact optimum.
+heuristics inside ``solve`` are pinned by special cases whose outcome follows
+from pinned steps (the restart candidate rule, the artificial-restart
+schedule, the primal weight at theta = 0 and 1, the default first step) and
+end to end (the solve reaches the exact optimum).  The PDLP step-size rule
+and restart conditions (i), (ii) are "parity unpinned" individually: the
+paper prints no trajectory; they are pinned only end to end.
 """
 from __future__ import annotations
 

@@ -38,10 +38,11 @@
  *
  * Readings of passages the paper leaves open are listed beside the code that
  * takes them (C1..C16 in the project notes use the same numbering).
- * Parity of the adaptive heuristics (restart conditions, step-size schedule,
- * primal-weight update) is pinned only end to end (the solve reaches the exact
- * optimum); their individual decisions are "parity unpinned": the paper prints
- * no trajectory to compare against.
+ * The adaptive heuristics are pinned by special cases (restart candidate
+ * rule, artificial-restart schedule, primal weight at theta = 0 and 1, default
+ * first step) and end to end (the solve reaches the exact optimum).  The
+ * step-size rule and restart conditions (i), (ii) are "parity unpinned"
+ * individually: the paper prints no trajectory to compare against.
  */
 #include <math.h>
 #include <stdint.h>

@@ -6,13 +6,13 @@ builds it on the CPU, and runs ``tests/test_oracle_pins.py`` against it in a
 child process; at least one pin must fail.  No mistake changes an index or a
 buffer size, so every mutant stays memory-safe.
 
-Mistakes in the Sec. 5 heuristics (restart conditions, step-size schedule,
-primal-weight update) may survive: the paper prints no trajectory to pin
-them against, and a changed heuristic can still converge to the same
-optimum.  Those cases are marked xfail ("parity unpinned").  Some of them
-XPASS: the solve then no longer reaches its tolerance within the capped
-pass budget (20 times what the unmodified oracle needs), which the
-end-to-end pins report.
+The Sec. 5 heuristics are pinned through special cases where their outcome
+follows from pinned steps and counts (the candidate rule, the artificial
+restart schedule, the primal weight at theta = 0 and 1, the default first
+step); mistakes in the step-size schedule (reading C6) and in restart
+condition (i) are caught end to end: the solve no longer reaches its
+tolerance within the capped pass budget (20 times what the unmodified
+oracle needs) or stops at another point.
 """
 import os
 import re
@@ -23,7 +23,6 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pdot_oracle.c")
-UNPINNED = pytest.mark.xfail(reason="parity unpinned: a Sec. 5 heuristic", strict=False)
 
 # (id, text in the oracle, planted replacement)
 MUTANTS = [
@@ -54,17 +53,14 @@ MUTANTS = [
     ("points_sqrt_on_sqeuclid", "if (kind == 2) acc = sqrt(acc);", "if (kind == 0 || kind == 2) acc = sqrt(acc);"),
     ("points_linf_sums", "else if (fabs(t) > acc) acc = fabs(t);", "else acc += fabs(t);"),
     ("theory_step_too_large", "0.5 / sqrt((double)(m + n))", "1.0 / sqrt((double)(m + n))"),
-    pytest.param("candidate_tie_inverted", "use_avg = !(kc.kkt < ka.kkt);", "use_avg = (kc.kkt < ka.kkt);",
-                 marks=UNPINNED),
-    pytest.param("restart_sufficient_flipped", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
-                 "restart = (kk->kkt >= opt->beta_suff * kkt0)", marks=UNPINNED),
-    pytest.param("restart_artificial_dropped", "|| ((double)k >= opt->beta_art * (double)total);", ";",
-                 marks=UNPINNED),
-    pytest.param("eta_bar_drops_factor_two", "(2.0 * fabs(inter))", "(fabs(inter))", marks=UNPINNED),
-    pytest.param("eta_growth_exponent", "pow(t1, -0.6)", "pow(t1, -0.3)", marks=UNPINNED),
-    pytest.param("primal_weight_inverted", "log(dy / dX)", "log(dX / dy)", marks=UNPINNED),
-    pytest.param("adaptive_eta0_doubled", "eta = opt->adaptive_step ? 1.0 / sqrt", "eta = opt->adaptive_step ? 2.0 / sqrt",
-                 marks=UNPINNED),
+    ("candidate_tie_inverted", "use_avg = !(kc.kkt < ka.kkt);", "use_avg = (kc.kkt < ka.kkt);"),
+    ("restart_sufficient_flipped", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
+                 "restart = (kk->kkt >= opt->beta_suff * kkt0)"),
+    ("restart_artificial_dropped", "|| ((double)k >= opt->beta_art * (double)total);", ";"),
+    ("eta_bar_drops_factor_two", "(2.0 * fabs(inter))", "(fabs(inter))"),
+    ("eta_growth_exponent", "pow(t1, -0.6)", "pow(t1, -0.3)"),
+    ("primal_weight_inverted", "log(dy / dX)", "log(dX / dy)"),
+    ("adaptive_eta0_doubled", "eta = opt->adaptive_step ? 1.0 / sqrt", "eta = opt->adaptive_step ? 2.0 / sqrt"),
 ]
 
 

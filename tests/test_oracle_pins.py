@@ -349,6 +349,74 @@ def test_solve_average_is_the_uniform_mean_of_the_iterates(ora):
     np.testing.assert_allclose(res.q, np.mean(qs, axis=0), rtol=1e-12, atol=1e-16)
 
 
+def _constant_step_run(ora, ins, K, eta):
+    """K constant-step Algorithm 2 iterations from the origin (pinned steps),
+    with the uniform average and the KKT errors of both."""
+    m, n = ins.C.shape
+    X, p, q, Xb, pb, qb = ora.pdhg_steps(ins.C, ins.f, ins.g, np.zeros((m, n)), np.zeros(m), np.zeros(n),
+                                        k=K, eta=eta)
+    return (X, p, q), (Xb, pb, qb), ora.kkt(ins.C, ins.f, ins.g, X, p, q), ora.kkt(ins.C, ins.f, ins.g, Xb, pb, qb)
+
+
+@pytest.mark.parametrize("K,average", [(1, True), (32, True), (64, False)])
+def test_restart_candidate_is_the_lower_kkt_of_current_and_average(ora, K, average):
+    """Sec. 5: the restart candidate is the current iterate if its KKT error is
+    smaller than the running average's, else the average (reading C13: a tie,
+    as after one step where both are the same point, goes to the average).
+    With a constant step the solve's first check is reproduced from pinned
+    Algorithm 2 steps; the three cases cover the tie and both outcomes."""
+    ins = _rand_instance(9, 7, 161)
+    eta = 0.1
+    cur, avg, kc, ka = _constant_step_run(ora, ins, K, eta)
+    assert (kc.kkt == ka.kkt) == (K == 1) and (not kc.kkt < ka.kkt) == average
+    res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=0.0, max_passes=K, check_every=K, adaptive_step=0,
+                                                     primal_weight_update=0, eta0=eta))
+    assert res.candidate_is_average == int(average)
+    for got, want in zip((res.X, res.p, res.q), avg if average else cur):
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-16)
+
+
+@pytest.mark.parametrize("beta_art,max_passes,restarts", [(1.0, 640, 1), (0.5, 1280, 5)])
+def test_artificial_restart_schedule(ora, beta_art, max_passes, restarts):
+    """Sec. 5 condition (iii), k >= beta_art * total, with reading C8 (total
+    counts the iterations since the solve began, k those since the last
+    restart, checks every 64 passes).  With (i) and (ii) switched off and a
+    constant step every pass is accepted, so the schedule follows from the
+    counts alone: beta_art = 1 restarts only at the first check; beta_art = 1/2
+    restarts at passes 64, 128, 256, 512, 1024 (k doubles with total)."""
+    ins = _rand_instance(9, 7, 162)
+    res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=0.0, max_passes=max_passes, adaptive_step=0,
+                                                     beta_suff=0.0, beta_nec=0.0, beta_art=beta_art, eta0=0.1))
+    assert res.status == ora.STATUS_MAX_ITER and res.rejected == 0 and res.iters == max_passes
+    assert res.restarts == restarts
+
+
+@pytest.mark.parametrize("theta", [0.0, 1.0])
+def test_primal_weight_update_special_cases(ora, theta):
+    """Sec. 5 PrimalWeightUpdate with smoothing theta at the one restart of a
+    constant-step run (beta_art = 1, pass 64, candidate = current iterate, as
+    in the K = 64 case above): theta = 0 keeps omega = 1; theta = 1 makes omega
+    the ratio of the dual to the primal distance moved since the start."""
+    ins = _rand_instance(9, 7, 161)
+    (X, p, q), _, kc, ka = _constant_step_run(ora, ins, 64, 0.1)
+    assert kc.kkt < ka.kkt
+    res = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=0.0, max_passes=128, adaptive_step=0, beta_suff=0.0,
+                                                     beta_nec=0.0, beta_art=1.0, eta0=0.1, theta=theta))
+    assert res.restarts == 1
+    want = 1.0 if theta == 0.0 else math.sqrt(p @ p + q @ q) / np.linalg.norm(X)
+    assert abs(res.omega - want) <= 1e-13 * want
+
+
+def test_adaptive_default_step_is_one_over_norm_A(ora):
+    """Reading C2: the adaptive mode starts from eta0 = 1 / ||A||_2 = 1 / sqrt(m + n)
+    (Prop. 1): the default run and a run given that eta0 are the same run."""
+    ins = _rand_instance(20, 12, 163)
+    a = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=1e-6))
+    b = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=1e-6, eta0=1.0 / math.sqrt(32)))
+    assert (a.passes, a.restarts, a.rejected) == (b.passes, b.restarts, b.rejected)
+    assert np.array_equal(a.X, b.X) and np.array_equal(a.p, b.p) and a.eta == b.eta
+
+
 def test_solve_rel_mode_one_plus(ora):
     """Reading C5, option 1 (cuPDLP's '1 +' denominators) also terminates correctly."""
     ins = I.points_instance(30, 30, 121)
