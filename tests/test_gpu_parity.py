@@ -252,6 +252,43 @@ def test_theory_mode_and_rel_mode_one():
     s1.close()
 
 
+def _heuristic_case(**kw):
+    """A constant-step FP64 run on both sides (Sec. 5 heuristics at special
+    cases whose decisions follow from counts or from KKT values 10-20 % apart)."""
+    ins = I.points_instance(40, 30, 171)
+    ro = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=1e-15, adaptive_step=0, **kw))
+    gkw = dict(kw)
+    gkw["max_iter"] = gkw.pop("max_passes")
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=60.0, adaptive_step=0, **gkw)
+    sol = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=1e-15)
+    s.close()
+    return ro, sol
+
+
+@pytest.mark.parametrize("eta0,average", [(0.05, 1), (0.12, 0)])
+def test_restart_candidate_rule_matches_oracle(eta0, average):
+    ro, sol = _heuristic_case(max_passes=64, primal_weight_update=0, eta0=eta0)
+    assert ro.candidate_is_average == average and sol.status == pdot.MAX_ITER
+    assert sol.result["returned_average"] == average and sol.result["passes"] == 64
+    assert rel(_np(sol.X), ro.X) < 1e-11 and rel(_np(sol.p), ro.p) < 1e-11 and rel(_np(sol.q), ro.q) < 1e-11
+
+
+@pytest.mark.parametrize("beta_art,max_passes,restarts", [(1.0, 640, 1), (0.5, 1280, 5)])
+def test_artificial_restart_schedule_matches_oracle(beta_art, max_passes, restarts):
+    ro, sol = _heuristic_case(max_passes=max_passes, beta_suff=0.0, beta_nec=0.0, beta_art=beta_art, eta0=0.1)
+    assert ro.restarts == restarts and sol.result["restarts"] == restarts
+    assert sol.result["passes"] == ro.passes == max_passes
+    assert abs(sol.result["primal_obj"] - ro.primal_obj) <= 1e-10 * abs(ro.primal_obj)
+
+
+@pytest.mark.parametrize("theta", [0.0, 1.0])
+def test_primal_weight_update_matches_oracle(theta):
+    ro, sol = _heuristic_case(max_passes=128, beta_suff=0.0, beta_nec=0.0, beta_art=1.0, eta0=0.1, theta=theta)
+    assert ro.restarts == 1 and sol.result["restarts"] == 1
+    assert abs(sol.result["omega"] - ro.omega) <= 1e-12 * ro.omega
+    assert (ro.omega == 1.0) == (theta == 0.0)
+
+
 @pytest.mark.parametrize("xt", [pdot.F32, pdot.F64])
 def test_round_parity(xt):
     s = pdot.Solver(device=0, x_dtype=xt)
