@@ -147,3 +147,48 @@ def test_row_sharded_step_equals_unsharded_gloo():
     np.testing.assert_array_equal(np.concatenate([o[2] for o in out]), po)
     for o in out:
         np.testing.assert_allclose(o[3], qo, rtol=1e-13, atol=1e-15)
+
+
+def test_recorded_traffic_is_null_once_the_kernel_source_changes(tmp_path, monkeypatch):
+    """bench.py reports the ncu DRAM traffic of the pass kernel only while the
+    kernel source still hashes to the value recorded with the capture."""
+    import hashlib
+    import json
+
+    import bench
+    src = tmp_path / "kernels.cu"
+    src.write_text("__global__ void k() {}\n")
+    rec = {"cost_dtype": "f32", "grid": 64, "kernel_variant": 1, "dram_bytes_per_launch_full_size": 123.0,
+           "kernel_source_sha256": hashlib.sha256(src.read_bytes()).hexdigest()}
+    traffic = tmp_path / "traffic.json"
+    traffic.write_text(json.dumps({"records": [rec]}))
+    monkeypatch.setattr(bench, "TRAFFIC", str(traffic))
+    monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
+    assert bench.recorded_traffic("f32", 64, 1) == 123.0
+    assert bench.recorded_traffic("bf16", 64, 1) is None      # no record for that cost storage
+    assert bench.recorded_traffic("f32", 64, 2) is None       # nor for another kernel variant
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench.recorded_traffic("f32", 64, 1) is None
+
+
+def test_committed_traffic_record_names_its_command_and_workload():
+    import json
+    import bench
+    recs = json.load(open(bench.TRAFFIC))["records"]
+    assert recs
+    for r in recs:
+        assert r["command"].startswith("ncu ") and "--clock-control none" in r["command"]
+        assert r["dram_bytes_per_launch_full_size"] == pytest.approx(
+            r["dram_bytes_read_per_launch"] + r["dram_bytes_write_per_launch"], rel=1e-6)
+        assert 0 < r["dram_bytes_per_launch_full_size"] <= 1.5 * r["algorithmic_bytes_per_launch"]
+
+
+def test_measured_peak_reads_the_copy_bandwidth(tmp_path, monkeypatch):
+    import json
+    import bench
+    peaks = tmp_path / "peaks.json"
+    peaks.write_text(json.dumps({"hbm_gbs": 6790.3, "bf16_tflops": 1900.0}))
+    monkeypatch.setattr(bench, "PEAKS", str(peaks))
+    assert bench.measured_peak() == (6790.3, "measured")
+    monkeypatch.setattr(bench, "PEAKS", str(tmp_path / "missing.json"))
+    assert bench.measured_peak() == (6800.0, "fallback")
