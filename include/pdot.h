@@ -19,6 +19,8 @@
  *     pdot_batch_submit, which only queues.
  *   - Errors are reported only through return codes; nothing is thrown across
  *     the ABI.  A handle is used by one host thread at a time.
+ *   - Calls that take a handle or a device index make that device the calling
+ *     thread's current CUDA device (cudaSetDevice) and leave it so.
  *   - Argument errors (PDOT_ERR_ARG): m < 1, n < 1, ldc < n, tol <= 0 (solve),
  *     null required pointers, unknown dtypes, |sum f - sum g| > 1e-9 * max(sum f, 1)
  *     or a negative entry in f or g (checked on a host copy), x_dtype other
