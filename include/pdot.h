@@ -257,10 +257,11 @@ pdot_status pdot_batch_pending(pdot_handle *h, int *queued, int *running);
  *   Limits: 1 <= m, n <= 32768 and x_dtype F32 or F64, else PDOT_ERR_ARG.
  *   The first call on a device looks up the array's device address (once per
  *   device); make that first call before any stream capture.
- *   All calls share the one array; calls that overlap on the GPU (other
- *   streams or host threads) race and must be serialised by the caller.  Each
- *   call writes every scratch word before reading it, so nothing carries over
- *   from the previous call.
+ *   All calls share the one array: the library runs one call per device at
+ *   a time (a lock held until the call's stream synchronises, on error paths
+ *   too), so calls from several host threads or on several streams wait for
+ *   each other instead of racing.  Each call writes every scratch word before
+ *   reading it, so nothing carries over from the previous call.
  */
 pdot_status pdot_round_noalloc(int device, void *cuda_stream, int64_t m, int64_t n, pdot_dtype x_dtype,
                                const void *X, const double *f, const double *g, void *X_out);

@@ -32,6 +32,9 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_WORDS];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+// One call at a time per device: a call holds its device's lock until its
+// stream has synchronised, so no two calls use the shared scratch at once.
+std::mutex g_call_mutex[NA_MAX_DEVICES];
 
 template <typename TX>
 __device__ __forceinline__ double na_scaled(const TX* X, long long n, long long i, long long j, const double* xs,
@@ -178,12 +181,14 @@ extern "C" pdot_status pdot_round_noalloc(int device, void* cuda_stream, int64_t
     double* base = nullptr;
     if (scratch_for_device(device, &base) != cudaSuccess) return PDOT_ERR_CUDA;
     const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lock(g_call_mutex[device]);
     cudaError_t e;
     if (x_dtype == PDOT_F64)
         e = run_round<double>(st, m, n, static_cast<const double*>(X), f, g, static_cast<double*>(X_out), base);
     else
         e = run_round<float>(st, m, n, static_cast<const float*>(X), f, g, static_cast<float*>(X_out), base);
-    if (e != cudaSuccess) return PDOT_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PDOT_ERR_CUDA;
+    // Synchronise on every path, so the scratch is idle when the lock is released.
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || es != cudaSuccess) return PDOT_ERR_CUDA;
     return PDOT_OK;
 }
