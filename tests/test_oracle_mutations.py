@@ -53,6 +53,12 @@ MUTANTS = [
     ("points_sqrt_on_sqeuclid", "if (kind == 2) acc = sqrt(acc);", "if (kind == 0 || kind == 2) acc = sqrt(acc);"),
     ("points_linf_sums", "else if (fabs(t) > acc) acc = fabs(t);", "else acc += fabs(t);"),
     ("theory_step_too_large", "0.5 / sqrt((double)(m + n))", "1.0 / sqrt((double)(m + n))"),
+    ("kkt_gap_sign", "out->gap = cx - dual;", "out->gap = dual - cx;"),
+    ("round_error_sign", "r[i] = f[i] - r[i];", "r[i] = r[i] - f[i];"),
+    ("exact_potential_update", "pi[v] += (dist[v] < dt ? dist[v] : dt);", "pi[v] += (dist[v] < dt ? dist[v] : 0.0);"),
+    ("points_divisor_ignored", "C[i * n + j] = acc / divisor;", "C[i * n + j] = acc;"),
+    ("restart_kkt0_not_updated", "        kkt0 = kk->kkt;\n        kkt_prev = kk->kkt;\n        k = 0;",
+     "        kkt_prev = kk->kkt;\n        k = 0;"),
     ("candidate_tie_inverted", "use_avg = !(kc.kkt < ka.kkt);", "use_avg = (kc.kkt < ka.kkt);"),
     ("restart_sufficient_flipped", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
                  "restart = (kk->kkt >= opt->beta_suff * kkt0)"),

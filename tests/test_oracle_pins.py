@@ -180,6 +180,22 @@ def test_relative_measures_closed_forms(ora):
     assert k0.rd2 == 0.0 and abs(k0.rel_gap - 1.0) < 1e-15 and abs(k1.rel_gap - t / (1.0 + t)) < 1e-15
 
 
+def test_gap_is_weak_duality_slack(ora):
+    """Eq. (1) and its dual: for a feasible plan X (X1 = f, X^T1 = g) and a
+    feasible dual (p_i + q_j <= C_ij) the gap <C,X> - f^T p - g^T q equals
+    sum_ij X_ij (C_ij - p_i - q_j) >= 0 (weak duality; it vanishes exactly
+    under complementary slackness)."""
+    ins = _rand_instance(8, 5, 46)
+    C, f, g = ins.C, ins.f, ins.g
+    X = 0.5 * ora.exact_transport(C, f, g)[1] + 0.5 * np.outer(f, g)
+    p = np.random.default_rng(47).standard_normal(8) * 0.1
+    q = (C - p[:, None]).min(axis=0)
+    k = ora.kkt(C, f, g, X, p, q)
+    slack = np.sum(X * (C - p[:, None] - q[None, :]))
+    assert k.rd2 < 1e-30 and slack > 0.0
+    assert abs(k.gap - slack) < 1e-14
+
+
 def test_relative_measures_scale_with_their_own_data(ora):
     """Reading C5: each relative part is measured against the data it refers
     to -- the primal part against the marginals only, the dual part against the
