@@ -79,8 +79,8 @@ typedef struct {
 } pdot_points_cost;
 
 /*
- * Solver options.  Defaults (pdot_default_options) follow Sec. 5 of the paper
- * and the readings recorded in the design notes:
+ * Solver options.  Defaults (pdot_default_options) follow Sec. 5 of the paper;
+ * where the paper leaves a value open the default is a stated reading:
  *   tol 1e-4 (Sec. 5.1), restart check every 64 passes, adaptive step on
  *   (PDLP rule), adaptive restart on (beta_suff 0.1, beta_nec 0.9,
  *   beta_art 0.36), primal-weight update on (theta 0.5, omega0 1,

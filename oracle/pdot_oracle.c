@@ -37,7 +37,7 @@
  *                                distance), the input of cost-on-the-fly solves.
  *
  * Readings of passages the paper leaves open are listed beside the code that
- * takes them (C1..C16 in the project notes use the same numbering).
+ * takes them, numbered C1..C16.
  * The adaptive heuristics are pinned by special cases (restart candidate
  * rule, artificial-restart schedule, primal weight at theta = 0 and 1, default
  * first step) and end to end (the solve reaches the exact optimum).  The

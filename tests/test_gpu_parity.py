@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived in the design notes): FP32 plans with FP64 duals match the
-oracle's iterates to 1e-5 relative (Frobenius / 2-norm) after k steps; FP64
-plans to 1e-11.  Full solves are compared on objectives (the iterates are not
+Tolerances, from the arithmetic: FP32 plans with FP64 duals round the plan and
+the reduced cost to FP32 every step (2^-24 relative each), so after k <= 100
+steps the iterates match the oracle's to 1e-5 relative (Frobenius / 2-norm);
+FP64 plans differ only in summation order and match to 1e-11.  Full solves are compared on objectives (the iterates are not
 unique, reading C14) against the exact LP optimum.
 """
 import math
