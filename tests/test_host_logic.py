@@ -192,3 +192,12 @@ def test_measured_peak_reads_the_copy_bandwidth(tmp_path, monkeypatch):
     assert bench.measured_peak() == (6790.3, "measured")
     monkeypatch.setattr(bench, "PEAKS", str(tmp_path / "missing.json"))
     assert bench.measured_peak() == (6800.0, "fallback")
+
+
+def test_oracle_sample_times_whole_check_periods():
+    """The CPU baseline times the oracle over one check period (the work mix
+    of a real solve): 64 passes up to 64 x 64 grids, 8 above."""
+    import bench
+    assert bench.oracle_period(32) == 64 and bench.oracle_period(64) == 64 and bench.oracle_period(128) == 8
+    t = bench.oracle_sample(4)          # a 16 x 16 instance: 64 passes and one check
+    assert 0.0 < t < 1.0
