@@ -92,7 +92,11 @@ typedef struct {
 typedef struct {
     double tol;                    /* relative KKT tolerance for termination */
     int64_t max_iter;              /* bound on PDHG passes (accepted + rejected) */
-    double time_limit_s;           /* wall-clock limit of one solve; <= 0: none */
+    double time_limit_s;           /* wall-clock limit of one solve, tested at chunk ends; <= 0: none.
+                                      pdot_solve then reports the current iterate with its own KKT
+                                      measures.  The batch engine returns the current iterate with the
+                                      measures of the last check's restart candidate, which is that
+                                      iterate unless the running average had the smaller KKT error */
     int32_t restart_check_every;   /* K: restart/termination check after every K-th pass */
     int32_t adaptive_step;         /* 1: PDLP adaptive step size (Sec. 5); 0: constant eta */
     int32_t adaptive_restart;      /* 1: three restart conditions (Sec. 5); 0: Eq. (6) */
