@@ -894,7 +894,8 @@ struct BSlot {
     size_t bytes = 0;
     Clock::time_point t_submit;
     bool cancel = false;
-    bool timed_out = false;
+    bool timed_out = false;   // past its time limit: stopped on the device before the next chunk
+    bool stop_sent = false;   // that status write has been issued
     bool fresh = true;        // admitted, init check not run yet
     Ctrl last{};              // last snapshot of its controller
 };
@@ -929,11 +930,11 @@ struct DevArr {
 }  // namespace
 
 // Device count words of the batch engine: plan tiles per type, vector tiles,
-// instances, init-check plan tiles per type, init-check vector tiles, and one
-// pinned source word for status writes.
+// instances, init-check plan tiles per type, init-check vector tiles, and two
+// pinned source words for status writes (cancel, time limit).
 constexpr int CNT_VEC = NTT, CNT_INST = NTT + 1, CNT_INIT = NTT + 2, CNT_INIT_VEC = 2 * NTT + 2, CNT_WORDS = 2 * NTT + 3,
-              CNT_CANCEL = 15;
-static_assert(CNT_WORDS <= CNT_CANCEL, "count words overlap");
+              CNT_TIMEOUT = 14, CNT_CANCEL = 15;
+static_assert(CNT_WORDS <= CNT_TIMEOUT, "count words overlap");
 
 struct BatchEngine {
     std::deque<BSlot*> queue;
@@ -1234,7 +1235,13 @@ bool batch_retire(pdot_handle* h, const BatchEngine::Flight& f) {
         if (s->cancel) stt = ST_CANCELLED;
         else if (stt == ST_RUNNING && tlim > 0.0 &&
                  std::chrono::duration<double>(Clock::now() - s->t_submit).count() > tlim) {
-            stt = ST_TIMEOUT;
+            // The chunk already in flight still advances this instance, so its
+            // buffers are read only from the first snapshot after the device
+            // has stopped it (batch_apply_cancels writes ST_TIMEOUT before the
+            // next chunk).
+            s->timed_out = true;
+        }
+        if (stt == ST_TIMEOUT) {   // stopped by the host: return the current iterate
             s->last.res_slot = s->last.cur;
             s->last.res_avg = 0;
         }
@@ -1327,12 +1334,20 @@ bool batch_admit(pdot_handle* h) {
 void batch_apply_cancels(pdot_handle* h) {
     // Stop cancelled / timed-out resident instances on the device before the next chunk.
     BatchEngine* B = h->batch;
-    B->cnt.h[CNT_CANCEL] = ST_CANCELLED;   // pinned source word of the status writes
+    B->cnt.h[CNT_CANCEL] = ST_CANCELLED;   // pinned source words of the status writes
+    B->cnt.h[CNT_TIMEOUT] = ST_TIMEOUT;
     for (size_t i = 0; i < B->live.size(); ++i) {
         BSlot* s = B->live[i];
-        if (!s->cancel) continue;
-        CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_CANCEL], sizeof(int), cudaMemcpyHostToDevice,
-                           h->stream));
+        if (s->cancel) {
+            CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_CANCEL], sizeof(int), cudaMemcpyHostToDevice,
+                               h->stream));
+        } else if (s->timed_out && !s->stop_sent) {
+            // A solve that finishes in the chunk still in flight is retired from
+            // that chunk's snapshot, which predates this write.
+            CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_TIMEOUT], sizeof(int), cudaMemcpyHostToDevice,
+                               h->stream));
+            s->stop_sent = true;
+        }
     }
 }
 
