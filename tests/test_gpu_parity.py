@@ -367,6 +367,34 @@ def test_max_iter_returns_candidate():
     s.close()
 
 
+def test_decision_parity_of_full_solves():
+    """The adaptive heuristics' decisions on the GPU (FP64 plan) against the
+    FP64 oracle, solve for solve, on 24 instance/tolerance pairs.  Both sides
+    take the same readings with the same expressions; their summation orders
+    differ (tile partials vs sequential loops) and the accept/reject sequence
+    amplifies those last-bit differences, so pass counts are reported, not
+    required to match.  Required: both reach the tolerance and their
+    objectives agree to within what that tolerance allows.
+    `pytest -s -k decision_parity` prints the table."""
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0)
+    rows = []
+    for k, (m, n) in enumerate([(64, 64), (90, 47), (33, 150), (120, 100), (200, 64), (64, 200)]):
+        for marg in ("uniform", "dirichlet"):
+            ins = I.points_instance(m, n, 500 + k, marginals=marg)
+            for tol in (1e-4, 1e-6):
+                g = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=tol)
+                o = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=tol))
+                assert g.status == pdot.OK and o.status == 0
+                d = abs(g.result["primal_obj"] - o.primal_obj) / abs(o.primal_obj)
+                rows.append((m, n, marg, tol, g.result["passes"], o.passes, g.result["restarts"], o.restarts, d))
+                assert d <= (5e-4 if tol == 1e-4 else 5e-6), rows[-1]
+    s.close()
+    print("\n m x n, marginals, tol: passes gpu/oracle, restarts gpu/oracle, rel. objective difference")
+    for r in rows:
+        print(f" {r[0]}x{r[1]} {r[2]:9s} {r[3]:g}: {r[4]}/{r[5]}, {r[6]}/{r[7]}, {r[8]:.2e}")
+    print(f" equal passes {sum(r[4] == r[5] for r in rows)}/24, equal restarts {sum(r[6] == r[7] for r in rows)}/24")
+
+
 def test_time_limit_returns_the_current_iterate():
     """A solve past its time limit stops at the next chunk boundary and
     reports the current iterate with that iterate's own KKT measures."""
