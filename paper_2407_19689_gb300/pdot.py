@@ -362,7 +362,10 @@ class Solver:
     def __init__(self, options: Options | None = None, device: int = 0, stream=None, **overrides):
         torch = _torch()
         self.options = options if options is not None else pdot_default_options()
+        known = {name for name, _ in Options._fields_}
         for k, v in overrides.items():
+            if k not in known:   # a misspelt option would otherwise be ignored silently
+                raise TypeError(f"unknown solver option {k!r}")
             setattr(self.options, k, v)
         self.device = device
         if stream is None:

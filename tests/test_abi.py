@@ -90,3 +90,9 @@ def test_watchdog_selftest_rejects_bad_arguments_before_any_cuda_call(lib):
     assert lib.pdot_watchdog_selftest(0, (1 << 24) + 1, ctypes.byref(out)) == pdot.ERR_ARG
     assert lib.pdot_watchdog_selftest(0, 4096, None) == pdot.ERR_ARG
     assert out.value == -1
+
+
+def test_unknown_solver_option_is_rejected_before_any_cuda_call():
+    from paper_2407_19689_gb300 import pdot
+    with pytest.raises(TypeError, match="beta_artt"):
+        pdot.Solver(device=0, beta_artt=0.5)
