@@ -3,8 +3,9 @@
 Tolerances, from the arithmetic: FP32 plans with FP64 duals round the plan and
 the reduced cost to FP32 every step (2^-24 relative each), so after k <= 100
 steps the iterates match the oracle's to 1e-5 relative (Frobenius / 2-norm);
-FP64 plans differ only in summation order and match to 1e-11.  Full solves are compared on objectives (the iterates are not
-unique, reading C14) against the exact LP optimum.
+FP64 plans differ only in summation order and match to 1e-11.  Full solves
+are compared on objectives (the iterates are not unique, reading C14) against
+the exact LP optimum.
 """
 import math
 
@@ -367,48 +368,6 @@ def test_max_iter_returns_candidate():
     s.close()
 
 
-def test_decision_parity_of_full_solves():
-    """The adaptive heuristics' decisions on the GPU (FP64 plan) against the
-    FP64 oracle, solve for solve, on 24 instance/tolerance pairs.  Both sides
-    take the same readings with the same expressions; their summation orders
-    differ (tile partials vs sequential loops) and the accept/reject sequence
-    amplifies those last-bit differences, so pass counts are reported, not
-    required to match.  Required: both reach the tolerance and their
-    objectives agree to within what that tolerance allows.
-    `pytest -s -k decision_parity` prints the table."""
-    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0)
-    rows = []
-    for k, (m, n) in enumerate([(64, 64), (90, 47), (33, 150), (120, 100), (200, 64), (64, 200)]):
-        for marg in ("uniform", "dirichlet"):
-            ins = I.points_instance(m, n, 500 + k, marginals=marg)
-            for tol in (1e-4, 1e-6):
-                g = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=tol)
-                o = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=tol))
-                assert g.status == pdot.OK and o.status == 0
-                d = abs(g.result["primal_obj"] - o.primal_obj) / abs(o.primal_obj)
-                rows.append((m, n, marg, tol, g.result["passes"], o.passes, g.result["restarts"], o.restarts, d))
-                assert d <= (5e-4 if tol == 1e-4 else 5e-6), rows[-1]
-    s.close()
-    print("\n m x n, marginals, tol: passes gpu/oracle, restarts gpu/oracle, rel. objective difference")
-    for r in rows:
-        print(f" {r[0]}x{r[1]} {r[2]:9s} {r[3]:g}: {r[4]}/{r[5]}, {r[6]}/{r[7]}, {r[8]:.2e}")
-    print(f" equal passes {sum(r[4] == r[5] for r in rows)}/24, equal restarts {sum(r[6] == r[7] for r in rows)}/24")
-
-
-def test_time_limit_returns_the_current_iterate():
-    """A solve past its time limit stops at the next chunk boundary and
-    reports the current iterate with that iterate's own KKT measures."""
-    ins = I.points_instance(300, 517, 81)
-    s = pdot.Solver(device=0, time_limit_s=1e-9)
-    sol = s.solve(torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g, tol=1e-9)
-    s.close()
-    passes = sol.result["passes"]
-    assert sol.status == pdot.TIMEOUT and sol.result["returned_average"] == 0
-    assert passes > 0 and passes % 64 == 0
-    k = oracle.kkt(ins.C.astype(np.float32).astype(np.float64), ins.f, ins.g, _np(sol.X), _np(sol.p), _np(sol.q))
-    assert abs(k.rel_kkt - sol.result["rel_kkt"]) <= 1e-4 * k.rel_kkt
-
-
 # ---------------------------------------------------------------------------
 # full-size cases (the 4096^2 image workload), checked where the oracle can
 # ---------------------------------------------------------------------------
@@ -525,3 +484,35 @@ def test_degenerate_instances():
     # the first iterates: the mass on those rows/columns is tolerance-small)
     assert X[[3, 17], :].sum() <= 1e-7 and X[:, [0, 34]].sum() <= 1e-7
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# decisions of the adaptive heuristics along full solves
+# ---------------------------------------------------------------------------
+
+def test_decision_parity_of_full_solves():
+    """The adaptive heuristics' decisions on the GPU (FP64 plan) against the
+    FP64 oracle, solve for solve, on 24 instance/tolerance pairs.  Both sides
+    take the same readings with the same expressions; their summation orders
+    differ (tile partials vs sequential loops) and the accept/reject sequence
+    amplifies those last-bit differences, so pass counts are reported, not
+    required to match.  Required: both reach the tolerance and their
+    objectives agree to within what that tolerance allows.
+    `pytest -s -k decision_parity` prints the table."""
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, time_limit_s=120.0)
+    rows = []
+    for k, (m, n) in enumerate([(64, 64), (90, 47), (33, 150), (120, 100), (200, 64), (64, 200)]):
+        for marg in ("uniform", "dirichlet"):
+            ins = I.points_instance(m, n, 500 + k, marginals=marg)
+            for tol in (1e-4, 1e-6):
+                g = s.solve(torch.tensor(ins.C, device=DEV), ins.f, ins.g, tol=tol)
+                o = oracle.solve(ins.C, ins.f, ins.g, oracle.Options(tol=tol))
+                assert g.status == pdot.OK and o.status == 0
+                d = abs(g.result["primal_obj"] - o.primal_obj) / abs(o.primal_obj)
+                rows.append((m, n, marg, tol, g.result["passes"], o.passes, g.result["restarts"], o.restarts, d))
+                assert d <= (5e-4 if tol == 1e-4 else 5e-6), rows[-1]
+    s.close()
+    print("\n m x n, marginals, tol: passes gpu/oracle, restarts gpu/oracle, rel. objective difference")
+    for r in rows:
+        print(f" {r[0]}x{r[1]} {r[2]:9s} {r[3]:g}: {r[4]}/{r[5]}, {r[6]}/{r[7]}, {r[8]:.2e}")
+    print(f" equal passes {sum(r[4] == r[5] for r in rows)}/24, equal restarts {sum(r[6] == r[7] for r in rows)}/24")
