@@ -222,3 +222,16 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == rec["value"] and cb["sample"]
     assert rec["e2e"] == {"value": rec["value"], "unit": rec["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun only rank 0 runs the oracle and prints; other ranks exit 0
+    without work or output."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--grid", "4",
+                          "--gpus", "2", "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=300, cwd=root, env=env)
+    assert out.returncode == 0 and out.stdout.strip() == "", out.stderr[-2000:]
