@@ -93,10 +93,10 @@ typedef struct {
     double tol;                    /* relative KKT tolerance for termination */
     int64_t max_iter;              /* bound on PDHG passes (accepted + rejected) */
     double time_limit_s;           /* wall-clock limit of one solve, tested at chunk ends; <= 0: none.
-                                      pdot_solve then reports the current iterate with its own KKT
-                                      measures.  The batch engine returns the current iterate with the
-                                      measures of the last check's restart candidate, which is that
-                                      iterate unless the running average had the smaller KKT error */
+                                      The solve then reports the current iterate with its own KKT
+                                      measures (pdot_solve evaluates it after the chunk in flight; the
+                                      batch engine stops the instance at its next restart check, where
+                                      that iterate's measures are computed anyway) */
     int32_t restart_check_every;   /* K: restart/termination check after every K-th pass */
     int32_t adaptive_step;         /* 1: PDLP adaptive step size (Sec. 5); 0: constant eta */
     int32_t adaptive_restart;      /* 1: three restart conditions (Sec. 5); 0: Eq. (6) */
@@ -120,6 +120,11 @@ typedef struct {
                                       a chunk advances the oldest resident instance, then younger ones in
                                       admission order whose per-pass plan bytes still fit this budget
                                       (large solves keep the bandwidth; small ones fill in beside them) */
+    int32_t pass_kernel;           /* plan-pass kernel of single-instance calls with FP32 plans (pdot_solve,
+                                      pdot_pdhg_steps, pdot_time_pass): 0 = the autotuner's choice (default),
+                                      1 = register pipeline, 2 = bulk copies per row, 3 = bulk copies per
+                                      4-row group (generated costs with d > 4 take 2 instead).  FP64 plans
+                                      always take the register pipeline.  Other values: PDOT_ERR_ARG */
 } pdot_options;
 
 typedef struct {
@@ -208,7 +213,9 @@ pdot_status pdot_solve_host(pdot_handle *h, int64_t m, int64_t n, const void *C,
  * omega (tau = eta/omega, sigma = eta*omega), no restarts, starting from the
  * device state (X, p, q) and overwriting it with (X^k, p^k, q^k).  The uniform
  * running averages (Xbar, pbar, qbar) of Algorithm 2 are written when the
- * pointers are non-null.  k >= 0.
+ * pointers are non-null.  k >= 0.  The plan pass is the kernel pdot_solve runs
+ * for the same shape and cost type (the autotuner's choice, or the handle's
+ * pass_kernel option), with the same tile height.
  */
 pdot_status pdot_pdhg_steps(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
                             const double *f, const double *g, int64_t k, double eta, double omega,
@@ -260,7 +267,9 @@ pdot_status pdot_batch_pending(pdot_handle *h, int *queued, int *running);
  *   synchronises.
  *   Limits: 1 <= m, n <= 32768 and x_dtype F32 or F64, else PDOT_ERR_ARG.
  *   The first call on a device looks up the array's device address (once per
- *   device); make that first call before any stream capture.
+ *   device); make that first call before any stream capture.  The address is
+ *   kept for the life of the process, so calls on a device after a
+ *   cudaDeviceReset of it are not supported.
  *   All calls share the one array: the library runs one call per device at
  *   a time (a lock held until the call's stream synchronises, on error paths
  *   too), so calls from several host threads or on several streams wait for

@@ -20,10 +20,11 @@ the exact solver are pinned by the ``-m "not gpu"`` tests (closed forms,
 brute force, library LP/assignment solvers, invariants).  The adaptive
 heuristics inside ``solve`` are pinned by special cases whose outcome follows
 from pinned steps (the restart candidate rule, the artificial-restart
-schedule, the primal weight at theta = 0 and 1, the default first step) and
-end to end (the solve reaches the exact optimum).  The PDLP step-size rule
-and restart conditions (i), (ii) are "parity unpinned" individually: the
-paper prints no trajectory; they are pinned only end to end.
+schedule, restart conditions (i) and (ii) each alone, the primal weight at
+theta = 0 and 1, the default first step), by one-step cases of the PDLP
+step-size rule derived by hand on 1 x 1 and 2 x 1 instances (reject, accept
+with omega != 1, growth while the plan stands still, the schedule index),
+and end to end (the solve reaches the exact optimum).
 """
 from __future__ import annotations
 

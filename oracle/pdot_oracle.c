@@ -39,10 +39,12 @@
  * Readings of passages the paper leaves open are listed beside the code that
  * takes them, numbered C1..C16.
  * The adaptive heuristics are pinned by special cases (restart candidate
- * rule, artificial-restart schedule, primal weight at theta = 0 and 1, default
- * first step) and end to end (the solve reaches the exact optimum).  The
- * step-size rule and restart conditions (i), (ii) are "parity unpinned"
- * individually: the paper prints no trajectory to compare against.
+ * rule, artificial-restart schedule, restart conditions (i) and (ii) each
+ * alone, primal weight at theta = 0 and 1, default first step), by one-step
+ * cases of the step-size rule derived by hand on 1 x 1 and 2 x 1 instances,
+ * and end to end (the solve reaches the exact optimum).  The paper prints no
+ * trajectory, so the sequence of decisions along a real solve is pinned only
+ * through these cases and end to end.
  */
 #include <math.h>
 #include <stdint.h>

@@ -602,6 +602,13 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
                    const double* f, const double* g) {
     const int ttype = ttype_of(ctype);
     const int gen_d = gen_dims_of(C, ctype);
+    if (h->opt.pass_kernel > 0) {
+        // An explicit kernel choice: no timing, no cache entry.
+        int v = h->opt.pass_kernel - 1;
+        if (ttype == TT_GEN && gen_d > 4 && v == 2) v = 1;   // no grouped kernel beyond 4 coordinates
+        h->cfg.pass_bulk = v;
+        return;
+    }
     if (ttype == TT_GEN && gen_d > 4) {
         // More than 4 coordinates: the per-row kernel is the only bulk one.
         h->cfg.pass_bulk = h->cfg_base.pass_bulk ? 1 : 0;
@@ -894,8 +901,8 @@ struct BSlot {
     size_t bytes = 0;
     Clock::time_point t_submit;
     bool cancel = false;
-    bool timed_out = false;   // past its time limit: stopped on the device before the next chunk
-    bool stop_sent = false;   // that status write has been issued
+    bool timed_out = false;   // past its time limit: a stop request goes out before the next chunk
+    bool stop_sent = false;   // that request has been issued
     bool fresh = true;        // admitted, init check not run yet
     Ctrl last{};              // last snapshot of its controller
 };
@@ -1237,13 +1244,9 @@ bool batch_retire(pdot_handle* h, const BatchEngine::Flight& f) {
                  std::chrono::duration<double>(Clock::now() - s->t_submit).count() > tlim) {
             // The chunk already in flight still advances this instance, so its
             // buffers are read only from the first snapshot after the device
-            // has stopped it (batch_apply_cancels writes ST_TIMEOUT before the
-            // next chunk).
+            // has stopped it: batch_apply_cancels sends a stop request before
+            // the next chunk, whose first check ends the solve (ST_TIMEOUT).
             s->timed_out = true;
-        }
-        if (stt == ST_TIMEOUT) {   // stopped by the host: return the current iterate
-            s->last.res_slot = s->last.cur;
-            s->last.res_avg = 0;
         }
         if (stt == ST_RUNNING) {
             keep.push_back(s);
@@ -1334,17 +1337,18 @@ bool batch_admit(pdot_handle* h) {
 void batch_apply_cancels(pdot_handle* h) {
     // Stop cancelled / timed-out resident instances on the device before the next chunk.
     BatchEngine* B = h->batch;
-    B->cnt.h[CNT_CANCEL] = ST_CANCELLED;   // pinned source words of the status writes
-    B->cnt.h[CNT_TIMEOUT] = ST_TIMEOUT;
+    B->cnt.h[CNT_CANCEL] = ST_CANCELLED;   // pinned source words of the control writes
+    B->cnt.h[CNT_TIMEOUT] = 1;
     for (size_t i = 0; i < B->live.size(); ++i) {
         BSlot* s = B->live[i];
         if (s->cancel) {
             CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_CANCEL], sizeof(int), cudaMemcpyHostToDevice,
                                h->stream));
         } else if (s->timed_out && !s->stop_sent) {
-            // A solve that finishes in the chunk still in flight is retired from
-            // that chunk's snapshot, which predates this write.
-            CK(cudaMemcpyAsync(&s->w.ctrl->status, &B->cnt.h[CNT_TIMEOUT], sizeof(int), cudaMemcpyHostToDevice,
+            // Stop request: the instance's next check reports its current
+            // iterate with that iterate's own measures (ST_TIMEOUT).  A solve
+            // that finishes first is reported as finished.
+            CK(cudaMemcpyAsync(&s->w.ctrl->stop_req, &B->cnt.h[CNT_TIMEOUT], sizeof(int), cudaMemcpyHostToDevice,
                                h->stream));
             s->stop_sent = true;
         }
@@ -1486,6 +1490,7 @@ void pdot_default_options(pdot_options* o) {
     o->max_batch_slots = 4096;
     o->chunk_checks = 4;
     o->batch_active_bytes = 0;
+    o->pass_kernel = 0;
 }
 
 const char* pdot_status_str(pdot_status s) {
@@ -1518,6 +1523,7 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         if (h->opt.tile_rows < 0 || h->opt.tile_rows > 4096 || h->opt.tile_rows % 2 != 0) {
             throw ArgError{"tile_rows must be 0 or an even number in [2, 4096]"};
         }
+        if (h->opt.pass_kernel < 0 || h->opt.pass_kernel > 3) throw ArgError{"pass_kernel must be in 0..3"};
         int ndev = 0;
         CK(cudaGetDeviceCount(&ndev));
         if (device < 0 || device >= ndev) throw ArgError{"no such CUDA device"};
@@ -1711,6 +1717,7 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
         if (k < 0 || !(eta > 0.0) || !(omega > 0.0) || !X || !p || !q) throw ArgError{"bad k, eta, omega or state"};
         const int ttype = ttype_of(c_dtype);
+        autotune_pass(h, m, n, C, c_dtype, ldc, f, g);   // the pass kernel a solve of this shape runs
         const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, c_dtype));
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);

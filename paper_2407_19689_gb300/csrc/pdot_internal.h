@@ -44,6 +44,8 @@ struct Ctrl {
     int cur, nxt, bar, barn, anc;
     int status;          // ST_RUNNING or a final status
     int res_slot, res_avg;
+    int stop_req;        // host-written: 1 = stop at the next check with the current iterate (time limit)
+    int pad_;
     // options
     double tol, beta, beta_suff, beta_nec, beta_art, theta, R, eps_zero;
     long long max_passes;

@@ -1634,6 +1634,15 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
     KP c;
     kkt_parts(S, A[0], A[7], A[6], A[2], c);
     S->checks += 1;
+    if (mode == MODE_CHECK && S->stop_req) {
+        // Stopped by the host (time limit): the current iterate, with the
+        // measures this check has just computed for it.
+        report(S, c);
+        S->status = ST_TIMEOUT;
+        S->res_slot = S->cur;
+        S->res_avg = 0;
+        return;
+    }
     if (mode == MODE_INIT) {
         report(S, c);
         S->kkt0 = c.kkt;

@@ -55,6 +55,7 @@ class Options(ctypes.Structure):
         ("max_batch_slots", ctypes.c_int32),
         ("chunk_checks", ctypes.c_int32),
         ("batch_active_bytes", ctypes.c_uint64),
+        ("pass_kernel", ctypes.c_int32),
     ]
 
 

@@ -118,3 +118,22 @@ def test_active_bytes_policy_keeps_results(active_bytes):
         _same(ra[ta], rb[tb])
     free.close()
     pol.close()
+
+
+def test_batch_time_limit_returns_the_current_iterate():
+    """A batch instance past its time limit is stopped at its next restart
+    check and returns the current iterate with that iterate's own KKT
+    measures (PDOT_TIMEOUT), as pdot_solve does."""
+    ins = I.points_instance(300, 517, 81)
+    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
+    b = pdot.BatchSolver(device=0, time_limit_s=1e-9)
+    t = b.submit(C, ins.f, ins.g, tol=1e-9)
+    sol = b.run()[t]
+    b.close()
+    r = sol.result
+    assert sol.status == pdot.TIMEOUT and r["returned_average"] == 0
+    assert r["passes"] > 0 and r["passes"] % 64 == 0
+    X, p, q = (t_.double().cpu().numpy() for t_ in (sol.X, sol.p, sol.q))
+    k = oracle.kkt(ins.C.astype(np.float32).astype(np.float64), ins.f, ins.g, X, p, q)
+    assert abs(k.rel_kkt - r["rel_kkt"]) <= 1e-4 * k.rel_kkt
+    assert abs(k.cx - r["primal_obj"]) <= 1e-6 * abs(k.cx)

@@ -378,20 +378,6 @@ def grid64():
     return ins
 
 
-def test_full_size_4096_kstep_parity(s32, grid64):
-    """Two PDHG steps at the full 4096 x 4096 size, every element compared."""
-    ins = grid64
-    C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
-    Co = _np(C)
-    m = n = 4096
-    z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
-    eta = 0.7 / math.sqrt(m + n)
-    g = s32.pdhg_steps(C, ins.f, ins.g, *z, k=3, eta=eta, omega=1.0)
-    o = oracle.pdhg_steps(Co, ins.f, ins.g, *z, k=3, eta=eta, omega=1.0)
-    for a, b in zip(g[:3], o[:3]):
-        assert rel(_np(a), b) < 1e-5
-
-
 def test_full_size_4096_solve_kkt_is_honest(s32, grid64):
     """A 1e-4 solve at 4096^2: the FP64 oracle recomputes the KKT of the
     returned (X, p, q) and agrees with the GPU's report."""
@@ -516,3 +502,60 @@ def test_decision_parity_of_full_solves():
     for r in rows:
         print(f" {r[0]}x{r[1]} {r[2]:9s} {r[3]:g}: {r[4]}/{r[5]}, {r[6]}/{r[7]}, {r[8]:.2e}")
     print(f" equal passes {sum(r[4] == r[5] for r in rows)}/24, equal restarts {sum(r[6] == r[7] for r in rows)}/24")
+
+
+# ---------------------------------------------------------------------------
+# GPU twins of the hand-derived step-size cases and of restart conditions
+# (i) and (ii) alone (tests/heuristic_cases.py); FP64 plans
+# ---------------------------------------------------------------------------
+
+def test_step_rule_from_the_origin_grows_then_rejects_on_gpu():
+    """Reading C6 on 1 x 1 from the origin, derived by hand: pass 1 is accepted
+    with eta_bar = inf and grows the step, pass 2 is rejected; the counts, the
+    kept state and the next step size match the derivation."""
+    from heuristic_cases import step_rule_from_origin_case
+    (C, f, g), eta2 = step_rule_from_origin_case()
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, restart_check_every=2, max_iter=2, eta0=1.0,
+                    primal_weight_update=0, time_limit_s=60.0)
+    sol = s.solve(torch.tensor(C, dtype=torch.float64, device=DEV), np.array(f), np.array(g), tol=1e-15)
+    s.close()
+    r = sol.result
+    assert sol.status == pdot.MAX_ITER
+    assert (r["passes"], r["iters"], r["rejected_steps"]) == (2, 1, 1)
+    assert abs(r["eta"] - eta2) <= 1e-14 * eta2
+    assert _np(sol.X)[0, 0] == 0.0 and _np(sol.p)[0] == 1.0 and _np(sol.q)[0] == 1.0
+
+
+def test_step_rule_growth_schedule_on_gpu():
+    """1 x 1, C = 1, f = g = 1 from the origin with eta0 = 0.3: two accepted
+    passes with eta_bar = inf grow the step to 0.3 (1 + 2^-0.6)(1 + 3^-0.6)."""
+    s = pdot.Solver(device=0, x_dtype=pdot.F64, restart_check_every=2, max_iter=2, eta0=0.3,
+                    primal_weight_update=0, time_limit_s=60.0)
+    sol = s.solve(torch.ones((1, 1), dtype=torch.float64, device=DEV), np.ones(1), np.ones(1), tol=1e-15)
+    s.close()
+    r = sol.result
+    want = 0.3 * (1 + 2 ** -0.6) * (1 + 3 ** -0.6)
+    assert (r["passes"], r["iters"], r["rejected_steps"]) == (2, 2, 0)
+    assert abs(r["eta"] - want) <= 1e-14 * want
+
+
+@pytest.mark.parametrize("which", ["i", "ii"])
+def test_restart_condition_alone_on_gpu(which):
+    """Sec. 5 condition (i) or (ii) alone, constant step: the GPU restarts at
+    the same check as the pinned composition (none when its pass budget ends
+    at that check, one when it ends a check later) and returns the same
+    candidate."""
+    from heuristic_cases import restart_condition_case
+    ins, opts, j, want = restart_condition_case(oracle, which)
+    K = opts["check_every"]
+    kw = dict(x_dtype=pdot.F64, time_limit_s=60.0, restart_check_every=K, adaptive_step=0, adaptive_restart=1,
+              primal_weight_update=0, eta0=opts["eta0"], beta_suff=opts["beta_suff"], beta_nec=opts["beta_nec"],
+              beta_art=opts["beta_art"])
+    C = torch.tensor(ins.C, device=DEV)
+    for budget, restarts in ((j * K, 0), ((j + 1) * K, 1)):
+        s = pdot.Solver(device=0, max_iter=budget, **kw)
+        sol = s.solve(C, ins.f, ins.g, tol=1e-15)
+        s.close()
+        assert sol.status == pdot.MAX_ITER and sol.result["restarts"] == restarts
+    for got, w in zip((sol.X, sol.p, sol.q), want):
+        assert rel(_np(got), w) < 1e-11

@@ -9,10 +9,10 @@ buffer size, so every mutant stays memory-safe.
 The Sec. 5 heuristics are pinned through special cases where their outcome
 follows from pinned steps and counts (the candidate rule, the artificial
 restart schedule, the primal weight at theta = 0 and 1, the default first
-step); mistakes in the step-size schedule (reading C6) and in restart
-condition (i) are caught end to end: the solve no longer reaches its
-tolerance within the capped pass budget (20 times what the unmodified
-oracle needs) or stops at another point.
+step, restart conditions (i) and (ii) each alone) and through one-step cases
+of the step-size rule derived by hand (reading C6).  For the mutants of the
+step-size rule and of conditions (i) and (ii) the check also names the pin
+that must fail: a direct pin, not only an end-to-end solve.
 """
 import os
 import re
@@ -61,10 +61,24 @@ MUTANTS = [
      "        kkt_prev = kk->kkt;\n        k = 0;"),
     ("candidate_tie_inverted", "use_avg = !(kc.kkt < ka.kkt);", "use_avg = (kc.kkt < ka.kkt);"),
     ("restart_sufficient_flipped", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
-                 "restart = (kk->kkt >= opt->beta_suff * kkt0)"),
+     "restart = (kk->kkt >= opt->beta_suff * kkt0)", "restart_condition_alone"),
     ("restart_artificial_dropped", "|| ((double)k >= opt->beta_art * (double)total);", ";"),
-    ("eta_bar_drops_factor_two", "(2.0 * fabs(inter))", "(fabs(inter))"),
-    ("eta_growth_exponent", "pow(t1, -0.6)", "pow(t1, -0.3)"),
+    ("eta_bar_drops_factor_two", "(2.0 * fabs(inter))", "(fabs(inter))", "step_rule"),
+    ("eta_growth_exponent", "pow(t1, -0.6)", "pow(t1, -0.3)", "step_rule"),
+    ("eta_bar_omega_swapped", "(omega * dX2 + dy2 / omega)", "(dX2 / omega + omega * dy2)", "step_rule"),
+    ("eta_inter_drops_columns", "inter += (qn[j] - q[j]) * cd[j];", ";", "step_rule"),
+    ("eta_dy_drops_columns", "dy2 += (qn[j] - q[j]) * (qn[j] - q[j]);", ";", "step_rule"),
+    ("eta_schedule_index", "double t1 = (double)(total + 2);", "double t1 = (double)(total + 3);", "step_rule"),
+    ("eta_accept_after_update", "accept = eta <= eta_bar;", "accept = eta_next <= eta_bar;", "step_rule"),
+    ("eta_shrink_uses_eta", "double a = (1.0 - pow(t1, -0.3)) * eta_bar;", "double a = (1.0 - pow(t1, -0.3)) * eta;",
+     "step_rule"),
+    ("restart_sufficient_vs_previous", "restart = (kk->kkt <= opt->beta_suff * kkt0)",
+     "restart = (kk->kkt <= opt->beta_suff * kkt_prev)", "restart_condition_alone"),
+    ("restart_necessary_no_rise_test", "(kk->kkt <= opt->beta_nec * kkt0 && kk->kkt > kkt_prev)",
+     "(kk->kkt <= opt->beta_nec * kkt0)", "restart_condition_alone"),
+    ("restart_necessary_rise_vs_start", "&& kk->kkt > kkt_prev)", "&& kk->kkt > kkt0)", "restart_condition_alone"),
+    ("restart_previous_not_tracked", "            kkt_prev = kk->kkt;\n            continue;", "            continue;",
+     "restart_condition_alone"),
     ("primal_weight_inverted", "log(dy / dX)", "log(dX / dy)"),
     ("adaptive_eta0_doubled", "eta = opt->adaptive_step ? 1.0 / sqrt", "eta = opt->adaptive_step ? 2.0 / sqrt"),
 ]
@@ -74,8 +88,10 @@ def _failed_pins(out: str):
     return sorted(set(re.findall(r"FAILED \S*::(\S+)", out)))
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=lambda v: v if isinstance(v, str) and " " not in v else "")
-def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+@pytest.mark.parametrize("case", MUTANTS, ids=lambda c: c[0])
+def test_pins_catch_planted_mistake(tmp_path, case):
+    name, old, new = case[:3]
+    direct = case[3] if len(case) > 3 else None   # a pin that must fail by itself
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site of {name} is not unique"
     base = str(tmp_path / "oracle_mutant")
@@ -83,10 +99,11 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new):
         fh.write(src.replace(old, new))
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", base + ".so", base + ".c", "-lm"])
     env = dict(os.environ, PDOT_ORACLE_MUTANT=base)
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+    pins = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+    args = [pins, "-x"] if direct is None else [pins, "-k", direct]
+    r = subprocess.run([sys.executable, "-m", "pytest", *args, "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
     out = r.stdout + r.stderr
     assert r.returncode in (0, 1), out[-2000:]
-    assert r.returncode == 1, f"mutant {name} survived every pin"
+    assert r.returncode == 1, f"mutant {name} survived every pin" + ("" if direct is None else f" named {direct!r}")
     assert _failed_pins(out), out[-2000:]

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2407_19689_gb300 import instances as I
+from heuristic_cases import restart_condition_case, step_rule_from_origin_case
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ot_closed_forms.txt")
 
@@ -431,6 +432,108 @@ def test_adaptive_default_step_is_one_over_norm_A(ora):
     b = ora.solve(ins.C, ins.f, ins.g, ora.Options(tol=1e-6, eta0=1.0 / math.sqrt(32)))
     assert (a.passes, a.restarts, a.rejected) == (b.passes, b.restarts, b.rejected)
     assert np.array_equal(a.X, b.X) and np.array_equal(a.p, b.p) and a.eta == b.eta
+
+
+# --------------------------------------------------------------------------
+# Sec. 5 adaptive step size (reading C6, PDLP's rule), on instances small
+# enough to take one step by hand
+# --------------------------------------------------------------------------
+#
+# With m = n = 1 (or m = 2, n = 1) one Algorithm 2 step is a handful of
+# scalar operations, so eta_bar, the accept/reject decision and the next step
+# size follow from the rule's statement without the oracle's code:
+#   eta_bar = (omega ||dX||^2 + ||(dp, dq)||^2 / omega) / (2 |dp^T dX 1 + dq^T dX^T 1|),
+#   accept iff eta <= eta_bar,  eta' = min((1 - t^-0.3) eta_bar, (1 + t^-0.6) eta)
+# with t = 2 + (iterations accepted so far); eta' is used next either way.
+
+def _few_passes(ora, C, f, g, X0, p0, q0, eta0, omega0, passes=1):
+    """A solve stopped by its pass budget after `passes` passes (one check,
+    at the end), adaptive step on, primal-weight update off."""
+    opts = ora.Options(tol=0.0, max_passes=passes, check_every=passes, adaptive_step=1, primal_weight_update=0,
+                       eta0=eta0, omega0=omega0)
+    arr = lambda v: np.array(v, dtype=np.float64)  # noqa: E731
+    return ora.solve(arr(C), arr(f), arr(g), opts, X0=arr(X0), p0=arr(p0), q0=arr(q0))
+
+
+def test_step_rule_rejects_a_step_beyond_eta_bar(ora):
+    """1 x 1, C = 1, f = g = 1, start X = 5/2, p = q = 0, eta = omega = 1.
+    X+ = 5/2 - (1 - 0 - 0) = 3/2; (2X+ - X) 1 = 1/2, so p+ = q+ = 1 - 1/2 = 1/2.
+    dX = -1, dp = dq = 1/2: ||dX||^2 = 1, ||dy||^2 = 1/2, dy^T A dx = -1, so
+    eta_bar = (1 + 1/2) / 2 = 3/4 < eta: rejected, the state is kept, and
+    eta' = min((1 - 2^-0.3) 3/4, (1 + 2^-0.6) 1) = (1 - 2^-0.3) 3/4."""
+    r = _few_passes(ora, [[1.0]], [1.0], [1.0], [[2.5]], [0.0], [0.0], 1.0, 1.0)
+    assert (r.passes, r.iters, r.rejected) == (1, 0, 1)
+    assert r.X[0, 0] == 2.5 and r.p[0] == 0.0 and r.q[0] == 0.0
+    assert abs(r.eta - 0.75 * (1 - 2 ** -0.3)) <= 1e-15
+
+
+def test_step_rule_accepts_and_weights_by_omega(ora):
+    """Same data, start X = 5/2, p = q = 0, eta = 1/2, omega = 2 (tau = 1/4,
+    sigma = 1).  X+ = 5/2 - 1/4 = 9/4; (2X+ - X) 1 = 2, so p+ = q+ = 1 - 2 = -1.
+    dX = -1/4, dp = dq = -1: omega ||dX||^2 = 1/8, ||dy||^2 / omega = 1 and
+    dy^T A dx = 1/2, so eta_bar = (1/8 + 1) / 1 = 9/8 >= eta: accepted, and
+    eta' = min((1 - 2^-0.3) 9/8, (1 + 2^-0.6) / 2) = (1 - 2^-0.3) 9/8.
+    (omega on the other two terms would give eta_bar = 4 + 1/32.)"""
+    r = _few_passes(ora, [[1.0]], [1.0], [1.0], [[2.5]], [0.0], [0.0], 0.5, 2.0)
+    assert (r.passes, r.iters, r.rejected) == (1, 1, 0)
+    assert r.X[0, 0] == 2.25 and r.p[0] == -1.0 and r.q[0] == -1.0
+    assert abs(r.eta - 1.125 * (1 - 2 ** -0.3)) <= 1e-15
+
+
+def test_step_rule_two_sources_one_target(ora):
+    """m = 2, n = 1: C = [1; 0], f = [1/2; 1/2], g = 1, start X = [1; 1],
+    p = 0, q = 0, eta = omega = 1.  X+ = [max(0, 1 - 1); max(0, 1 - 0)] = [0; 1];
+    2X+ - X = [-1; 1] has row sums [-1; 1] and column sum 0, so
+    p+ = [1/2 + 1; 1/2 - 1] = [3/2; -1/2] and q+ = 1 - 0 = 1.
+    dX = [-1; 0], dp = [3/2; -1/2], dq = 1: ||dX||^2 = 1,
+    ||dy||^2 = 9/4 + 1/4 + 1 = 7/2, dy^T A dx = (3/2)(-1) + (-1/2)(0) + (1)(-1) = -5/2,
+    eta_bar = (1 + 7/2) / 5 = 9/10 < eta: rejected, eta' = (1 - 2^-0.3) 9/10.
+    (Without the column part dq^T dX^T 1, eta_bar would be 3/2: accepted.)"""
+    r = _few_passes(ora, [[1.0], [0.0]], [0.5, 0.5], [1.0], [[1.0], [1.0]], [0.0, 0.0], [0.0], 1.0, 1.0)
+    assert (r.passes, r.iters, r.rejected) == (1, 0, 1)
+    assert abs(r.eta - 0.9 * (1 - 2 ** -0.3)) <= 1e-15
+
+
+def test_step_rule_grows_the_step_while_the_plan_does_not_move(ora):
+    """1 x 1, C = 1, f = g = 1 from the origin with eta = 0.3: the first two
+    passes leave X = 0 (reduced cost C - p - q = 1, then 1 - 0.6 = 0.4 > 0),
+    so dX = 0, dy^T A dx = 0, eta_bar = +inf: both are accepted and the step
+    grows by (1 + t^-0.6) with t = 2, then t = 3."""
+    r = _few_passes(ora, [[1.0]], [1.0], [1.0], [[0.0]], [0.0], [0.0], 0.3, 1.0, passes=2)
+    assert (r.passes, r.iters, r.rejected) == (2, 2, 0)
+    assert r.X[0, 0] == 0.0
+    assert abs(r.eta - 0.3 * (1 + 2 ** -0.6) * (1 + 3 ** -0.6)) <= 1e-15
+
+
+def test_step_rule_from_the_origin_grows_then_rejects(ora):
+    (C, f, g), eta2 = step_rule_from_origin_case()
+    r = _few_passes(ora, C, f, g, [[0.0]], [0.0], [0.0], 1.0, 1.0, passes=2)
+    assert (r.passes, r.iters, r.rejected) == (2, 1, 1)
+    assert r.X[0, 0] == 0.0 and r.p[0] == 1.0 and r.q[0] == 1.0
+    assert abs(r.eta - eta2) <= 1e-15 * eta2
+
+
+# --------------------------------------------------------------------------
+# Sec. 5 restart conditions (i) and (ii), each alone, with a constant step
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["i", "ii"])
+def test_restart_condition_alone(ora, which):
+    """Each of Sec. 5's conditions (i) and (ii) alone (the others switched
+    off: beta_nec = 0 or beta_suff = 0, and beta_art so large that (iii) never
+    holds), constant step 0.1, a check every 8 passes.  A solve whose pass
+    budget ends at check j (where its termination test comes first) has not
+    restarted; one whose budget ends a check later restarted once, at check j,
+    to that check's candidate, and returns the candidate of the next 8 steps."""
+    ins, opts, j, want = restart_condition_case(ora, which)
+    K = opts["check_every"]
+    assert (which, j) in (("i", 3), ("ii", 4))
+    r0 = ora.solve(ins.C, ins.f, ins.g, ora.Options(max_passes=j * K, **opts))
+    assert r0.status == ora.STATUS_MAX_ITER and r0.restarts == 0
+    r1 = ora.solve(ins.C, ins.f, ins.g, ora.Options(max_passes=(j + 1) * K, **opts))
+    assert r1.status == ora.STATUS_MAX_ITER and r1.restarts == 1
+    for got, w in zip((r1.X, r1.p, r1.q), want):
+        np.testing.assert_allclose(got, w, rtol=1e-12, atol=1e-16)
 
 
 def test_solve_rel_mode_one_plus(ora):
