@@ -46,6 +46,8 @@ def parse():
                     help="storage type of the cost matrix; points: generated from the pixel coordinates in every pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched-vs-plain record (256 uneven instances) out of the default line")
     ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
                     help="grid: the single image-like instance (default, the headline); batch: 256 uneven "
                          "instances through the batch engine vs one instance per launch; serve: Poisson "
@@ -206,6 +208,17 @@ def oracle_sample(grid: int):
     t = time.perf_counter()
     oracle.solve(C32, ins.f, ins.g, oracle.Options(tol=0.0, max_passes=passes, check_every=passes))
     return (time.perf_counter() - t) / passes
+
+
+def oracle_objective(grid: int, tol: float):
+    """The FP64 oracle's own objective at this tolerance on the workload
+    (recorded by oracle/reference_counts.py), or None."""
+    path = os.path.join(ROOT, "oracle", "reference_counts.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)[f"grid{grid}"][f"{tol:g}"]["primal_obj"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def oracle_passes_to_tol(grid: int, tol: float):
@@ -377,6 +390,13 @@ def run_ours(args):
                "sample": f"{sample_passes} FP64 PDHG passes and one check of the oracle on the full instance: "
                          f"{sec_pass:.3f} s/pass x {p_tol} passes to tol ({p_src})"}
 
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        # The batched workload's own record (256 uneven instances through the
+        # batch engine vs one instance per launch), after the timed region.
+        batch = batch_record(1e-6)
+
+    ref_obj = oracle_objective(args.grid, args.tol) if args.cdtype == "f32" else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
@@ -386,12 +406,15 @@ def run_ours(args):
             "config": grid_config(args, world),
             "time_to_tol_s": elapsed / args.steps, "passes_to_tol": passes, "iters": last.iters,
             "restarts": last.restarts, "rel_kkt": last.rel_kkt, "primal_obj": last.primal_obj,
+            "primal_obj_rel_err_vs_oracle": (abs(last.primal_obj - ref_obj) / abs(ref_obj)) if ref_obj else None,
+            "oracle_primal_obj": ref_obj,
             "hbm_gbs_per_iter": last.hbm_bytes / (elapsed / args.steps) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": pdot.kernel_name(variant, ctype),
                          "bytes_per_launch": bytes_pass, "ms_per_launch": ms_pass,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     solver.close()
@@ -402,15 +425,22 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched and served workloads (manual runs; one JSON line each)
 # ---------------------------------------------------------------------------
-def run_batch(args):
+def batch_record(tol: float = 1e-6, count: int = 256) -> dict:
+    """The batched workload: `count` instances, m and n log-uniform in
+    [64, 2048] (seeded), U[0,1]^2 points, squared-Euclidean FP32 cost,
+    Dirichlet(1) marginals, each solved to `tol`; once through the batch
+    engine (all submitted at once) and once one instance per launch
+    (pdot_solve, the same kernels).  Inputs are on the device before either
+    timed region; the clocks are host wall clocks around whole runs (each
+    run ends with a device synchronisation)."""
+    import math
+
     import torch
 
-    from paper_2407_19689_gb300 import _build, pdot
     from paper_2407_19689_gb300 import instances as I
-    _build.build()
-    pdot.load()
+    from paper_2407_19689_gb300 import pdot
     dev = "cuda:0"
-    sizes = I.batch_sizes(args.batch_count, I.seed_for(3))
+    sizes = I.batch_sizes(count, I.seed_for(3))
     insts = []
     for k, (m, n) in enumerate(sizes):
         ins = I.batch_instance(m, n, I.seed_for(3, k + 1))
@@ -420,7 +450,7 @@ def run_batch(args):
     def batched():
         b = pdot.BatchSolver(device=0, chunk_checks=4)
         for C, f, g in insts:
-            b.submit(C, f, g, tol=args.tol, want_plan=False)
+            b.submit(C, f, g, tol=tol, want_plan=False)
         torch.cuda.synchronize()
         t = time.perf_counter()
         res = b.run()
@@ -434,7 +464,7 @@ def run_batch(args):
         s = pdot.Solver(device=0)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        res = [s.solve(C, f, g, tol=args.tol, want_plan=False) for C, f, g in insts]
+        res = [s.solve(C, f, g, tol=tol, want_plan=False) for C, f, g in insts]
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         s.close()
@@ -445,7 +475,6 @@ def run_batch(args):
     tp, rp = plain()
     okb = sum(1 for v in rb.values() if v.status == pdot.OK)
     okp = sum(1 for v in rp if v.status == pdot.OK)
-    import math
 
     def sgm10(ts):
         # shifted geometric mean with shift 10 s, the paper's summary of solve times
@@ -459,20 +488,30 @@ def run_batch(args):
     objs_b = sorted((tid, v.result["primal_obj"]) for tid, v in rb.items())
     maxdiff = max(abs(a[1] - b.result["primal_obj"]) / abs(b.result["primal_obj"])
                   for a, b in zip(objs_b, rp))
-    line = {"metric": METRIC, "value": len(insts) / tb, "unit": f"solves/s ({len(insts)} uneven instances to "
-            f"{args.tol:g} rel. KKT)", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tb * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals",
-            "data": "synthetic",
-            "config": {"workload": f"batch{len(insts)}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems,
-                       "tol": args.tol},
-            "batched": {"seconds": tb, "solves_per_s": len(insts) / tb, "ok": okb, "gpu_launches": launches,
+    return {"workload": f"batch{count}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems, "tol": tol,
+            "batched": {"seconds": tb, "solves_per_s": count / tb, "ok": okb, "gpu_launches": launches,
+                        "passes": sum(v.result["passes"] for v in rb.values()),
                         "sgm10_completion_s": sgm10([v.result["seconds"] for v in rb.values()]),
                         "geomean_gap": geomean_gap(list(rb.values()))},
-            "plain": {"seconds": tp, "solves_per_s": len(insts) / tp, "ok": okp,
+            "plain": {"seconds": tp, "solves_per_s": count / tp, "ok": okp,
+                      "passes": sum(v.result["passes"] for v in rp),
                       "sgm10_solve_s": sgm10([v.result["seconds"] for v in rp]),
                       "geomean_gap": geomean_gap(rp),
                       "form": "pdot_solve one instance at a time, same kernels"},
             "speedup_vs_plain": tp / tb, "max_rel_obj_diff_batched_vs_plain": maxdiff}
+
+
+def run_batch(args):
+    from paper_2407_19689_gb300 import _build, pdot
+    _build.build()
+    pdot.load()
+    rec = batch_record(args.tol, args.batch_count)
+    tb = rec["batched"]["seconds"]
+    line = {"metric": METRIC, "value": args.batch_count / tb, "unit": f"solves/s ({args.batch_count} uneven "
+            f"instances to {args.tol:g} rel. KKT)", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tb * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 plan/cost, f64 duals",
+            "data": "synthetic",
+            "config": {"workload": rec["workload"], "elements": rec["elements"], "tol": args.tol}, **rec}
     print(json.dumps(line), flush=True)
 
 

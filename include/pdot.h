@@ -125,6 +125,12 @@ typedef struct {
                                       1 = register pipeline, 2 = bulk copies per row, 3 = bulk copies per
                                       4-row group (generated costs with d > 4 take 2 instead).  FP64 plans
                                       always take the register pipeline.  Other values: PDOT_ERR_ARG */
+    int32_t compensated_cost;      /* FP32 plans (reading C9): 1 = the reduced cost C - p - q is formed
+                                      from the FP64 duals split into FP32 hi/lo pairs, with the rounding
+                                      error of C - p_hi recovered exactly (TwoSum), so its error is
+                                      relative to itself rather than to p and q (fewer passes at tight
+                                      tolerances; about 6 % more time per pass at 4096^2, 1 % at 16384^2);
+                                      0 (default) = (C - (float)p) - (float)q.  No effect on FP64 plans */
 } pdot_options;
 
 typedef struct {
@@ -201,6 +207,46 @@ pdot_status pdot_destroy(pdot_handle *h);
 pdot_status pdot_solve(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
                        const double *f, const double *g, double tol,
                        void *X_out, double *p_out, double *q_out, pdot_result *res);
+
+/*
+ * Starting point and solver state of pdot_solve_from.  Algorithm 2 takes an
+ * initial point (X^{0,0}, p^{0,0}, q^{0,0}) as input; pdot_solve starts at the
+ * origin (reading C1).  pdot_solve_from starts from a caller's point, or
+ * resumes a solve from the state an earlier call exported (checkpoint /
+ * resume: the paper has no counterpart).  All pointers are device memory.
+ *   X0 (m x n, x_dtype), p0 (m), q0 (n): nullable initial point (a null part
+ *       is 0).  The solve then runs exactly as pdot_solve does from there.
+ *   state_in: nullable; pdot_state_bytes(m, n, x_dtype) bytes written as
+ *       state_out by an earlier call on the same (m, n, x_dtype), the same C,
+ *       f, g and the same options.  The solve continues from that state: the
+ *       plans, duals, averages and restart anchor, the step size, primal
+ *       weight and every counter.  A solve split at a stop by max_iter or
+ *       time_limit_s and resumed this way takes the same passes and returns
+ *       the same result, bit for bit, as the uninterrupted solve on a handle
+ *       that picks the same pass kernel and tile height (the autotuner's
+ *       choice is cached per handle; pass_kernel and tile_rows fix it).
+ *       max_iter counts passes from the original start.  Overrides X0/p0/q0.
+ *       A blob of another shape or type, or not written by this library:
+ *       PDOT_ERR_ARG.
+ *   state_out: nullable; receives the state when the solve stops (before the
+ *       Algorithm 3 rounding of round_plan), whatever the status.
+ */
+typedef struct {
+    const void *X0;
+    const double *p0, *q0;
+    const void *state_in;
+    void *state_out;
+} pdot_start;
+
+/* Bytes of a solver-state blob for an m x n solve with plans in x_dtype
+ * (F32 or F64); 0 for invalid arguments.  Needs no GPU. */
+int64_t pdot_state_bytes(int64_t m, int64_t n, pdot_dtype x_dtype);
+
+/* pdot_solve from a starting point or a saved state (see pdot_start); start
+ * may be NULL (then the same as pdot_solve). */
+pdot_status pdot_solve_from(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                            const double *f, const double *g, double tol, const pdot_start *start,
+                            void *X_out, double *p_out, double *q_out, pdot_result *res);
 
 /* Same as pdot_solve with every pointer in HOST memory; the host <-> device
  * copies happen inside the call. */
@@ -285,7 +331,9 @@ int64_t pdot_launch_count(pdot_handle *h);
 /* Diagnostics for roofline measurement: set up the instance, take three
  * PDHG steps (so the running average is read), then launch the fused plan
  * pass `reps` times back to back on the handle's stream between two CUDA
- * events.  *ms_per_pass receives the mean device time of one pass;
+ * events, each launch reading the plans the previous one wrote (as accepted
+ * passes of a solve do; the dual update is left out, so every launch moves
+ * the same bytes).  *ms_per_pass receives the mean device time of one pass;
  * *bytes_per_pass (nullable) the algorithmic bytes one pass moves:
  * m n (sizeof C + 4 sizeof X) (read C, X, Xbar; write X+, Xbar+; sizeof C
  * is 0 for a generated cost);

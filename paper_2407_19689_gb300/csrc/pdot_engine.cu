@@ -104,6 +104,8 @@ struct Work {
     double* V = nullptr;
     double* rowpart = nullptr;
     double* colpart = nullptr;
+    double* rowpart2 = nullptr;
+    double* colpart2 = nullptr;
     double* tpart = nullptr;
     double* vpart = nullptr;
     Ctrl* ctrl = nullptr;
@@ -125,6 +127,8 @@ size_t work_bytes(long long m, long long n, int xtype, int tile_rows, Work* w) {
     const size_t oV = take((size_t)NSLOT * 2 * (m + n) * sizeof(double));
     const size_t oR = take((size_t)nstrips * m * sizeof(double));
     const size_t oC = take((size_t)nchunks * ldx * sizeof(double));
+    const size_t oR2 = take((size_t)nstrips * m * sizeof(double));
+    const size_t oC2 = take((size_t)nchunks * ldx * sizeof(double));
     const size_t oT = take((size_t)ntiles * TP * sizeof(double));
     const size_t oP = take((size_t)nvt * VP * sizeof(double));
     const size_t oS = take(sizeof(Ctrl));
@@ -137,6 +141,8 @@ size_t work_bytes(long long m, long long n, int xtype, int tile_rows, Work* w) {
         w->V = (double*)(b + oV);
         w->rowpart = (double*)(b + oR);
         w->colpart = (double*)(b + oC);
+        w->rowpart2 = (double*)(b + oR2);
+        w->colpart2 = (double*)(b + oC2);
         w->tpart = (double*)(b + oT);
         w->vpart = (double*)(b + oP);
         w->ctrl = (Ctrl*)(b + oS);
@@ -159,6 +165,7 @@ Inst make_inst(const Work& w, const void* C, int ctype, long long ldc, const dou
     I.X = w.X; I.xslot = w.m * w.ldx;
     I.V = w.V; I.vslot = 2 * (w.m + w.n);
     I.rowpart = w.rowpart; I.colpart = w.colpart; I.tpart = w.tpart; I.vpart = w.vpart;
+    I.rowpart2 = w.rowpart2; I.colpart2 = w.colpart2;
     I.ctrl = w.ctrl; I.ticket = w.ticket;
     I.nstrips = w.nstrips; I.nchunks = w.nchunks; I.tile_rows = w.tile_rows; I.ntiles = w.ntiles; I.nvt = w.nvt;
     I.l2_keep_c = 0;
@@ -225,6 +232,7 @@ struct pdot_handle {
     int coop = 0;                // 1: single FP32-plan solves run one cooperative launch per chunk (opt-in: measured slower)
     GridBar* d_gb = nullptr;
     long long l2_bytes = 0;
+    void* d_tp = nullptr;        // pdot_time_pass: a second instance view and controller
 };
 
 namespace {
@@ -312,18 +320,21 @@ void validate_marginals(pdot_handle* h, long long m, long long n, const double* 
 
 // Rows per plan tile.  `kernel`: the FP32-plan pass kernel the tiles are for
 // (0 register, 1 bulk per row, 2 bulk per 4-row group).
-int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kernel, bool batch) {
+// split: for the grouped kernel too, one tile per resident warp instead of
+// 32-row tiles through the queue.
+int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kernel, bool batch, bool split = false) {
     if (h->opt.tile_rows > 0) return h->opt.tile_rows;
     const long long nstrips = (n + STRIP - 1) / STRIP;
     if (batch) return 64;   // many instances share the tile queue: moderate tiles keep it balanced
     if (ttype == TT_F64) kernel = 0;
-    if (kernel == 2) return 32;   // grouped kernel: short tiles through the dynamic queue
+    if (kernel == 2 && !split) return 32;   // grouped kernel: short tiles through the dynamic queue
     // Otherwise split the instance evenly over the resident warps, one tile
     // each (the last wave of a dynamic queue would leave a tail), as tall as
     // that allows (fewer column partials).
     const long long blocks = ttype == TT_F64 ? h->cfg.tile_blocks_f64
                              : kernel == 1   ? (h->coop && h->cfg.coop_blocks > 0 ? h->cfg.coop_blocks
                                                                                   : h->cfg.bulk_blocks)
+                             : kernel == 2   ? h->cfg.group_blocks
                                              : h->cfg.tile_blocks;
     const long long warps = blocks * TWARPS;
     long long nch = warps / nstrips;
@@ -430,6 +441,7 @@ bool keep_c_in_l2(pdot_handle* h, const Inst& I) {
 void stage_instance(pdot_handle* h, const Inst& I) {
     *h->h_inst = I;
     h->h_inst->l2_keep_c = keep_c_in_l2(h, I) ? 1 : 0;
+    h->h_inst->comp = h->opt.compensated_cost ? 1 : 0;
     h->cfg.gen_dims = I.ctype == PDOT_POINTS ? I.gen.d : 0;
     CK(cudaMemcpyAsync(h->d_inst, h->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
@@ -473,7 +485,8 @@ void launch_chunk(pdot_handle* h, int ttype, int K) {
                               w.m * 4 + ttype,
                               w.n,
                               K,
-                              (long long)h->cfg.pdl * 100 + (long long)h->cfg.pass_bulk * 10 + (long long)h->cfg.pass_u,
+                              (long long)h->cfg.comp * 1000 + (long long)h->cfg.pdl * 100 +
+                                  (long long)h->cfg.pass_bulk * 10 + (long long)h->cfg.pass_u,
                               w.tile_rows,
                               h->cfg.gen_dims};
     if (!h->opt.use_graph) {
@@ -629,13 +642,14 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
     }
     // Each candidate is timed on whole PDHG steps (pass + dual update): tile
     // height also sets how many partial sums the dual update has to read.
-    const int cands[4][2] = {{1, 0}, {2, 32}, {2, 64}, {2, 128}};
+    // Tile height 0: one tile per resident warp.
+    const int cands[5][2] = {{1, 0}, {2, 0}, {2, 32}, {2, 64}, {2, 128}};
     float best = 1e30f;
     int best_k = 1, best_tr = tile_rows_for(h, m, n, ttype, 1, false);
     const int reps = m * n >= (1LL << 26) ? 6 : 20;
     for (const auto& c : cands) {
         const int kern = c[0];
-        const int tr = c[1] ? c[1] : tile_rows_for(h, m, n, ttype, kern, false);
+        const int tr = c[1] ? c[1] : tile_rows_for(h, m, n, ttype, kern, false, true);
         h->cfg.pass_bulk = kern;
         ensure_work(h, m, n, h->opt.x_dtype, tr);
         ensure_maps(h);
@@ -677,9 +691,113 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
     h->cfg.pass_bulk = best_k;
 }
 
+// ---------------------------------------------------------------------------
+// Solver-state blob of pdot_solve_from (checkpoint / resume): a header with
+// the controller, then the plans of the current, average and anchor slots
+// (m x ldx each) and their vector sets ([p | q | r | c]).
+// ---------------------------------------------------------------------------
+constexpr uint64_t STATE_MAGIC = 0x3130455441545350ull;   // "PSTATE01"
+constexpr size_t STATE_HEAD = 1024;
+struct StateHead {
+    uint64_t magic;
+    long long m, n;
+    int xtype;
+    int replay;   // 1: the last check stopped at the pass budget before its restart logic ran
+    Ctrl ctrl;
+};
+static_assert(sizeof(StateHead) <= STATE_HEAD, "state header too large");
+
+struct StateLayout {
+    size_t plan, vec, total;
+    size_t plan_off(int k) const { return STATE_HEAD + (size_t)k * plan; }
+    size_t vec_off(int k) const { return STATE_HEAD + 3 * plan + (size_t)k * vec; }
+};
+StateLayout state_layout(long long m, long long n, int xtype) {
+    const long long ldx = (n + 3) / 4 * 4;
+    StateLayout L;
+    L.plan = align_up((size_t)m * (size_t)ldx * xsize_of(xtype), 256);
+    L.vec = align_up(sizeof(double) * 2 * (size_t)(m + n), 256);
+    L.total = STATE_HEAD + 3 * L.plan + 3 * L.vec;
+    return L;
+}
+
+// Write the state of the handle's workspace (controller S, as read back from
+// the device after the last chunk) into the device blob `out`.
+void export_state(pdot_handle* h, const Ctrl& S, void* out) {
+    const Work& w = h->ws;
+    const StateLayout L = state_layout(w.m, w.n, w.xtype);
+    StateHead hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = STATE_MAGIC;
+    hd.m = w.m;
+    hd.n = w.n;
+    hd.xtype = w.xtype;
+    hd.replay = S.status == ST_MAX_ITER ? 1 : 0;
+    hd.ctrl = S;
+    char* o = static_cast<char*>(out);
+    CK(cudaMemcpyAsync(o, &hd, sizeof(hd), cudaMemcpyHostToDevice, h->stream));
+    const int role[3] = {S.cur, S.bar, S.anc};
+    const size_t pb = (size_t)w.m * (size_t)w.ldx * xsize_of(w.xtype), vb = sizeof(double) * 2 * (size_t)(w.m + w.n);
+    for (int k = 0; k < 3; ++k) {
+        CK(cudaMemcpyAsync(o + L.plan_off(k), (const char*)w.X + (size_t)role[k] * pb, pb, cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(cudaMemcpyAsync(o + L.vec_off(k), w.V + (size_t)role[k] * 2 * (size_t)(w.m + w.n), vb,
+                           cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));   // hd lives on this stack frame
+}
+
+// Load a blob into the workspace (slots 0, 1, 2 = current, average, anchor)
+// and build the controller to upload: the blob's iteration state with the
+// handle's options (S holds a freshly initialised controller on entry).
+// Returns true when the stopped check must run again (its restart logic).
+bool import_state(pdot_handle* h, const void* in, Ctrl* S) {
+    const Work& w = h->ws;
+    StateHead hd;
+    CK(cudaMemcpyAsync(&hd, in, sizeof(hd), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hd.magic != STATE_MAGIC || hd.m != w.m || hd.n != w.n || hd.xtype != w.xtype)
+        throw ArgError{"state_in is not a state blob of this shape and plan type"};
+    const StateLayout L = state_layout(w.m, w.n, w.xtype);
+    const char* b = static_cast<const char*>(in);
+    const size_t pb = (size_t)w.m * (size_t)w.ldx * xsize_of(w.xtype), vb = sizeof(double) * 2 * (size_t)(w.m + w.n);
+    for (int k = 0; k < 3; ++k) {
+        CK(cudaMemcpyAsync((char*)w.X + (size_t)k * pb, b + L.plan_off(k), pb, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(w.V + (size_t)k * 2 * (size_t)(w.m + w.n), b + L.vec_off(k), vb, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    }
+    const Ctrl& B = hd.ctrl;
+    S->eta = B.eta; S->omega = B.omega; S->tau = B.tau; S->sigma = B.sigma;
+    S->kkt0 = B.kkt0; S->kkt_prev = B.kkt_prev;
+    S->k = B.k; S->total = B.total; S->passes = B.passes; S->restarts = B.restarts; S->rejected = B.rejected;
+    S->checks = B.checks - (hd.replay ? 1 : 0);   // the stopped check runs again
+    S->norm_b = B.norm_b; S->norm_C = B.norm_C;
+    S->r_rp2 = B.r_rp2; S->r_rd2 = B.r_rd2; S->r_cx = B.r_cx; S->r_dual = B.r_dual; S->r_gap = B.r_gap;
+    S->r_kkt = B.r_kkt; S->r_rel_p = B.r_rel_p; S->r_rel_d = B.r_rel_d; S->r_rel_gap = B.r_rel_gap; S->r_rel = B.r_rel;
+    S->cur = 0; S->bar = 1; S->anc = 2; S->nxt = 3; S->barn = 4;
+    S->status = ST_RUNNING;
+    S->res_slot = 0;
+    S->res_avg = 0;
+    return hd.replay != 0;
+}
+
+// Initial point of pdot_solve_from in slot 0 (a null part is 0).
+void upload_start(pdot_handle* h, const pdot_start* st) {
+    const Work& w = h->ws;
+    const size_t xs = xsize_of(w.xtype);
+    CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xs, h->stream));
+    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));
+    if (st && st->X0)
+        CK(cudaMemcpy2DAsync(w.X, (size_t)w.ldx * xs, st->X0, (size_t)w.n * xs, (size_t)w.n * xs, (size_t)w.m,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    if (st && st->p0) CK(cudaMemcpyAsync(w.V, st->p0, sizeof(double) * (size_t)w.m, cudaMemcpyDeviceToDevice, h->stream));
+    if (st && st->q0)
+        CK(cudaMemcpyAsync(w.V + w.m, st->q0, sizeof(double) * (size_t)w.n, cudaMemcpyDeviceToDevice, h->stream));
+}
+
 pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, int ctype, long long ldc,
                        const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
-                       pdot_result* res) {
+                       pdot_result* res, const pdot_start* start = nullptr) {
     const auto t_start = Clock::now();
     if (!res) throw ArgError{"null result"};
     check_common_args(h, m, n, C, ctype, ldc, f, g);
@@ -699,12 +817,18 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
 
     Ctrl* S = h->h_ctrl;
     init_ctrl(h, S, m, n, tol, norm_b, 0.0, false, 0.0, 0.0);   // norms: computed by the init check
-    CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-    const size_t xs = xsize_of(w.xtype);
-    CK(cudaMemsetAsync(w.X, 0, (size_t)w.m * w.ldx * xs, h->stream));                 // X = 0 (C1)
-    CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));  // p = q = 0
     CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
-    run_check(h, ttype, MODE_INIT);
+    if (start && start->state_in) {
+        // Resume: the saved state, the handle's options; the check the saved
+        // solve stopped at runs again with its restart logic.
+        const bool replay = import_state(h, start->state_in, S);
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        if (replay) run_check(h, ttype, MODE_CHECK);
+    } else {
+        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        upload_start(h, start);   // X = 0, p = q = 0 (C1) unless a starting point is given
+        run_check(h, ttype, MODE_INIT);
+    }
 
     const int K = std::max(1, h->opt.restart_check_every);
     const double tlim = h->opt.time_limit_s;
@@ -744,6 +868,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     cudaEventDestroy(ev[1]);
     CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (start && start->state_out) export_state(h, *S, start->state_out);
     if (timed_out && S->status == ST_RUNNING) {
         // Evaluate the current iterate and report it.
         run_check(h, ttype, MODE_INIT);
@@ -1074,6 +1199,7 @@ void batch_compose(pdot_handle* h) {
             ldc = padded_ldc(s->req.n, s->req.c_dtype);
         }
         B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
+        B->insts.h[i].comp = h->opt.compensated_cost ? 1 : 0;
         const int tt = s->ttype;
         const bool act = active[(size_t)i] != 0;
         for (int t = 0; t < s->w.ntiles; ++t) {
@@ -1491,6 +1617,7 @@ void pdot_default_options(pdot_options* o) {
     o->chunk_checks = 4;
     o->batch_active_bytes = 0;
     o->pass_kernel = 0;
+    o->compensated_cost = 0;
 }
 
 const char* pdot_status_str(pdot_status s) {
@@ -1575,6 +1702,7 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         // Programmatic dependent launch: on (PDOT_PDL=0 turns it off).
         const char* pp = getenv("PDOT_PDL");
         h->cfg.pdl = (pp && atoi(pp) == 0) ? 0 : 1;
+        h->cfg.comp = h->opt.compensated_cost ? 1 : 0;
         h->cfg_base = h->cfg;
         CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
         CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));
@@ -1628,6 +1756,7 @@ pdot_status pdot_destroy(pdot_handle* h) {
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->d_cnt) cudaFree(h->d_cnt);
     if (h->d_gb) cudaFree(h->d_gb);
+    if (h->d_tp) cudaFree(h->d_tp);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1641,6 +1770,22 @@ pdot_status pdot_solve(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         return solve_impl(h, m, n, C, c_dtype, ldc, f, g, tol, X_out, p_out, q_out, res);
+    });
+}
+
+int64_t pdot_state_bytes(int64_t m, int64_t n, pdot_dtype x_dtype) {
+    if (m < 1 || n < 1 || m > (1LL << 31) / 2 || n > (1LL << 31) / 2) return 0;
+    if (x_dtype != PDOT_F32 && x_dtype != PDOT_F64) return 0;
+    return (int64_t)state_layout(m, n, x_dtype).total;
+}
+
+pdot_status pdot_solve_from(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                            const double* f, const double* g, double tol, const pdot_start* start, void* X_out,
+                            double* p_out, double* q_out, pdot_result* res) {
+    if (!h) return PDOT_ERR_ARG;
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        return solve_impl(h, m, n, C, c_dtype, ldc, f, g, tol, X_out, p_out, q_out, res, start);
     });
 }
 
@@ -1912,17 +2057,35 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
         CK(cudaMemsetAsync(w.V, 0, sizeof(double) * 2 * (size_t)(w.m + w.n), h->stream));
         run_check(h, ttype, MODE_INIT);
         for (int s = 0; s < 3; ++s) run_step(h, ttype);   // steady state: k > 0, the average is read
+        // Two views of the instance whose controllers swap the current and
+        // next roles (and the pass parity, so the row order alternates):
+        // launches alternate between them, so each pass reads the plans the
+        // previous one wrote, as accepted passes of a solve do; the dual
+        // update is left out, so every launch moves the same bytes.
+        if (!h->d_tp) {
+            CK(cudaMalloc(&h->d_tp, sizeof(Inst) + sizeof(Ctrl) + 256));
+        }
+        Inst* d_inst2 = reinterpret_cast<Inst*>(h->d_tp);
+        Ctrl* d_ctrl2 = reinterpret_cast<Ctrl*>(reinterpret_cast<char*>(h->d_tp) + align_up(sizeof(Inst), 256));
+        CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        std::swap(S->cur, S->nxt);
+        std::swap(S->bar, S->barn);
+        S->passes += 1;
+        Inst I2 = *h->h_inst;
+        I2.ctrl = d_ctrl2;
+        CK(cudaMemcpyAsync(d_ctrl2, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(d_inst2, &I2, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));   // I2 lives on this stack frame
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        // The plan pass alone, repeated on the same state (roles do not change
-        // without the dual kernel), so every launch moves the same bytes.
         CK(cudaEventRecord(e0, h->stream));
-        // Alternate two work counters: each launch resets every counter but
-        // its own, so the next launch finds its counter at zero.
+        // Alternate two work counters too: each launch resets every counter
+        // but its own, so the next launch finds its counter at zero.
         for (int r = 0; r < reps; ++r) {
             const int wc = (r & 1) ? wc_index(WC_AUX, ttype) : wc_index(WC_PASS, ttype);
-            CKL(launch_pass(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream, wc));
+            CKL(launch_pass(ttype, (r & 1) ? d_inst2 : h->d_inst, h->d_tmap, h->d_cnt, h->wctr, h->cfg, h->stream, wc));
         }
         CK(cudaEventRecord(e1, h->stream));
         CK(cudaEventSynchronize(e1));

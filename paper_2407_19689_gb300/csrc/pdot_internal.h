@@ -9,7 +9,9 @@
 //   V    : NSLOT vector sets of 2(m+n) doubles, one per plan slot:
 //          [p (m) | q (n) | r = X1 (m) | c = X^T1 (n)].
 //   rowpart[nstrips][m], colpart[nchunks][ldx]: FP64 partial row/column sums
-//          written by the plan-tile kernels and reduced in a fixed order.
+//          written by the plan-tile kernels and reduced in a fixed order (a
+//          pass writes sums of X+ - X; the check, sums of the average);
+//          rowpart2 / colpart2: the check's sums of the current plan.
 //   tpart[ntiles][TP], vpart[nvt][VP]: FP64 per-tile scalar partials
 //          (nvt = ceil((m+n)/VE) vector tiles).
 //   Ctrl : the scalar state of Algorithm 2 and the Sec. 5 controller.
@@ -123,12 +125,16 @@ struct Inst {
     long long vslot;
     double* rowpart;
     double* colpart;
+    double* rowpart2;    // the check's exact row / column sums of the current plan
+    double* colpart2;
     double* tpart;
     double* vpart;
     Ctrl* ctrl;
     unsigned int* ticket;
     int nstrips, nchunks, tile_rows, ntiles, nvt;
     int l2_keep_c;       // 1: C fits in L2 next to the streams; load it evict-last, stream X evict-first
+    int comp;            // FP32 plans: 1 = compensated reduced cost (duals as FP32 hi/lo pairs), 0 = plain
+    int pad_;
 };
 
 // Grid barrier state of the cooperative chunk kernel (device memory, zeroed
@@ -173,12 +179,15 @@ struct LaunchCfg {
     int coop_blocks;      // CTAs of the cooperative chunk kernel (all co-resident)
     int pdl;              // 1: launch with programmatic dependent launch
     int gen_dims;         // largest coordinate count of the generated costs in flight (TT_GEN)
+    int comp;             // 1: plan passes of FP32 plans form the compensated reduced cost
 };
 
 // Tile and vector-tile counts are read from device memory, so one captured
 // graph serves every batch composition; nv_hint sizes the vector grids.
+// dir_xor flips the row order a pass takes (the order alternates with the
+// instance's pass count; the pass timer flips it between its launches).
 int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
-                const LaunchCfg& cfg, void* stream, int wc_override = -1);
+                const LaunchCfg& cfg, void* stream, int wc_override = -1, int dir_xor = 0);
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream, bool direct = false);
 int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr, int mode,

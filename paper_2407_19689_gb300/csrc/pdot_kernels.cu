@@ -144,6 +144,37 @@ struct CostRow<GenC<DM>, A> {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Reduced cost C_ij - p_i - q_j of the plan pass (reading C9)
+// ---------------------------------------------------------------------------
+// FP32 plans take the FP64 duals as FP32 pairs, y = hi + lo with hi = RN(y)
+// and lo = RN(y - hi).  With `comp` the reduced cost is then formed so that
+// its error is of its own size, not of the size of p and q: the rounding
+// error e of s = c - p_hi is recovered exactly (Knuth's TwoSum: c - p_hi =
+// s + e), s - q_hi is exact where the reduced cost is small (Sterbenz: s is
+// then within a factor 2 of q_hi), and the small terms e, p_lo, q_lo are
+// added last.  Without `comp`: (c - p_hi) - q_hi, two FP32 roundings of the
+// size of p and q (the plan's fixed point is then only as accurate as that).
+// FP64 plans use the FP64 duals directly.
+__device__ __forceinline__ void split_dual(double y, float& hi, float& lo) {
+    hi = (float)y;
+    lo = (float)(y - (double)hi);
+}
+__device__ __forceinline__ void split_dual(double y, double& hi, double& lo) {
+    hi = y;
+    lo = 0.0;
+}
+__device__ __forceinline__ float reduced_cost(float c, float ph, float pl, float qh, float ql, bool comp) {
+    if (!comp) return (c - ph) - qh;
+    const float s = c - ph;
+    const float bv = s - c;
+    const float e = (c - (s - bv)) + (-ph - bv);   // c - ph = s + e exactly
+    return (s - qh) + (e - (pl + ql));
+}
+__device__ __forceinline__ double reduced_cost(double c, double ph, double, double qh, double, bool) {
+    return (c - ph) - qh;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     // Butterfly: every lane ends with the same, order-fixed sum.
@@ -241,8 +272,21 @@ __device__ __forceinline__ void reset_other_counters(unsigned* wctr, int mine) {
 // ---------------------------------------------------------------------------
 // Plan pass: Algorithm 2 primal step + running average + partial sums
 // ---------------------------------------------------------------------------
-template <typename TC, typename TX, int U>
-__device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, int lane) {
+// Row order of a plan tile: every other pass walks its tiles bottom-up, so the
+// rows a pass reads first are the ones the previous pass touched last, which
+// are still in L2 (C read, X+ and Xbar+ just written) when the plan does not
+// fit in it.  Which order a pass takes changes only the order of its FP32
+// column partial sums; it is a function of the instance's pass count (and of
+// `dir_xor`, a launch parameter used by the pass timer), so runs stay
+// reproducible and an instance gives the same result alone or in a batch.
+__device__ __forceinline__ bool pass_reversed(const Ctrl& S, int dir_xor) {
+    return ((S.passes ^ (long long)dir_xor) & 1) != 0;
+}
+
+// CP: compensated reduced cost (a kernel template parameter, so the plain
+// path is compiled without the compensated one and costs nothing extra).
+template <typename TC, typename TX, int U, bool CP>
+__device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, int lane, bool rev) {
     typedef TX A;
     const long long m = I.m, n = I.n, ldx = I.ldx;
     const int strip = lt % I.nstrips, chunk = lt / I.nstrips;
@@ -261,30 +305,32 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
     const A tau = (A)S.tau;
     const A w = (A)(1.0 / (double)(S.k + 1));
 
-    A qv[4];
+    A qv[4], ql[4];
     bool valid[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         valid[e] = j0 + e < n;
-        qv[e] = valid[e] ? (A)q[j0 + e] : A(0);
+        split_dual(valid[e] ? q[j0 + e] : 0.0, qv[e], ql[e]);
     }
     double cs[4] = {0.0, 0.0, 0.0, 0.0};
     double dx2 = 0.0;
     double* rowpart = I.rowpart + (long long)strip * m;
-    // Row pointers advanced by the leading dimension (lanes past n never dereference).
-    const long long xo = i0 * ldx + j0;
-    const TX* Xr = X + xo;
-    const TX* Xbr = Xb + xo;
-    TX* Xnr = Xn + xo;
-    TX* Xbnr = Xbn + xo;
+    const long long nb = (i1 - i0 + U - 1) / U;   // batches of U rows, walked in either order
 
-    for (long long ib = i0; ib < i1; ib += U) {
-        A c[U][4], x[U][4], xb[U][4], pv[U];
+    for (long long bi = 0; bi < nb; ++bi) {
+        const long long ib = i0 + (rev ? nb - 1 - bi : bi) * U;
+        // Row pointers of the batch (lanes past n never dereference).
+        const long long xo = ib * ldx + j0;
+        const TX* Xr = X + xo;
+        const TX* Xbr = Xb + xo;
+        TX* Xnr = Xn + xo;
+        TX* Xbnr = Xbn + xo;
+        A c[U][4], x[U][4], xb[U][4], pv[U], pl[U];
         // Issue every load of the U-row batch before any arithmetic.
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool rv = ib + u < i1;
-            pv[u] = rv ? (A)p[ib + u] : A(0);
+            split_dual(rv ? p[ib + u] : 0.0, pv[u], pl[u]);
             if (rv && on) {
                 cr.get(ib + u, c[u]);
                 ld4(Xr + u * ldx, x[u]);
@@ -307,14 +353,14 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
             A rs = A(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const A R = (c[u][e] - pv[u]) - qv[e];          // reduced cost C - p - q
+                const A R = reduced_cost(c[u][e], pv[u], pl[u], qv[e], ql[e], CP);   // C - p - q
                 A v = x[u][e] - tau * R;
                 v = v > A(0) ? v : A(0);                         // projection onto X >= 0
                 v = (valid[e] && rv) ? v : A(0);                 // padding columns / rows past the tile stay 0
                 const A d = v - x[u][e];
                 dxa += d * d;
-                rs += v;
-                csa[e] += v;
+                rs += d;                                          // row / column sums of X+ - X
+                csa[e] += d;
                 xn[e] = v;
                 xbn[e] = first ? v : xb[u][e] + w * (v - xb[u][e]);
             }
@@ -328,10 +374,6 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
 #pragma unroll
         for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
         dx2 += (double)dxa;
-        Xr += U * ldx;
-        Xbr += U * ldx;
-        Xnr += U * ldx;
-        Xbnr += U * ldx;
     }
     if (on) {
         double* cp = I.colpart + (long long)chunk * ldx + j0;
@@ -342,9 +384,10 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
     if (lane == 0) I.tpart[(long long)lt * TP + 0] = dx2;
 }
 
-template <typename TC, typename TX, int U>
+template <typename TC, typename TX, int U, bool CP>
 __global__ void __launch_bounds__(TWARPS * 32, sizeof(TX) == 4 ? 2 : 1)
-k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc) {
+k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp, unsigned* wctr, int wc,
+       int dir_xor) {
     pdl_enter();
     const int T = *Tp;
     reset_other_counters(wctr, wc);
@@ -357,7 +400,7 @@ k_pass(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const i
         const Inst& I = insts[tr.inst];
         const Ctrl& S = *I.ctrl;
         if (S.status != ST_RUNNING) continue;
-        pass_tile<TC, TX, U>(I, S, tr.local, lane);
+        pass_tile<TC, TX, U, CP>(I, S, tr.local, lane, pass_reversed(S, dir_xor));
     }
 }
 
@@ -431,9 +474,11 @@ __device__ __forceinline__ bool wait_stage(unsigned bar, unsigned parity, long l
 
 constexpr int STAGE_BYTES = 3 * STRIP * 4;   // C (<= 512 B), X (512 B), Xbar (512 B)
 
-constexpr int MAX_TILE_ROWS = 256;
+// Row duals of a tile are staged in shared memory, as FP32 pairs, per window
+// of PWIN rows.
+constexpr int PWIN = 128;
 template <int S>
-__host__ __device__ constexpr int warp_smem_bytes() { return S * STAGE_BYTES + S * 8 + S * 8 + MAX_TILE_ROWS * 4; }
+__host__ __device__ constexpr int warp_smem_bytes() { return S * STAGE_BYTES + S * 8 + S * 8 + PWIN * 8; }
 
 struct RowRef {       // what a stage holds
     int tile;         // global tile index (into tmap), -1 = none
@@ -450,7 +495,7 @@ template <int S>
 struct RowPipe {
     unsigned char* wbase;
     RowRef* refs;
-    float* pbuf;
+    float2* pbuf;
     unsigned wbase_s, bars_s;
     long long issued, consumed;
 };
@@ -460,7 +505,7 @@ __device__ __forceinline__ void row_pipe_init(RowPipe<S>& P, unsigned char* dsm,
     P.wbase = dsm + warp * warp_smem_bytes<S>();
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(P.wbase + S * STAGE_BYTES);
     P.refs = reinterpret_cast<RowRef*>(P.wbase + S * STAGE_BYTES + S * 8);
-    P.pbuf = reinterpret_cast<float*>(P.wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
+    P.pbuf = reinterpret_cast<float2*>(P.wbase + S * STAGE_BYTES + S * 16);   // p_i of the tile's rows
     P.wbase_s = smem_u32(P.wbase);
     P.bars_s = smem_u32(bars);
     P.issued = P.consumed = 0;
@@ -475,13 +520,13 @@ __device__ __forceinline__ void row_pipe_init(RowPipe<S>& P, unsigned char* dsm,
 // One pass over the tiles handed out by the queue counter `qctr`.  Returns
 // false when a stage never completed (bounded wait); the instance's status
 // is then set to an error.
-template <typename TC, int S>
+template <typename TC, int S, bool CP>
 __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, int T, unsigned* qctr,
-                             bulk::RowPipe<S>& P, int lane) {
+                             bulk::RowPipe<S>& P, int lane, int dir_xor) {
     using namespace bulk;
     unsigned char* wbase = P.wbase;
     RowRef* refs = P.refs;
-    float* pbuf = P.pbuf;
+    float2* pbuf = P.pbuf;
     const unsigned wbase_s = P.wbase_s;
     const unsigned bars_s = P.bars_s;
     constexpr int DM = GenDims<TC>::value;
@@ -491,10 +536,11 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
 
     // ---- producer: the tile being issued, resolved once per tile ----
     int p_tile = T;
-    long long p_row = 0, p_end = 0, p_last_ragged = -1;
-    const char* p_c = nullptr;          // C row p_row, column c0
-    const char* p_x = nullptr;          // X row p_row
-    const char* p_xb = nullptr;         // Xbar row p_row
+    long long p_row = 0, p_stop = 0, p_r0 = 0, p_last_ragged = -1;
+    long long p_dir = 1;                // +1: top-down, -1: bottom-up (pass_reversed)
+    const char* p_c0 = nullptr;         // C at the tile's first row, column c0
+    const char* p_x0 = nullptr;         // X at the tile's first row
+    const char* p_xb0 = nullptr;        // Xbar at the tile's first row
     long long p_cstride = 0, p_xstride = 0;
     unsigned p_cbytes = 0, p_xbytes = 0;
     bool p_first = true;
@@ -513,17 +559,22 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
             const long long c0 = (long long)strip * STRIP;
             const long long ncols = min((long long)STRIP, I.n - c0);
-            p_row = (long long)chunk * I.tile_rows;
-            p_end = min(p_row + (long long)I.tile_rows, I.m);
+            const long long r0 = (long long)chunk * I.tile_rows;
+            const long long r1 = min(r0 + (long long)I.tile_rows, I.m);
+            const bool rev = pass_reversed(Sc, dir_xor);
+            p_dir = rev ? -1 : 1;
+            p_r0 = r0;
+            p_row = rev ? r1 - 1 : r0;
+            p_stop = rev ? r0 - 1 : r1;
             p_xstride = I.ldx * 4;
             if constexpr (!GEN) {
                 p_cstride = I.ldc * (long long)sizeof(TC);
-                p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+                p_c0 = reinterpret_cast<const char*>(I.C) + r0 * p_cstride + c0 * (long long)sizeof(TC);
             }
-            p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
-                                                p_row * I.ldx + c0);
-            p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
-                                                 p_row * I.ldx + c0);
+            p_x0 = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
+                                                 r0 * I.ldx + c0);
+            p_xb0 = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
+                                                  r0 * I.ldx + c0);
             p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
             if constexpr (!GEN) {
                 p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
@@ -540,6 +591,10 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     const long long base = issued;   // rows of earlier passes (ring position)
     auto issue = [&]() {
         const int st = (int)(issued % S);
+        const long long dr = p_row - p_r0;
+        const char* p_c = p_c0 + dr * p_cstride;
+        const char* p_x = p_x0 + dr * p_xstride;
+        const char* p_xb = p_xb0 + dr * p_xstride;
         if (lane == 0) {
             refs[st].tile = p_tile;
             refs[st].row = (int)p_row;
@@ -560,10 +615,8 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             }
         }
         ++issued;
-        p_c += p_cstride;
-        p_x += p_xstride;
-        p_xb += p_xstride;
-        if (++p_row >= p_end) next_tile();
+        p_row += p_dir;
+        if (p_row == p_stop) next_tile();
     };
     next_tile();
     while (issued - base < S && p_tile < T) issue();
@@ -578,7 +631,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     double* c_rowpart = nullptr;
     long long j0 = 0;
     bool on = false, valid[4] = {false, false, false, false};
-    float qv[4] = {0.f, 0.f, 0.f, 0.f};
+    float qv[4] = {0.f, 0.f, 0.f, 0.f}, ql[4] = {0.f, 0.f, 0.f, 0.f};
     float tau = 0.f, w = 0.f;
     bool first = true;
     double cs[4] = {0.0, 0.0, 0.0, 0.0}, dx2 = 0.0;
@@ -646,7 +699,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             valid[e] = j0 + e < c_n;
-            qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+            split_dual(valid[e] ? q[j0 + e] : 0.0, qv[e], ql[e]);
         }
         tau = (float)Sc.tau;
         w = (float)(1.0 / (double)(Sc.k + 1));
@@ -753,18 +806,22 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
 #pragma unroll
             for (int e = 0; e < 4; ++e) { c[e] = GEN ? c[e] : 0.f; x[e] = 0.f; xb[e] = 0.f; }
         }
-        // Row duals are staged in shared memory per window of MAX_TILE_ROWS rows
+        // Row duals are staged in shared memory per window of PWIN rows
         // instead of one dependent global load per row.
-        const long long win = di / MAX_TILE_ROWS;
+        const long long win = di / PWIN;
         if (win != c_win) {
-            const long long r0 = c_i0 + win * MAX_TILE_ROWS;
-            const long long r1 = min(r0 + (long long)MAX_TILE_ROWS, c_i1);
+            const long long r0 = c_i0 + win * PWIN;
+            const long long r1 = min(r0 + (long long)PWIN, c_i1);
             __syncwarp();
-            for (long long r = r0 + lane; r < r1; r += 32) pbuf[r - r0] = (float)c_p[r];
+            for (long long r = r0 + lane; r < r1; r += 32) {
+                float h, l;
+                split_dual(c_p[r], h, l);
+                pbuf[r - r0] = make_float2(h, l);
+            }
             __syncwarp();
             c_win = win;
         }
-        const float pv = pbuf[di - win * MAX_TILE_ROWS];
+        const float2 pv = pbuf[di - win * PWIN];
         // The stage has been read: release it to the producer.
         __syncwarp();
         ++consumed;
@@ -773,14 +830,14 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
         float xn[4], xbn[4], rs = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float R = (c[e] - pv) - qv[e];
+            const float R = reduced_cost(c[e], pv.x, pv.y, qv[e], ql[e], CP);
             float v = x[e] - tau * R;
             v = v > 0.f ? v : 0.f;
             v = valid[e] ? v : 0.f;
             const float d = v - x[e];
             dxa += d * d;
-            rs += v;
-            csa[e] += v;
+            rs += d;                                              // row / column sums of X+ - X
+            csa[e] += d;
             xn[e] = v;
             xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
         }
@@ -821,10 +878,10 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
     return !failed;
 }
 
-template <typename TC, int S>
+template <typename TC, int S, bool CP>
 __global__ void __launch_bounds__(TWARPS * 32, 2)
 k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
-            unsigned* wctr, int wc) {
+            unsigned* wctr, int wc, int dir_xor) {
     // Setup that does not depend on the preceding kernel (tile count and maps
     // are host-written; shared-memory barriers are local) runs before the wait.
     const int T = *Tp;
@@ -835,7 +892,7 @@ k_pass_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, co
     prefetch_first_tile(insts, tmap, T);
     pdl_enter();
     reset_other_counters(wctr, wc);
-    pass_row_run<TC, S>(insts, tmap, T, &wctr[wc], P, lane);
+    pass_row_run<TC, S, CP>(insts, tmap, T, &wctr[wc], P, lane, dir_xor);
     pdl_release();
 }
 
@@ -856,7 +913,7 @@ struct GroupRef {
 };
 
 template <int R, int S>
-__host__ __device__ constexpr int warp_smem_bytes_g() { return S * R * STAGE_BYTES + S * 8 + S * 16 + MAX_TILE_ROWS * 4; }
+__host__ __device__ constexpr int warp_smem_bytes_g() { return S * R * STAGE_BYTES + S * 8 + S * 16 + PWIN * 8; }
 
 // Sum v[r] over the 32 lanes for R = 4 rows with 6 shuffles.  The total of
 // row r ends in lanes 8r .. 8r+7.
@@ -877,10 +934,10 @@ __device__ __forceinline__ float rows4_sum(const float (&v)[4], int lane) {
 
 }  // namespace bulk
 
-template <typename TC, int S>
-__global__ void __launch_bounds__(TWARPS * 32)
+template <typename TC, int S, bool CP>
+__global__ void __launch_bounds__(TWARPS * 32, 2)
 k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
-             unsigned* wctr, int wc) {
+             unsigned* wctr, int wc, int dir_xor) {
     using namespace bulk;
     constexpr int R = 4;
     const int T = *Tp;   // host-written: read before the wait (see k_pass_bulk)
@@ -892,7 +949,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     unsigned char* wbase = dsm + warp * warp_smem_bytes_g<R, S>();
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + S * R * STAGE_BYTES);
     GroupRef* refs = reinterpret_cast<GroupRef*>(wbase + S * R * STAGE_BYTES + S * 8);
-    float* pbuf = reinterpret_cast<float*>(wbase + S * R * STAGE_BYTES + S * 24);
+    float2* pbuf = reinterpret_cast<float2*>(wbase + S * R * STAGE_BYTES + S * 24);
     const unsigned wbase_s = smem_u32(wbase);
     const unsigned bars_s = smem_u32(bars);
     if (lane == 0) {
@@ -905,12 +962,13 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     constexpr int DA = GEN ? DM : 1;                     // coordinate array size
     constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
 
-    // ---- producer ----
+    // ---- producer: a tile's R-row groups, walked in either order (pass_reversed) ----
     int p_tile = T;
-    long long p_row = 0, p_end = 0, p_last_ragged = -1;
-    const char* p_c = nullptr;
-    const char* p_x = nullptr;
-    const char* p_xb = nullptr;
+    long long p_r0 = 0, p_r1 = 0, p_G = 0, p_gi = 0, p_last_ragged = -1;
+    bool p_rev = false;
+    const char* p_c0 = nullptr;         // C, X, Xbar at the tile's first row
+    const char* p_x0 = nullptr;
+    const char* p_xb0 = nullptr;
     long long p_cstride = 0, p_xstride = 0;
     unsigned p_cbytes = 0, p_xbytes = 0;
     bool p_first = true;
@@ -926,17 +984,20 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
             const long long c0 = (long long)strip * STRIP;
             const long long ncols = min((long long)STRIP, I.n - c0);
-            p_row = (long long)chunk * I.tile_rows;
-            p_end = min(p_row + (long long)I.tile_rows, I.m);
+            p_r0 = (long long)chunk * I.tile_rows;
+            p_r1 = min(p_r0 + (long long)I.tile_rows, I.m);
+            p_G = (p_r1 - p_r0 + R - 1) / R;
+            p_gi = 0;
+            p_rev = pass_reversed(Sc, dir_xor);
             p_xstride = I.ldx * 4;
             if constexpr (!GEN) {
                 p_cstride = I.ldc * (long long)sizeof(TC);
-                p_c = reinterpret_cast<const char*>(I.C) + p_row * p_cstride + c0 * (long long)sizeof(TC);
+                p_c0 = reinterpret_cast<const char*>(I.C) + p_r0 * p_cstride + c0 * (long long)sizeof(TC);
             }
-            p_x = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
-                                                p_row * I.ldx + c0);
-            p_xb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
-                                                 p_row * I.ldx + c0);
+            p_x0 = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.cur * I.xslot +
+                                                 p_r0 * I.ldx + c0);
+            p_xb0 = reinterpret_cast<const char*>(reinterpret_cast<const float*>(I.X) + (long long)Sc.bar * I.xslot +
+                                                  p_r0 * I.ldx + c0);
             p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
             if constexpr (!GEN) {
                 p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
@@ -949,7 +1010,12 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     long long issued = 0, consumed = 0;   // in groups
     auto issue = [&]() {
         const int st = (int)(issued % S);
-        const int g = (int)min((long long)R, p_end - p_row);
+        const long long p_row = p_r0 + R * (p_rev ? p_G - 1 - p_gi : p_gi);   // the group's first row
+        const int g = (int)min((long long)R, p_r1 - p_row);
+        const long long dr = p_row - p_r0;
+        const char* p_c = p_c0 + dr * p_cstride;
+        const char* p_x = p_x0 + dr * p_xstride;
+        const char* p_xb = p_xb0 + dr * p_xstride;
         const unsigned bar = bars_s + 8 * st;
         const unsigned dst = wbase_s + st * (R * STAGE_BYTES);
         // The C copy of the last matrix row of a ragged strip is skipped (lanes load it).
@@ -979,11 +1045,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             }
         }
         ++issued;
-        p_c += g * p_cstride;
-        p_x += g * p_xstride;
-        p_xb += g * p_xstride;
-        p_row += g;
-        if (p_row >= p_end) next_tile();
+        if (++p_gi == p_G) next_tile();
     };
     next_tile();
     while (issued < S && p_tile < T) issue();
@@ -998,7 +1060,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
     double* c_rowpart = nullptr;
     long long j0 = 0;
     bool on = false, valid[4] = {false, false, false, false};
-    float qv[4] = {0.f, 0.f, 0.f, 0.f};
+    float qv[4] = {0.f, 0.f, 0.f, 0.f}, ql[4] = {0.f, 0.f, 0.f, 0.f};
     float tau = 0.f, w = 0.f;
     bool first = true;
     double cs[4] = {0.0, 0.0, 0.0, 0.0}, dx2 = 0.0;
@@ -1065,7 +1127,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             valid[e] = j0 + e < c_n;
-            qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+            split_dual(valid[e] ? q[j0 + e] : 0.0, qv[e], ql[e]);
         }
         tau = (float)Sc.tau;
         w = (float)(1.0 / (double)(Sc.k + 1));
@@ -1093,17 +1155,21 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             const long long i = ref.row0 + r;
             const long long di = i - c_i0;
             const unsigned char* rst = stage + r * STAGE_BYTES;
-            // Row duals staged per window of MAX_TILE_ROWS rows.
-            const long long win = di / MAX_TILE_ROWS;
+            // Row duals staged per window of PWIN rows.
+            const long long win = di / PWIN;
             if (win != c_win) {
-                const long long r0 = c_i0 + win * MAX_TILE_ROWS;
-                const long long r1 = min(r0 + (long long)MAX_TILE_ROWS, c_i1);
+                const long long r0 = c_i0 + win * PWIN;
+                const long long r1 = min(r0 + (long long)PWIN, c_i1);
                 __syncwarp();
-                for (long long rr = r0 + lane; rr < r1; rr += 32) pbuf[rr - r0] = (float)c_p[rr];
+                for (long long rr = r0 + lane; rr < r1; rr += 32) {
+                    float h, l;
+                    split_dual(c_p[rr], h, l);
+                    pbuf[rr - r0] = make_float2(h, l);
+                }
                 __syncwarp();
                 c_win = win;
             }
-            const float pv = pbuf[di - win * MAX_TILE_ROWS];
+            const float2 pv = pbuf[di - win * PWIN];
             float c[4], x[4], xb[4];
             if constexpr (GEN) {
                 // Same operations as gen_cost; every lane takes part in the shuffles.
@@ -1186,14 +1252,14 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             float xn[4], xbn[4], rs = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float Rc = (c[e] - pv) - qv[e];
+                const float Rc = reduced_cost(c[e], pv.x, pv.y, qv[e], ql[e], CP);
                 float v = x[e] - tau * Rc;
                 v = v > 0.f ? v : 0.f;
                 v = valid[e] ? v : 0.f;
                 const float d = v - x[e];
                 dxa += d * d;
-                rs += v;
-                csa[e] += v;
+                rs += d;                                          // row / column sums of X+ - X
+                csa[e] += d;
                 xn[e] = v;
                 xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
             }
@@ -1383,14 +1449,17 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
         for (int g2 = 0; g2 < VG; ++g2) t += sgrp[g2 * 32 + lane];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;   // ||dy||^2, dy^T A dx, ||dX||^2 (this tile's slice)
         if (row || col) {
+            // t: this row's or column's sum of X+ - X (the pass sums the change
+            // itself, so the step-size term dy^T A dX below is not a difference
+            // of two nearly equal sums); (2X+ - X) 1 = r + 2t, X+ 1 = r + t.
             const double w = 1.0 / (double)(k + 1);
-            const double yn = y + sigma * (b - (2.0 * t - r));
+            const double yn = y + sigma * (b - (r + 2.0 * t));
             Vn[yo] = yn;
-            Vn[so] = t;
+            Vn[so] = r + t;
             Vbn[yo] = k == 0 ? yn : ybar + w * (yn - ybar);
             const double dy = yn - y;
             a0 = dy * dy;
-            a1 = dy * (t - r);
+            a1 = dy * t;
         }
         {
             const long long T = I.ntiles;
@@ -1481,6 +1550,9 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
     const double* pb = slot_v(I, S.bar);
     const double* qb = pb + m;
 
+    // The check's dual residual [p + q - C]^+ takes the plain reduced cost:
+    // its FP32 rounding (of the size of p and q) is far below ||C||_F, the
+    // scale this term is measured against.
     A qv[4], qbv[4];
     bool valid[4];
 #pragma unroll
@@ -1491,7 +1563,9 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
     }
     double acc[TP] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // cxc, rd2c, cxb, rd2b, dXac, dXab
     double cs[4] = {0.0, 0.0, 0.0, 0.0};
+    double cs2[4] = {0.0, 0.0, 0.0, 0.0};   // check: exact column sums of the current plan
     double* rowpart = I.rowpart + (long long)strip * m;
+    double* rowpart2 = I.rowpart2 + (long long)strip * m;
 
     for (long long ib = i0; ib < i1; ib += KU) {
         A c[KU][4], x[KU][4], xb[KU][4], xa[KU][4], pv[KU], pbv[KU];
@@ -1515,12 +1589,12 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
             }
         }
         A t[TP] = {A(0), A(0), A(0), A(0), A(0), A(0)};
-        A csa[4] = {A(0), A(0), A(0), A(0)};
+        A csa[4] = {A(0), A(0), A(0), A(0)}, csa2[4] = {A(0), A(0), A(0), A(0)};
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
             const long long i = ib + u;
             const bool rv = i < i1;
-            A rs = A(0);
+            A rs = A(0), rs2 = A(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (!valid[e] || !rv) continue;
@@ -1540,21 +1614,35 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
                 const A sv = init ? x[u][e] : xb[u][e];
                 rs += sv;
                 csa[e] += sv;
+                rs2 += x[u][e];
+                csa2[e] += x[u][e];
             }
             if (sums) {
                 rs = warp_sum(rs);
                 if (rv && lane == 0) rowpart[i] = (double)rs;
             }
+            if (!init) {
+                rs2 = warp_sum(rs2);
+                if (rv && lane == 0) rowpart2[i] = (double)rs2;
+            }
         }
 #pragma unroll
         for (int k = 0; k < TP; ++k) acc[k] += (double)t[k];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) cs[e] += (double)csa[e];
+        for (int e = 0; e < 4; ++e) {
+            cs[e] += (double)csa[e];
+            cs2[e] += (double)csa2[e];
+        }
     }
     if (sums && on) {
         double* cp = I.colpart + (long long)chunk * ldx + j0;
         reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0], cs[1]);
         reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2], cs[3]);
+    }
+    if (!init && on) {
+        double* cp = I.colpart2 + (long long)chunk * ldx + j0;
+        reinterpret_cast<double2*>(cp)[0] = make_double2(cs2[0], cs2[1]);
+        reinterpret_cast<double2*>(cp)[1] = make_double2(cs2[2], cs2[3]);
     }
 #pragma unroll
     for (int k = 0; k < TP; ++k) acc[k] = warp_sum(acc[k]);
@@ -1729,10 +1817,14 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
     const bool avg = !init && S->k > 0;
     const bool row = e < m, col = !row && e < m + n;
     const long long idx = row ? e : e - m;          // i or j
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;
     if (init || avg) {   // uniform across the block
         s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx, row || col,
                       sgrp);
+    }
+    if (!init) {   // the current plan's exact sums (the passes carry them forward by sums of changes)
+        s2 = group_sum(row ? I.rowpart2 : I.colpart2, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
+                       row || col, sgrp);
     }
     double* Vc = slot_v(I, S->cur);
     double* Vb = slot_v(I, S->bar);
@@ -1754,7 +1846,8 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
             a[4] = b * b;
             a[5] = (b >= 0.0 && isfinite(b)) ? 0.0 : 1.0;
         } else {
-            const double r = Vc[so];
+            const double r = s2;
+            Vc[so] = s2;
             a[0] = (r - b) * (r - b);
             a[2] = b * y;
             const double ya = Va[yo];
@@ -1862,7 +1955,7 @@ __device__ bool grid_barrier(GridBar* gb, unsigned nblocks, int* s_ok) {
     return *s_ok != 0;
 }
 
-template <typename TC>
+template <typename TC, bool CP>
 __global__ void __launch_bounds__(TWARPS * 32, 2)
 k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
              const TileRef* __restrict__ vmap, const int* __restrict__ NVp, unsigned* wctr, GridBar* gb, int npass,
@@ -1882,7 +1975,7 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         // Every CTA reads the status after the same barrier: a uniform exit.
         if (*(volatile int*)&S0->status != ST_RUNNING) break;
         const int qc = (s & 1) ? wc_b : wc_a;
-        pass_row_run<TC, BULK_ROW_S>(insts, tmap, T, &wctr[qc], P, lane);
+        pass_row_run<TC, BULK_ROW_S, CP>(insts, tmap, T, &wctr[qc], P, lane, 0);
         ok = grid_barrier(gb, G, &s_ok);
         if (!ok) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&wctr[qc], 0u);   // ready for pass s + 2
@@ -1982,8 +2075,9 @@ constexpr int bulk_smem() { return TWARPS * bulk::warp_smem_bytes<BULK_S>(); }
 constexpr int GROUP_S = 2;   // stages of 4 rows: 8 rows in flight per warp
 constexpr int group_smem() { return TWARPS * bulk::warp_smem_bytes_g<4, GROUP_S>(); }
 
-int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
-                const LaunchCfg& cfg, void* stream, int wc_override) {
+template <bool CP>
+static int launch_pass_t(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                         const LaunchCfg& cfg, void* stream, int wc_override, int dir_xor) {
     const cudaStream_t st = (cudaStream_t)stream;
     const int wc = wc_override >= 0 ? wc_override : wc_index(WC_PASS, ttype);
     const bool pdl = cfg.pdl != 0;
@@ -1993,41 +2087,47 @@ int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int
         // one for up to 4 coordinates), or the register pipeline when the
         // bulk kernels are switched off.
         if (cfg.pass_bulk == 2 && cfg.gen_dims <= 4)
-            return launch_k(pdl, k_pass_group<GenC4, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st,
-                            d_insts, d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass_group<GenC4, GROUP_S, CP>, (unsigned)cfg.group_blocks, th, group_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc, dir_xor);
         if (cfg.pass_bulk && cfg.gen_dims <= 4)
-            return launch_k(pdl, k_pass_bulk<GenC4, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
-                            d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass_bulk<GenC4, BULK_S, CP>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                            d_tmap, T, wctr, wc, dir_xor);
         if (cfg.pass_bulk)
-            return launch_k(pdl, k_pass_bulk<GenC8, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
-                            d_tmap, T, wctr, wc);
-        return launch_k(pdl, k_pass<GenC8, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass_bulk<GenC8, BULK_S, CP>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                            d_tmap, T, wctr, wc, dir_xor);
+        return launch_k(pdl, k_pass<GenC8, float, 2, CP>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc, dir_xor);
     }
     if (cfg.pass_bulk == 2 && ttype != TT_F64) {
         if (ttype == TT_BF16)
-            return launch_k(pdl, k_pass_group<unsigned short, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st,
-                            d_insts, d_tmap, T, wctr, wc);
-        return launch_k(pdl, k_pass_group<float, GROUP_S>, (unsigned)cfg.group_blocks, th, group_smem(), st, d_insts,
-                        d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass_group<unsigned short, GROUP_S, CP>, (unsigned)cfg.group_blocks, th, group_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc, dir_xor);
+        return launch_k(pdl, k_pass_group<float, GROUP_S, CP>, (unsigned)cfg.group_blocks, th, group_smem(), st, d_insts,
+                        d_tmap, T, wctr, wc, dir_xor);
     }
     if (cfg.pass_bulk && ttype != TT_F64) {
         if (ttype == TT_BF16)
-            return launch_k(pdl, k_pass_bulk<unsigned short, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st,
-                            d_insts, d_tmap, T, wctr, wc);
-        return launch_k(pdl, k_pass_bulk<float, BULK_S>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
-                        d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass_bulk<unsigned short, BULK_S, CP>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st,
+                            d_insts, d_tmap, T, wctr, wc, dir_xor);
+        return launch_k(pdl, k_pass_bulk<float, BULK_S, CP>, (unsigned)cfg.bulk_blocks, th, bulk_smem(), st, d_insts,
+                        d_tmap, T, wctr, wc, dir_xor);
     }
     if (ttype == TT_F64)
-        return launch_k(pdl, k_pass<double, double, 2>, (unsigned)cfg.tile_blocks_f64, th, 0, st, d_insts, d_tmap, T,
-                        wctr, wc);
+        return launch_k(pdl, k_pass<double, double, 2, CP>, (unsigned)cfg.tile_blocks_f64, th, 0, st, d_insts, d_tmap, T,
+                        wctr, wc, dir_xor);
     if (ttype == TT_BF16) {
         if (cfg.pass_u == 4)
-            return launch_k(pdl, k_pass<unsigned short, float, 4>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
-        return launch_k(pdl, k_pass<unsigned short, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+            return launch_k(pdl, k_pass<unsigned short, float, 4, CP>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc, dir_xor);
+        return launch_k(pdl, k_pass<unsigned short, float, 2, CP>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc, dir_xor);
     }
-    if (cfg.pass_u == 4) return launch_k(pdl, k_pass<float, float, 4>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
-    return launch_k(pdl, k_pass<float, float, 2>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc);
+    if (cfg.pass_u == 4) return launch_k(pdl, k_pass<float, float, 4, CP>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc, dir_xor);
+    return launch_k(pdl, k_pass<float, float, 2, CP>, tb, th, 0, st, d_insts, d_tmap, T, wctr, wc, dir_xor);
 }
+int launch_pass(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, unsigned* wctr,
+                const LaunchCfg& cfg, void* stream, int wc_override, int dir_xor) {
+    if (cfg.comp) return launch_pass_t<true>(ttype, d_insts, d_tmap, T, wctr, cfg, stream, wc_override, dir_xor);
+    return launch_pass_t<false>(ttype, d_insts, d_tmap, T, wctr, cfg, stream, wc_override, dir_xor);
+}
+
 int launch_dual(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr,
                 const LaunchCfg& cfg, void* stream, bool direct) {
     // nv_hint: an upper bound of the vector-tile count (one CTA each); with
@@ -2083,35 +2183,43 @@ static int occ(const void* fn, int threads) {
 }
 int occupancy_tile_blocks_per_sm(int ttype) {
     if (ttype == TT_F64) {
-        const int a = occ((const void*)k_pass<double, double, 2>, TWARPS * 32);
+        const int a = occ((const void*)k_pass<double, double, 2, true>, TWARPS * 32);
         const int b = occ((const void*)k_kkt<double, double>, TWARPS * 32);
         return a < b ? a : b;
     }
-    const int a = occ((const void*)k_pass<float, float, 2>, TWARPS * 32);
-    const int b = occ((const void*)k_kkt<float, float>, TWARPS * 32);
-    const int c = occ((const void*)k_pass<unsigned short, float, 4>, TWARPS * 32);
-    const int d = occ((const void*)k_kkt<unsigned short, float>, TWARPS * 32);
-    const int e = occ((const void*)k_pass<GenC8, float, 2>, TWARPS * 32);
-    const int g = occ((const void*)k_kkt<GenC8, float>, TWARPS * 32);
-    int r = a;
-    if (b < r) r = b;
-    if (c < r) r = c;
-    if (d < r) r = d;
-    if (e < r) r = e;
-    if (g < r) r = g;
+    const void* fns[] = {(const void*)k_pass<float, float, 2, true>,          (const void*)k_pass<float, float, 2, false>,
+                         (const void*)k_pass<unsigned short, float, 4, true>,  (const void*)k_pass<unsigned short, float, 4, false>,
+                         (const void*)k_pass<GenC8, float, 2, true>,           (const void*)k_pass<GenC8, float, 2, false>,
+                         (const void*)k_kkt<float, float>,                     (const void*)k_kkt<unsigned short, float>,
+                         (const void*)k_kkt<GenC8, float>};
+    int r = 1 << 20;
+    for (const void* f : fns) {
+        const int a = occ(f, TWARPS * 32);
+        if (a < r) r = a;
+    }
     return r;
 }
-int setup_coop_chunk() {
-    const int bytes = bulk_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_chunk_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_chunk_coop<unsigned short>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_chunk_coop<float>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chunk_coop<unsigned short>, TWARPS * 32, bytes);
-    const int r = a < b ? a : b;
+
+// Opt every instantiation of a kernel with dynamic shared memory into `bytes`;
+// returns minus the fewest CTAs per SM any of them holds, or a positive
+// cudaError_t code.
+static int setup_dyn(const void* const* fns, int nf, int bytes) {
+    int r = 1 << 20;
+    for (int i = 0; i < nf; ++i) {
+        const cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return (int)e;
+        int a = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fns[i], TWARPS * 32, bytes);
+        if (a < r) r = a;
+    }
     return -(r > 0 ? r : 1);
+}
+
+int setup_coop_chunk() {
+    const void* fns[] = {(const void*)k_chunk_coop<float, true>, (const void*)k_chunk_coop<float, false>,
+                         (const void*)k_chunk_coop<unsigned short, true>,
+                         (const void*)k_chunk_coop<unsigned short, false>};
+    return setup_dyn(fns, 4, bulk_smem());
 }
 
 int launch_chunk_coop(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const TileRef* d_vmap,
@@ -2129,50 +2237,33 @@ int launch_chunk_coop(int ttype, const Inst* d_insts, const TileRef* d_tmap, con
     const int wa = wc_index(WC_PASS, ttype), wb = wc_index(WC_AUX, ttype), wk = wc_index(WC_KKT, ttype);
     cudaError_t e;
     if (ttype == TT_BF16)
-        e = cudaLaunchKernelEx(&c, k_chunk_coop<unsigned short>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb, npass, wa,
-                               wb, wk);
+        e = cfg.comp ? cudaLaunchKernelEx(&c, k_chunk_coop<unsigned short, true>, d_insts, d_tmap, T, d_vmap, NV, wctr,
+                                          gb, npass, wa, wb, wk)
+                     : cudaLaunchKernelEx(&c, k_chunk_coop<unsigned short, false>, d_insts, d_tmap, T, d_vmap, NV, wctr,
+                                          gb, npass, wa, wb, wk);
     else
-        e = cudaLaunchKernelEx(&c, k_chunk_coop<float>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb, npass, wa, wb, wk);
+        e = cfg.comp ? cudaLaunchKernelEx(&c, k_chunk_coop<float, true>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb, npass,
+                                          wa, wb, wk)
+                     : cudaLaunchKernelEx(&c, k_chunk_coop<float, false>, d_insts, d_tmap, T, d_vmap, NV, wctr, gb,
+                                          npass, wa, wb, wk);
     return err(e);
 }
 
 int setup_group_pass() {
-    const int bytes = group_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_pass_group<float, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_pass_group<unsigned short, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_pass_group<GenC4, GROUP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    int a = 0, b = 0, c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_group<float, GROUP_S>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_group<unsigned short, GROUP_S>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass_group<GenC4, GROUP_S>, TWARPS * 32, bytes);
-    int r = a < b ? a : b;
-    if (c < r) r = c;
-    return -(r > 0 ? r : 1);
+    const void* fns[] = {(const void*)k_pass_group<float, GROUP_S, true>, (const void*)k_pass_group<float, GROUP_S, false>,
+                         (const void*)k_pass_group<unsigned short, GROUP_S, true>,
+                         (const void*)k_pass_group<unsigned short, GROUP_S, false>,
+                         (const void*)k_pass_group<GenC4, GROUP_S, true>, (const void*)k_pass_group<GenC4, GROUP_S, false>};
+    return setup_dyn(fns, 6, group_smem());
 }
 
 int setup_bulk_pass() {
-    const int bytes = bulk_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_pass_bulk<float, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_pass_bulk<unsigned short, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_pass_bulk<GenC4, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_pass_bulk<GenC8, BULK_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return (int)e;
-    int a = 0, b = 0, c = 0, d = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass_bulk<float, BULK_S>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_bulk<unsigned short, BULK_S>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass_bulk<GenC4, BULK_S>, TWARPS * 32, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_pass_bulk<GenC8, BULK_S>, TWARPS * 32, bytes);
-    int r = a < b ? a : b;
-    if (c < r) r = c;
-    if (d < r) r = d;
-    return -(r > 0 ? r : 1);   // negative: blocks per SM
+    const void* fns[] = {(const void*)k_pass_bulk<float, BULK_S, true>, (const void*)k_pass_bulk<float, BULK_S, false>,
+                         (const void*)k_pass_bulk<unsigned short, BULK_S, true>,
+                         (const void*)k_pass_bulk<unsigned short, BULK_S, false>,
+                         (const void*)k_pass_bulk<GenC4, BULK_S, true>, (const void*)k_pass_bulk<GenC4, BULK_S, false>,
+                         (const void*)k_pass_bulk<GenC8, BULK_S, true>, (const void*)k_pass_bulk<GenC8, BULK_S, false>};
+    return setup_dyn(fns, 8, bulk_smem());   // negative: blocks per SM
 }
 
 int occupancy_vec_blocks_per_sm() {

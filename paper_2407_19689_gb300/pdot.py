@@ -56,6 +56,7 @@ class Options(ctypes.Structure):
         ("chunk_checks", ctypes.c_int32),
         ("batch_active_bytes", ctypes.c_uint64),
         ("pass_kernel", ctypes.c_int32),
+        ("compensated_cost", ctypes.c_int32),
     ]
 
 
@@ -122,12 +123,23 @@ class PointsCostDesc(ctypes.Structure):
     ]
 
 
+class Start(ctypes.Structure):
+    """pdot_start: a starting point or a saved solver state (device pointers)."""
+    _fields_ = [
+        ("X0", ctypes.c_void_p),
+        ("p0", ctypes.c_void_p),
+        ("q0", ctypes.c_void_p),
+        ("state_in", ctypes.c_void_p),
+        ("state_out", ctypes.c_void_p),
+    ]
+
+
 # Every symbol include/pdot.h declares (checked by the CPU tests).
 DECLARED = [
     "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
-    "pdot_solve_host", "pdot_pdhg_steps", "pdot_kkt", "pdot_round", "pdot_batch_submit", "pdot_poll",
-    "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass", "pdot_round_noalloc",
-    "pdot_watchdog_selftest",
+    "pdot_solve_host", "pdot_solve_from", "pdot_state_bytes", "pdot_pdhg_steps", "pdot_kkt", "pdot_round",
+    "pdot_batch_submit", "pdot_poll", "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass",
+    "pdot_round_noalloc", "pdot_watchdog_selftest",
 ]
 
 _LIB = None
@@ -154,6 +166,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_destroy": (i32, [H]),
         "pdot_solve": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, vp, vp, vp, ctypes.POINTER(Result)]),
         "pdot_solve_host": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, vp, vp, vp, ctypes.POINTER(Result)]),
+        "pdot_solve_from": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, ctypes.POINTER(Start), vp, vp, vp,
+                                  ctypes.POINTER(Result)]),
+        "pdot_state_bytes": (i64, [i64, i64, i32]),
         "pdot_pdhg_steps": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i64, dbl, dbl, vp, vp, vp, vp, vp, vp]),
         "pdot_kkt": (i32, [H, i64, i64, vp, i32, i64, vp, vp, vp, vp, vp, ctypes.POINTER(KktParts)]),
         "pdot_round": (i32, [H, i64, i64, vp, vp, vp, vp]),
@@ -221,6 +236,17 @@ def pdot_solve_host(h, m, n, C, c_dtype, ldc, f, g, tol, X_out=0, p_out=0, q_out
     st = load().pdot_solve_host(h, m, n, C, c_dtype, ldc, f, g, tol, X_out or None, p_out or None,
                                 q_out or None, ctypes.byref(r))
     return st, r
+
+
+def pdot_solve_from(h, m, n, C, c_dtype, ldc, f, g, tol, start: Start | None, X_out=0, p_out=0, q_out=0):
+    r = Result()
+    st = load().pdot_solve_from(h, m, n, C, c_dtype, ldc, f, g, tol, ctypes.byref(start) if start else None,
+                                X_out or None, p_out or None, q_out or None, ctypes.byref(r))
+    return st, r
+
+
+def pdot_state_bytes(m, n, x_dtype) -> int:
+    return load().pdot_state_bytes(m, n, x_dtype)
 
 
 def pdot_pdhg_steps(h, m, n, C, c_dtype, ldc, f, g, k, eta, omega, X, p, q, Xbar=0, pbar=0, qbar=0) -> int:
@@ -417,7 +443,14 @@ class Solver:
         g = self._cuda(g, torch.float64)
         return c, f, g
 
-    def solve(self, C, f, g, tol: float | None = None, want_plan: bool = True) -> Solution:
+    def state_bytes(self, m: int, n: int) -> int:
+        return pdot_state_bytes(m, n, self.options.x_dtype)
+
+    def solve(self, C, f, g, tol: float | None = None, want_plan: bool = True, X0=None, p0=None, q0=None,
+              state_in=None, state_out=None) -> Solution:
+        """Solve from the origin, from a starting point (X0, p0, q0; a missing
+        part is 0) or from a saved state (state_in: a uint8 CUDA tensor a
+        previous call filled as state_out, of state_bytes(m, n) bytes)."""
         torch = _torch()
         c, f, g = self._prep(C, f, g)
         m, n = c.m, c.n
@@ -425,9 +458,29 @@ class Solver:
         X = torch.empty((m, n), dtype=xt, device=f.device) if want_plan else None
         p = torch.empty(m, dtype=torch.float64, device=f.device)
         q = torch.empty(n, dtype=torch.float64, device=f.device)
-        st, r = pdot_solve(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(),
-                           tol if tol is not None else self.options.tol, X.data_ptr() if X is not None else 0,
-                           p.data_ptr(), q.data_ptr())
+        tol = tol if tol is not None else self.options.tol
+        if X0 is None and p0 is None and q0 is None and state_in is None and state_out is None:
+            st, r = pdot_solve(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(), tol,
+                               X.data_ptr() if X is not None else 0, p.data_ptr(), q.data_ptr())
+        else:
+            keep = []
+
+            def dev(t, dtype):
+                if t is None:
+                    return None
+                t = self._cuda(t, dtype)
+                keep.append(t)
+                return t.data_ptr()
+
+            for blob in (state_in, state_out):
+                if blob is not None and (not isinstance(blob, torch.Tensor) or not blob.is_cuda or
+                                         blob.numel() * blob.element_size() < self.state_bytes(m, n)):
+                    raise ValueError(f"state blobs must be CUDA tensors of at least {self.state_bytes(m, n)} bytes")
+            start = Start(X0=dev(X0, xt), p0=dev(p0, torch.float64), q0=dev(q0, torch.float64),
+                          state_in=state_in.data_ptr() if state_in is not None else None,
+                          state_out=state_out.data_ptr() if state_out is not None else None)
+            st, r = pdot_solve_from(self.h, m, n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(), tol, start,
+                                    X.data_ptr() if X is not None else 0, p.data_ptr(), q.data_ptr())
         _check(self.h, st, allow=(OK, MAX_ITER, TIMEOUT, ERR_NUMERIC))
         return Solution(r.as_dict(), st, X, p, q)
 

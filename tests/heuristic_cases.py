@@ -87,3 +87,39 @@ def restart_condition_case(ora, which):
         opts = dict(base, beta_suff=0.0, beta_nec=0.9)
     _, after = check_candidates(ora, ins, K, eta, 1, start=seq[j - 1][0])
     return ins, opts, j, after[0][0]
+
+
+# One-pass cases of the step-size rule (reading C6), derived by hand.  With
+# m = n = 1 (or m = 2, n = 1) one Algorithm 2 step is a handful of scalar
+# operations, so eta_bar, the accept/reject decision and the next step size
+# follow from the rule's statement:
+#   eta_bar = (omega ||dX||^2 + ||(dp, dq)||^2 / omega) / (2 |dp^T dX 1 + dq^T dX^T 1|),
+#   accept iff eta <= eta_bar,  eta' = min((1 - t^-0.3) eta_bar, (1 + t^-0.6) eta),
+# t = 2 + (iterations accepted so far); eta' is used next either way.  Each
+# case: data, starting point, (eta0, omega0), and the expected (iters,
+# rejected), final eta and final point after one pass.
+STEP_RULE_CASES = [
+    # "reject": C = 1, f = g = 1, start X = 5/2, p = q = 0, eta = omega = 1.
+    # X+ = 5/2 - (1 - 0 - 0) = 3/2; (2X+ - X) 1 = 1/2, so p+ = q+ = 1 - 1/2 = 1/2.
+    # dX = -1, dp = dq = 1/2: ||dX||^2 = 1, ||dy||^2 = 1/2, dy^T A dx = -1,
+    # eta_bar = (1 + 1/2) / 2 = 3/4 < eta: rejected, the state is kept,
+    # eta' = min((1 - 2^-0.3) 3/4, (1 + 2^-0.6) 1) = (1 - 2^-0.3) 3/4.
+    dict(name="reject", C=[[1.0]], f=[1.0], g=[1.0], X0=[[2.5]], p0=[0.0], q0=[0.0], eta0=1.0, omega0=1.0,
+         iters=0, rejected=1, eta=0.75 * (1 - 2 ** -0.3), X=[[2.5]], p=[0.0], q=[0.0]),
+    # "accept, omega = 2": same data, start X = 5/2, p = q = 0, eta = 1/2 (tau = 1/4, sigma = 1).
+    # X+ = 5/2 - 1/4 = 9/4; (2X+ - X) 1 = 2, so p+ = q+ = 1 - 2 = -1.
+    # dX = -1/4, dp = dq = -1: omega ||dX||^2 = 1/8, ||dy||^2 / omega = 1, dy^T A dx = 1/2,
+    # eta_bar = (1/8 + 1) / 1 = 9/8 >= eta: accepted, eta' = min((1 - 2^-0.3) 9/8, (1 + 2^-0.6) / 2)
+    # = (1 - 2^-0.3) 9/8.  (omega on the other two terms would give eta_bar = 4 + 1/32.)
+    dict(name="accept_omega2", C=[[1.0]], f=[1.0], g=[1.0], X0=[[2.5]], p0=[0.0], q0=[0.0], eta0=0.5, omega0=2.0,
+         iters=1, rejected=0, eta=1.125 * (1 - 2 ** -0.3), X=[[2.25]], p=[-1.0], q=[-1.0]),
+    # "two sources": m = 2, n = 1, C = [1; 0], f = [1/2; 1/2], g = 1, start X = [1; 1], p = q = 0,
+    # eta = omega = 1.  X+ = [max(0, 1 - 1); max(0, 1 - 0)] = [0; 1]; 2X+ - X = [-1; 1] has row sums
+    # [-1; 1] and column sum 0, so p+ = [3/2; -1/2], q+ = 1.  dX = [-1; 0], dp = [3/2; -1/2], dq = 1:
+    # ||dX||^2 = 1, ||dy||^2 = 9/4 + 1/4 + 1 = 7/2, dy^T A dx = (3/2)(-1) + (-1/2)(0) + (1)(-1) = -5/2,
+    # eta_bar = (1 + 7/2) / 5 = 9/10 < eta: rejected, eta' = (1 - 2^-0.3) 9/10.
+    # (Without the column part dq^T dX^T 1, eta_bar would be 3/2: accepted.)
+    dict(name="two_sources", C=[[1.0], [0.0]], f=[0.5, 0.5], g=[1.0], X0=[[1.0], [1.0]], p0=[0.0, 0.0], q0=[0.0],
+         eta0=1.0, omega0=1.0, iters=0, rejected=1, eta=0.9 * (1 - 2 ** -0.3), X=[[1.0], [1.0]], p=[0.0, 0.0],
+         q=[0.0]),
+]

@@ -50,7 +50,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 @pytest.mark.parametrize("cname,pyname", [("pdot_options", "Options"), ("pdot_result", "Result"),
                                           ("pdot_kkt_parts", "KktParts"), ("pdot_request", "Request"),
-                                          ("pdot_points_cost", "PointsCostDesc")])
+                                          ("pdot_points_cost", "PointsCostDesc"), ("pdot_start", "Start")])
 def test_ctypes_structs_follow_header(cname, pyname):
     from paper_2407_19689_gb300 import pdot
     py = [f for f, _ in getattr(pdot, pyname)._fields_]
@@ -96,3 +96,19 @@ def test_unknown_solver_option_is_rejected_before_any_cuda_call():
     from paper_2407_19689_gb300 import pdot
     with pytest.raises(TypeError, match="beta_artt"):
         pdot.Solver(device=0, beta_artt=0.5)
+
+
+def test_state_bytes_needs_no_gpu(lib):
+    """pdot_state_bytes: a 1 KB header, then three plans of m x ldx (ldx = n
+    rounded up to 4) and three vector sets of 2(m + n) doubles, each piece
+    256-byte aligned; 0 for invalid arguments."""
+    from paper_2407_19689_gb300 import pdot
+
+    def al(b):
+        return (b + 255) // 256 * 256
+
+    for m, n, xt, xs in [(300, 517, pdot.F32, 4), (1, 1, pdot.F64, 8), (4096, 4096, pdot.F32, 4)]:
+        ldx = (n + 3) // 4 * 4
+        assert pdot.pdot_state_bytes(m, n, xt) == 1024 + 3 * al(m * ldx * xs) + 3 * al(16 * (m + n))
+    assert pdot.pdot_state_bytes(0, 5, pdot.F32) == 0
+    assert pdot.pdot_state_bytes(5, 5, pdot.BF16) == 0

@@ -1,5 +1,6 @@
 """CPU tests of host-side logic: the replica aggregation of bench.py across
 ranks (two gloo processes), and the seeded workload generators."""
+import json
 import math
 import os
 import socket
@@ -235,3 +236,13 @@ def test_reference_arm_runs_on_rank_zero_only():
                           "--gpus", "2", "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
                          timeout=300, cwd=root, env=env)
     assert out.returncode == 0 and out.stdout.strip() == "", out.stderr[-2000:]
+
+
+def test_oracle_objective_record():
+    """bench.py reports the headline objective's relative error against the
+    FP64 oracle's own objective on the same workload, read from the committed
+    record (written by oracle/reference_counts.py); None where no record exists."""
+    import bench
+    rec = json.load(open(os.path.join(os.path.dirname(bench.TRAFFIC), "..", "oracle", "reference_counts.json")))
+    assert bench.oracle_objective(64, 1e-6) == rec["grid64"]["1e-06"]["primal_obj"]
+    assert bench.oracle_objective(64, 1e-5) is None and bench.oracle_objective(7, 1e-6) is None

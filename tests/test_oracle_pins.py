@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2407_19689_gb300 import instances as I
-from heuristic_cases import restart_condition_case, step_rule_from_origin_case
+from heuristic_cases import STEP_RULE_CASES, restart_condition_case, step_rule_from_origin_case
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ot_closed_forms.txt")
 
@@ -455,43 +455,19 @@ def _few_passes(ora, C, f, g, X0, p0, q0, eta0, omega0, passes=1):
     return ora.solve(arr(C), arr(f), arr(g), opts, X0=arr(X0), p0=arr(p0), q0=arr(q0))
 
 
-def test_step_rule_rejects_a_step_beyond_eta_bar(ora):
-    """1 x 1, C = 1, f = g = 1, start X = 5/2, p = q = 0, eta = omega = 1.
-    X+ = 5/2 - (1 - 0 - 0) = 3/2; (2X+ - X) 1 = 1/2, so p+ = q+ = 1 - 1/2 = 1/2.
-    dX = -1, dp = dq = 1/2: ||dX||^2 = 1, ||dy||^2 = 1/2, dy^T A dx = -1, so
-    eta_bar = (1 + 1/2) / 2 = 3/4 < eta: rejected, the state is kept, and
-    eta' = min((1 - 2^-0.3) 3/4, (1 + 2^-0.6) 1) = (1 - 2^-0.3) 3/4."""
-    r = _few_passes(ora, [[1.0]], [1.0], [1.0], [[2.5]], [0.0], [0.0], 1.0, 1.0)
-    assert (r.passes, r.iters, r.rejected) == (1, 0, 1)
-    assert r.X[0, 0] == 2.5 and r.p[0] == 0.0 and r.q[0] == 0.0
-    assert abs(r.eta - 0.75 * (1 - 2 ** -0.3)) <= 1e-15
-
-
-def test_step_rule_accepts_and_weights_by_omega(ora):
-    """Same data, start X = 5/2, p = q = 0, eta = 1/2, omega = 2 (tau = 1/4,
-    sigma = 1).  X+ = 5/2 - 1/4 = 9/4; (2X+ - X) 1 = 2, so p+ = q+ = 1 - 2 = -1.
-    dX = -1/4, dp = dq = -1: omega ||dX||^2 = 1/8, ||dy||^2 / omega = 1 and
-    dy^T A dx = 1/2, so eta_bar = (1/8 + 1) / 1 = 9/8 >= eta: accepted, and
-    eta' = min((1 - 2^-0.3) 9/8, (1 + 2^-0.6) / 2) = (1 - 2^-0.3) 9/8.
-    (omega on the other two terms would give eta_bar = 4 + 1/32.)"""
-    r = _few_passes(ora, [[1.0]], [1.0], [1.0], [[2.5]], [0.0], [0.0], 0.5, 2.0)
-    assert (r.passes, r.iters, r.rejected) == (1, 1, 0)
-    assert r.X[0, 0] == 2.25 and r.p[0] == -1.0 and r.q[0] == -1.0
-    assert abs(r.eta - 1.125 * (1 - 2 ** -0.3)) <= 1e-15
-
-
-def test_step_rule_two_sources_one_target(ora):
-    """m = 2, n = 1: C = [1; 0], f = [1/2; 1/2], g = 1, start X = [1; 1],
-    p = 0, q = 0, eta = omega = 1.  X+ = [max(0, 1 - 1); max(0, 1 - 0)] = [0; 1];
-    2X+ - X = [-1; 1] has row sums [-1; 1] and column sum 0, so
-    p+ = [1/2 + 1; 1/2 - 1] = [3/2; -1/2] and q+ = 1 - 0 = 1.
-    dX = [-1; 0], dp = [3/2; -1/2], dq = 1: ||dX||^2 = 1,
-    ||dy||^2 = 9/4 + 1/4 + 1 = 7/2, dy^T A dx = (3/2)(-1) + (-1/2)(0) + (1)(-1) = -5/2,
-    eta_bar = (1 + 7/2) / 5 = 9/10 < eta: rejected, eta' = (1 - 2^-0.3) 9/10.
-    (Without the column part dq^T dX^T 1, eta_bar would be 3/2: accepted.)"""
-    r = _few_passes(ora, [[1.0], [0.0]], [0.5, 0.5], [1.0], [[1.0], [1.0]], [0.0, 0.0], [0.0], 1.0, 1.0)
-    assert (r.passes, r.iters, r.rejected) == (1, 0, 1)
-    assert abs(r.eta - 0.9 * (1 - 2 ** -0.3)) <= 1e-15
+@pytest.mark.parametrize("case", STEP_RULE_CASES, ids=lambda c: c["name"])
+def test_step_rule_one_pass_by_hand(ora, case):
+    """One pass of the adaptive step-size rule on a 1 x 1 or 2 x 1 instance
+    whose eta_bar and decision are derived by hand (tests/heuristic_cases.py):
+    a rejection that keeps the state, an acceptance with omega = 2 (tests where
+    omega enters eta_bar), and a rejection that needs the column part of
+    dy^T A dx and of ||dy||^2."""
+    r = _few_passes(ora, case["C"], case["f"], case["g"], case["X0"], case["p0"], case["q0"], case["eta0"],
+                    case["omega0"])
+    assert (r.passes, r.iters, r.rejected) == (1, case["iters"], case["rejected"])
+    assert abs(r.eta - case["eta"]) <= 1e-15
+    assert np.array_equal(r.X, np.array(case["X"])) and np.array_equal(r.p, np.array(case["p"]))
+    assert np.array_equal(r.q, np.array(case["q"]))
 
 
 def test_step_rule_grows_the_step_while_the_plan_does_not_move(ora):
