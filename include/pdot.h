@@ -128,9 +128,12 @@ typedef struct {
     int32_t compensated_cost;      /* FP32 plans (reading C9): 1 = the reduced cost C - p - q is formed
                                       from the FP64 duals split into FP32 hi/lo pairs, with the rounding
                                       error of C - p_hi recovered exactly (TwoSum), so its error is
-                                      relative to itself rather than to p and q (fewer passes at tight
-                                      tolerances; about 6 % more time per pass at 4096^2, 1 % at 16384^2);
-                                      0 (default) = (C - (float)p) - (float)q.  No effect on FP64 plans */
+                                      relative to itself rather than to p and q (far fewer passes where
+                                      FP32 rounding would stall the solve; about 6 % more time per pass
+                                      at 4096^2, 1 % at 16384^2, none where a pass is latency-bound);
+                                      0 = (C - (float)p) - (float)q; 2 (default) = 1 for instances of
+                                      fewer than 4M plan entries and in the batch engine, 0 above.
+                                      No effect on FP64 plans.  Other values: PDOT_ERR_ARG */
 } pdot_options;
 
 typedef struct {

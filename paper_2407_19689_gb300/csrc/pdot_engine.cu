@@ -406,6 +406,7 @@ void init_ctrl(pdot_handle* h, Ctrl* S, long long m, long long n, double tol, do
     }
     S->eta = eta;
     S->omega = omega;
+    S->wavg = 1.0;
     S->tau = eta / omega;
     S->sigma = eta * omega;
     S->tol = tol;
@@ -441,7 +442,6 @@ bool keep_c_in_l2(pdot_handle* h, const Inst& I) {
 void stage_instance(pdot_handle* h, const Inst& I) {
     *h->h_inst = I;
     h->h_inst->l2_keep_c = keep_c_in_l2(h, I) ? 1 : 0;
-    h->h_inst->comp = h->opt.compensated_cost ? 1 : 0;
     h->cfg.gen_dims = I.ctype == PDOT_POINTS ? I.gen.d : 0;
     CK(cudaMemcpyAsync(h->d_inst, h->h_inst, sizeof(Inst), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
@@ -606,6 +606,16 @@ double round_plan_dev(pdot_handle* h, long long m, long long n, int xtype, const
                       const double* f, const double* g, void* X_out, const void* C, int ctype, long long ldc,
                       const GenSpec* gen);
 
+// Compensated reduced cost (option compensated_cost; reading C9): 2 = on
+// where a pass is latency-bound (fewer than 4M plan entries, the autotuner's
+// threshold too), where it costs nothing, and off above, where it costs about
+// 6 % per pass at 4096^2.  The batch engine (many small instances) takes it
+// unless it is switched off.
+bool compensation_for(pdot_handle* h, long long m, long long n) {
+    const int c = h->opt.compensated_cost;
+    return c == 1 || (c == 2 && m * n < (1LL << 22));
+}
+
 // Autotuner: on the first single-instance solve of a shape (m, n, dtype),
 // time whole PDHG steps (fused pass + dual update, constant step) for each
 // candidate (pass kernel, tile height) on this device with CUDA events --
@@ -615,6 +625,7 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
                    const double* f, const double* g) {
     const int ttype = ttype_of(ctype);
     const int gen_d = gen_dims_of(C, ctype);
+    h->cfg.comp = compensation_for(h, m, n) ? 1 : 0;
     if (h->opt.pass_kernel > 0) {
         // An explicit kernel choice: no timing, no cache entry.
         int v = h->opt.pass_kernel - 1;
@@ -642,10 +653,12 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
     }
     // Each candidate is timed on whole PDHG steps (pass + dual update): tile
     // height also sets how many partial sums the dual update has to read.
-    // Tile height 0: one tile per resident warp.
-    const int cands[5][2] = {{1, 0}, {2, 0}, {2, 32}, {2, 64}, {2, 128}};
+    // Tile height 0: one tile per resident warp.  The first candidate (the
+    // grouped kernel with one tile per warp, the fastest at 4096^2 in every
+    // measurement) is the default the others must beat by 5 %.
+    const int cands[5][2] = {{2, 0}, {1, 0}, {2, 32}, {2, 64}, {2, 128}};
     float best = 1e30f;
-    int best_k = 1, best_tr = tile_rows_for(h, m, n, ttype, 1, false);
+    int best_k = 2, best_tr = tile_rows_for(h, m, n, ttype, 2, false, true);
     const int reps = m * n >= (1LL << 26) ? 6 : 20;
     for (const auto& c : cands) {
         const int kern = c[0];
@@ -767,7 +780,7 @@ bool import_state(pdot_handle* h, const void* in, Ctrl* S) {
                            h->stream));
     }
     const Ctrl& B = hd.ctrl;
-    S->eta = B.eta; S->omega = B.omega; S->tau = B.tau; S->sigma = B.sigma;
+    S->eta = B.eta; S->omega = B.omega; S->tau = B.tau; S->sigma = B.sigma; S->wavg = B.wavg;
     S->kkt0 = B.kkt0; S->kkt_prev = B.kkt_prev;
     S->k = B.k; S->total = B.total; S->passes = B.passes; S->restarts = B.restarts; S->rejected = B.rejected;
     S->checks = B.checks - (hd.replay ? 1 : 0);   // the stopped check runs again
@@ -1199,7 +1212,6 @@ void batch_compose(pdot_handle* h) {
             ldc = padded_ldc(s->req.n, s->req.c_dtype);
         }
         B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
-        B->insts.h[i].comp = h->opt.compensated_cost ? 1 : 0;
         const int tt = s->ttype;
         const bool act = active[(size_t)i] != 0;
         for (int t = 0; t < s->w.ntiles; ++t) {
@@ -1282,12 +1294,13 @@ void batch_launch_chunk(pdot_handle* h) {
     BatchEngine* B = h->batch;
     const int types = B->types;
     h->cfg.gen_dims = B->gen_dims;
+    h->cfg.comp = h->opt.compensated_cost != 0 ? 1 : 0;
     long long tmaps = 0;
     for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
     const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->cnt.d,
                               (long long)(uintptr_t)B->vmap.d, tmaps,
                               types | ((long long)B->nv_grid << 8) | ((long long)B->gen_dims << 48),
-                              h->opt.restart_check_every, h->opt.chunk_checks, 0};
+                              h->opt.restart_check_every, h->opt.chunk_checks, h->cfg.comp};
     if (!h->opt.use_graph) {
         batch_issue_chunk(h, types);
     } else {
@@ -1617,7 +1630,7 @@ void pdot_default_options(pdot_options* o) {
     o->chunk_checks = 4;
     o->batch_active_bytes = 0;
     o->pass_kernel = 0;
-    o->compensated_cost = 0;
+    o->compensated_cost = 2;
 }
 
 const char* pdot_status_str(pdot_status s) {
@@ -1651,6 +1664,7 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
             throw ArgError{"tile_rows must be 0 or an even number in [2, 4096]"};
         }
         if (h->opt.pass_kernel < 0 || h->opt.pass_kernel > 3) throw ArgError{"pass_kernel must be in 0..3"};
+        if (h->opt.compensated_cost < 0 || h->opt.compensated_cost > 2) throw ArgError{"compensated_cost must be in 0..2"};
         int ndev = 0;
         CK(cudaGetDeviceCount(&ndev));
         if (device < 0 || device >= ndev) throw ArgError{"no such CUDA device"};
@@ -1676,6 +1690,11 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         const int grp = setup_group_pass();
         if (grp > 0) throw CudaError{(cudaError_t)grp};
         h->cfg.group_blocks = h->sm_count * (-grp);
+        const int kb = setup_kkt_bulk();
+        if (kb > 0) throw CudaError{(cudaError_t)kb};
+        h->cfg.kkt_blocks = h->sm_count * (-kb);
+        const char* kk = getenv("PDOT_KKT_BULK");
+        if (kk && atoi(kk) == 0) h->cfg.kkt_blocks = 0;   // the register KKT pass (comparison)
         const int coop = setup_coop_chunk();
         if (coop > 0) throw CudaError{(cudaError_t)coop};
         int coop_ok = 0;
@@ -1702,7 +1721,7 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         // Programmatic dependent launch: on (PDOT_PDL=0 turns it off).
         const char* pp = getenv("PDOT_PDL");
         h->cfg.pdl = (pp && atoi(pp) == 0) ? 0 : 1;
-        h->cfg.comp = h->opt.compensated_cost ? 1 : 0;
+        h->cfg.comp = h->opt.compensated_cost == 1 ? 1 : 0;   // set per call (compensation_for)
         h->cfg_base = h->cfg;
         CK(cudaMalloc(&h->wctr, sizeof(unsigned) * WC_N));
         CK(cudaMemset(h->wctr, 0, sizeof(unsigned) * WC_N));

@@ -41,6 +41,7 @@ constexpr int ST_OK = 0, ST_ARG = 1, ST_DEVICE = 3, ST_NUMERIC = 4, ST_MAX_ITER 
 struct Ctrl {
     // iteration state
     double eta, omega, tau, sigma;
+    double wavg;         // 1 / (k + 1): the running average's weight of the next accepted iterate
     double kkt0, kkt_prev;
     long long k, total, passes, restarts, rejected, checks;
     int cur, nxt, bar, barn, anc;
@@ -133,8 +134,6 @@ struct Inst {
     unsigned int* ticket;
     int nstrips, nchunks, tile_rows, ntiles, nvt;
     int l2_keep_c;       // 1: C fits in L2 next to the streams; load it evict-last, stream X evict-first
-    int comp;            // FP32 plans: 1 = compensated reduced cost (duals as FP32 hi/lo pairs), 0 = plain
-    int pad_;
 };
 
 // Grid barrier state of the cooperative chunk kernel (device memory, zeroed
@@ -180,6 +179,7 @@ struct LaunchCfg {
     int pdl;              // 1: launch with programmatic dependent launch
     int gen_dims;         // largest coordinate count of the generated costs in flight (TT_GEN)
     int comp;             // 1: plan passes of FP32 plans form the compensated reduced cost
+    int kkt_blocks;       // CTAs of the bulk-copy KKT pass (0: the register KKT pass)
 };
 
 // Tile and vector-tile counts are read from device memory, so one captured
@@ -203,6 +203,7 @@ int occupancy_vec_blocks_per_sm();
 // the CTAs per SM it can hold, or a positive cudaError_t code.
 int setup_bulk_pass();
 int setup_group_pass();
+int setup_kkt_bulk();
 int setup_coop_chunk();
 // K passes and one check of a single FP32-plan instance in one cooperative launch.
 int launch_chunk_coop(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const TileRef* d_vmap,

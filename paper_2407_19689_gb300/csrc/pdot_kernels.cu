@@ -183,29 +183,6 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Sum NV doubles over a 256-thread block in a fixed order; result in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[w * NV + k];
-            v[k] = s;
-        }
-    }
-    __syncthreads();
-}
-
 template <typename TX>
 __device__ __forceinline__ TX* slot_x(const Inst& I, int s) {
     return reinterpret_cast<TX*>(I.X) + (long long)s * I.xslot;
@@ -303,7 +280,7 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
     const double* q = p + m;
     const bool first = S.k == 0;
     const A tau = (A)S.tau;
-    const A w = (A)(1.0 / (double)(S.k + 1));
+    const A w = (A)S.wavg;
 
     A qv[4], ql[4];
     bool valid[4];
@@ -702,7 +679,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             split_dual(valid[e] ? q[j0 + e] : 0.0, qv[e], ql[e]);
         }
         tau = (float)Sc.tau;
-        w = (float)(1.0 / (double)(Sc.k + 1));
+        w = (float)Sc.wavg;
         first = Sc.k == 0;
         c_p = pv;
         c_i1 = i1;
@@ -1130,7 +1107,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
             split_dual(valid[e] ? q[j0 + e] : 0.0, qv[e], ql[e]);
         }
         tau = (float)Sc.tau;
-        w = (float)(1.0 / (double)(Sc.k + 1));
+        w = (float)Sc.wavg;
         first = Sc.k == 0;
         c_win = -1;
 #pragma unroll
@@ -1331,7 +1308,9 @@ __device__ __forceinline__ SchedFactors sched_factors(const Ctrl* S, long long t
     return r;
 }
 
-__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, SchedFactors fac) {
+// w_next: 1 / (k + 2), the averaging weight after an accepted step (computed
+// by the caller early, off this serial path).
+__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, SchedFactors fac, double w_next) {
     S->passes += 1;
     S->last_dX2 = dX2;
     S->last_dy2 = dy2;
@@ -1364,6 +1343,7 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, Sch
         S->bar = S->barn;
         assign_free(S);
         S->k += 1;
+        S->wavg = w_next;
         S->total += 1;
     } else {
         S->rejected += 1;
@@ -1371,27 +1351,6 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, Sch
     S->eta = eta;
     S->tau = eta / S->omega;
     S->sigma = eta * S->omega;
-}
-
-// Fixed-order sum of a partial column: group g (of VG) adds partials g, g+VG, ...
-// of entry `idx`, then group 0 combines the VG group sums in order.
-__device__ __forceinline__ double group_sum(const double* part, long long stride, int count, long long idx,
-                                            bool active, double* sgrp) {
-    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    double s = 0.0;
-    if (active) {
-#pragma unroll 4
-        for (int k = grp; k < count; k += VG) s += part[(long long)k * stride + idx];
-    }
-    sgrp[grp * 32 + lane] = s;
-    __syncthreads();
-    double t = 0.0;
-    if (grp == 0) {
-#pragma unroll
-        for (int g2 = 0; g2 < VG; ++g2) t += sgrp[g2 * 32 + lane];
-    }
-    __syncthreads();
-    return t;
 }
 
 // One vector tile (VE = 32 entries of [p; q]) per CTA.  All warps add the
@@ -1411,7 +1370,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
     const long long yo = row ? idx : m + idx;                   // p_i or q_j
     const long long so = row ? m + n + idx : 2 * m + n + idx;   // r_i or c_j
     int status = ST_RUNNING;
-    double sigma = 0.0, b = 0.0, r = 0.0, y = 0.0, ybar = 0.0;
+    double sigma = 0.0, b = 0.0, r = 0.0, y = 0.0, ybar = 0.0, wavg = 1.0, w_next = 0.5;
     long long k = 0;
     double* Vn = nullptr;
     double* Vbn = nullptr;
@@ -1420,6 +1379,8 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
         status = S->status;
         sigma = S->sigma;
         k = S->k;
+        wavg = S->wavg;
+        w_next = 1.0 / (double)(k + 2);   // used by the instance's last tile, if the step is accepted
         // requested now, used only by the instance's last tile
         if (S->adaptive_step) fac = sched_factors(S, S->total);
         const double* Vc = slot_v(I, S->cur);
@@ -1452,7 +1413,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
             // t: this row's or column's sum of X+ - X (the pass sums the change
             // itself, so the step-size term dy^T A dX below is not a difference
             // of two nearly equal sums); (2X+ - X) 1 = r + 2t, X+ 1 = r + t.
-            const double w = 1.0 / (double)(k + 1);
+            const double w = wavg;
             const double yn = y + sigma * (b - (r + 2.0 * t));
             Vn[yo] = yn;
             Vn[so] = r + t;
@@ -1490,7 +1451,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
             b2 = warp_sum(b2);
             if (lane == 0) {
                 *I.ticket = 0u;
-                finalize_step(S, b2, b0, b1, fac);
+                finalize_step(S, b2, b0, b1, fac, w_next);
             }
         }
     }
@@ -1567,6 +1528,13 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
     double* rowpart = I.rowpart + (long long)strip * m;
     double* rowpart2 = I.rowpart2 + (long long)strip * m;
 
+    // FP32 plans accumulate in FP32 over KFLUSH row batches before adding
+    // into the FP64 partials (an FP64 add per batch of two rows would make
+    // this pass bound by the narrow FP64 pipe).
+    constexpr int KFLUSH = sizeof(A) == 4 ? 8 : 1;
+    A t[TP] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+    A csa[4] = {A(0), A(0), A(0), A(0)}, csa2[4] = {A(0), A(0), A(0), A(0)};
+    int nbatch = 0;
     for (long long ib = i0; ib < i1; ib += KU) {
         A c[KU][4], x[KU][4], xb[KU][4], xa[KU][4], pv[KU], pbv[KU];
 #pragma unroll
@@ -1588,8 +1556,6 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
                 }
             }
         }
-        A t[TP] = {A(0), A(0), A(0), A(0), A(0), A(0)};
-        A csa[4] = {A(0), A(0), A(0), A(0)}, csa2[4] = {A(0), A(0), A(0), A(0)};
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
             const long long i = ib + u;
@@ -1626,12 +1592,20 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
                 if (rv && lane == 0) rowpart2[i] = (double)rs2;
             }
         }
+        if (++nbatch == KFLUSH || ib + KU >= i1) {
 #pragma unroll
-        for (int k = 0; k < TP; ++k) acc[k] += (double)t[k];
+            for (int k = 0; k < TP; ++k) {
+                acc[k] += (double)t[k];
+                t[k] = A(0);
+            }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            cs[e] += (double)csa[e];
-            cs2[e] += (double)csa2[e];
+            for (int e = 0; e < 4; ++e) {
+                cs[e] += (double)csa[e];
+                cs2[e] += (double)csa2[e];
+                csa[e] = A(0);
+                csa2[e] = A(0);
+            }
+            nbatch = 0;
         }
     }
     if (sums && on) {
@@ -1668,6 +1642,309 @@ k_kkt(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const in
         const Ctrl& S = *I.ctrl;
         if (S.status != ST_RUNNING) continue;
         kkt_tile<TC, TX>(I, S, tr.local, lane, mode);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// KKT pass, bulk-copy pipeline (FP32 plans with a stored FP32 or BF16 cost):
+// the arithmetic of kkt_tile, with each warp streaming its tile's rows of C,
+// X, Xbar and the restart anchor through KS shared-memory stages filled by
+// cp.async.bulk (completion counted on one mbarrier per stage, bounded wait),
+// so a warp keeps KS rows of four arrays in flight without holding them in
+// registers.  The FP32 accumulators are added into FP64 every 16 rows.
+// ---------------------------------------------------------------------------
+constexpr int KS = 4;                     // stages per warp (two CTAs per SM: 64 rows of 4 arrays in flight)
+constexpr int KSTAGE = 4 * STRIP * 4;     // C (<= 512 B), X, Xbar, anchor (512 B each)
+constexpr int KACC = TP + 8;              // FP64 accumulators per lane kept in shared memory (6 scalars, 2 x 4 columns)
+__host__ __device__ constexpr int kkt_warp_smem() {
+    return KS * KSTAGE + KS * 8 + KS * 8 + bulk::PWIN * 8 + KACC * 32 * 8;
+}
+constexpr int kkt_smem() { return TWARPS * kkt_warp_smem(); }
+
+template <typename TC>
+__global__ void __launch_bounds__(TWARPS * 32, 2)
+k_kkt_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
+           unsigned* wctr, int wc, int mode) {
+    using namespace bulk;
+    const int T = *Tp;   // host-written: read before the wait
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wbase = dsm + warp * kkt_warp_smem();
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(wbase + KS * KSTAGE);
+    RowRef* refs = reinterpret_cast<RowRef*>(wbase + KS * KSTAGE + KS * 8);
+    float2* pbuf = reinterpret_cast<float2*>(wbase + KS * KSTAGE + KS * 16);   // (p_i, pbar_i) of a row window
+    // The lane's FP64 accumulators (kept out of registers): [k * 32 + lane],
+    // k < TP the tile scalars, then 4 column sums (average / initial plan), 4
+    // column sums (current plan).
+    double* sacc = reinterpret_cast<double*>(wbase + KS * KSTAGE + KS * 16 + bulk::PWIN * 8);
+    const unsigned wbase_s = smem_u32(wbase);
+    const unsigned bars_s = smem_u32(bars);
+    if (lane == 0) {
+        for (int s = 0; s < KS; ++s) mbar_init(bars_s + 8 * s, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    prefetch_first_tile(insts, tmap, T);
+    pdl_enter();
+    reset_other_counters(wctr, wc);
+    const bool init = mode == MODE_INIT;
+    constexpr long long CQ = sizeof(TC) == 2 ? 8 : 4;   // C elements per 16 bytes
+
+    // ---- producer ----
+    int p_tile = T;
+    long long p_row = 0, p_end = 0, p_r0 = 0, p_last_ragged = -1;
+    const char* p_c0 = nullptr;     // C, X, Xbar, anchor at the tile's first row
+    const char* p_x0 = nullptr;
+    const char* p_xb0 = nullptr;
+    const char* p_xa0 = nullptr;
+    long long p_cstride = 0, p_xstride = 0;
+    unsigned p_cbytes = 0, p_xbytes = 0;
+    bool p_avg = false;
+    bool q_first = true;
+    auto next_tile = [&]() {
+        for (;;) {
+            p_tile = tile_next(&wctr[wc], q_first);
+            if (p_tile >= T) return;
+            const TileRef tr = tmap[p_tile];
+            const Inst& I = insts[tr.inst];
+            const Ctrl& Sc = *I.ctrl;
+            if (Sc.status != ST_RUNNING) continue;
+            const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
+            const long long c0 = (long long)strip * STRIP;
+            const long long ncols = min((long long)STRIP, I.n - c0);
+            p_r0 = (long long)chunk * I.tile_rows;
+            p_row = p_r0;
+            p_end = min(p_r0 + (long long)I.tile_rows, I.m);
+            p_xstride = I.ldx * 4;
+            p_cstride = I.ldc * (long long)sizeof(TC);
+            p_c0 = reinterpret_cast<const char*>(I.C) + p_r0 * p_cstride + c0 * (long long)sizeof(TC);
+            const float* Xb = reinterpret_cast<const float*>(I.X);
+            p_x0 = reinterpret_cast<const char*>(Xb + (long long)Sc.cur * I.xslot + p_r0 * I.ldx + c0);
+            p_xb0 = reinterpret_cast<const char*>(Xb + (long long)Sc.bar * I.xslot + p_r0 * I.ldx + c0);
+            p_xa0 = reinterpret_cast<const char*>(Xb + (long long)Sc.anc * I.xslot + p_r0 * I.ldx + c0);
+            p_xbytes = (unsigned)(((ncols + 3) / 4) * 16);
+            p_cbytes = (unsigned)(((ncols + CQ - 1) / CQ) * CQ * (long long)sizeof(TC));
+            // The rounded-up C copy could run past the caller's allocation on
+            // the last matrix row of a ragged strip: lanes load that row.
+            p_last_ragged = (ncols % CQ) != 0 ? I.m - 1 : -1;
+            p_avg = !init && Sc.k > 0;
+            return;
+        }
+    };
+    long long issued = 0, consumed = 0;
+    auto issue = [&]() {
+        const int st = (int)(issued % KS);
+        const long long dr = p_row - p_r0;
+        if (lane == 0) {
+            refs[st].tile = p_tile;
+            refs[st].row = (int)p_row;
+            const unsigned bar = bars_s + 8 * st;
+            const unsigned dst = wbase_s + st * KSTAGE;
+            const unsigned cb = p_row == p_last_ragged ? 0u : p_cbytes;
+            fence_proxy_async();
+            mbar_expect_tx(bar, cb + p_xbytes + (p_avg ? p_xbytes : 0u) + (init ? 0u : p_xbytes));
+            if (cb) g2s(dst, p_c0 + dr * p_cstride, cb, bar);
+            g2s(dst + STRIP * 4, p_x0 + dr * p_xstride, p_xbytes, bar);
+            if (p_avg) g2s(dst + 2 * STRIP * 4, p_xb0 + dr * p_xstride, p_xbytes, bar);
+            if (!init) g2s(dst + 3 * STRIP * 4, p_xa0 + dr * p_xstride, p_xbytes, bar);
+        }
+        ++issued;
+        if (++p_row >= p_end) next_tile();
+    };
+    next_tile();
+    while (issued < KS && p_tile < T) issue();
+
+    // ---- consumer ----
+    int c_tile = -1, c_local = 0;
+    const Inst* CI = nullptr;
+    const TC* c_C = nullptr;
+    long long c_ldc = 0, c_i0 = 0, c_i1 = 0, c_n = 0, c_last_ragged = -1, c_chunk = 0, c_win = -1, j0 = 0;
+    bool on = false, c_avg = false, valid[4] = {false, false, false, false};
+    float qv[4] = {0.f, 0.f, 0.f, 0.f}, qbv[4] = {0.f, 0.f, 0.f, 0.f};
+    const double* c_p = nullptr;
+    const double* c_pb = nullptr;
+    double* c_rowpart = nullptr;
+    double* c_rowpart2 = nullptr;
+    float t[TP], csa[4], csa2[4];
+    int rows_in_batch = 0;
+    auto flush_acc = [&]() {
+#pragma unroll
+        for (int k = 0; k < TP; ++k) { sacc[k * 32 + lane] += (double)t[k]; t[k] = 0.f; }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            sacc[(TP + e) * 32 + lane] += (double)csa[e];
+            sacc[(TP + 4 + e) * 32 + lane] += (double)csa2[e];
+            csa[e] = 0.f;
+            csa2[e] = 0.f;
+        }
+        rows_in_batch = 0;
+    };
+    auto flush_tile = [&]() {
+        if (c_tile < 0) return;
+        flush_acc();
+        const double* cs = sacc + TP * 32;
+        if (on && (init || c_avg)) {
+            double* cp = CI->colpart + c_chunk * CI->ldx + j0;
+            reinterpret_cast<double2*>(cp)[0] = make_double2(cs[0 * 32 + lane], cs[1 * 32 + lane]);
+            reinterpret_cast<double2*>(cp)[1] = make_double2(cs[2 * 32 + lane], cs[3 * 32 + lane]);
+        }
+        if (on && !init) {
+            double* cp = CI->colpart2 + c_chunk * CI->ldx + j0;
+            reinterpret_cast<double2*>(cp)[0] = make_double2(cs[4 * 32 + lane], cs[5 * 32 + lane]);
+            reinterpret_cast<double2*>(cp)[1] = make_double2(cs[6 * 32 + lane], cs[7 * 32 + lane]);
+        }
+#pragma unroll
+        for (int k = 0; k < TP; ++k) {
+            const double a = warp_sum(sacc[k * 32 + lane]);
+            if (lane == 0) CI->tpart[(long long)c_local * TP + k] = a;
+        }
+    };
+    auto open_consumer = [&](int tt) {
+        flush_tile();
+        c_tile = tt;
+        const TileRef tr = tmap[tt];
+        CI = &insts[tr.inst];
+        const Ctrl& Sc = *CI->ctrl;
+        c_local = tr.local;
+        const int strip = tr.local % CI->nstrips;
+        c_chunk = tr.local / CI->nstrips;
+        const long long c0 = (long long)strip * STRIP;
+        c_n = CI->n;
+        c_ldc = CI->ldc;
+        c_i0 = c_chunk * CI->tile_rows;
+        c_i1 = min(c_i0 + (long long)CI->tile_rows, CI->m);
+        j0 = c0 + lane * 4;
+        on = j0 < c_n;
+        const long long ncols = min((long long)STRIP, c_n - c0);
+        c_last_ragged = (ncols % CQ) != 0 ? CI->m - 1 : -1;
+        c_C = reinterpret_cast<const TC*>(CI->C) + j0;
+        c_avg = !init && Sc.k > 0;
+        c_p = slot_v(*CI, Sc.cur);
+        c_pb = slot_v(*CI, Sc.bar);
+        const double* q = c_p + CI->m;
+        const double* qb = c_pb + CI->m;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            valid[e] = j0 + e < c_n;
+            qv[e] = valid[e] ? (float)q[j0 + e] : 0.f;
+            qbv[e] = (valid[e] && c_avg) ? (float)qb[j0 + e] : 0.f;
+        }
+        c_rowpart = CI->rowpart + (long long)strip * CI->m;
+        c_rowpart2 = CI->rowpart2 + (long long)strip * CI->m;
+        c_win = -1;
+#pragma unroll
+        for (int k = 0; k < KACC; ++k) sacc[k * 32 + lane] = 0.0;
+#pragma unroll
+        for (int k = 0; k < TP; ++k) t[k] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { csa[e] = 0.f; csa2[e] = 0.f; }
+        rows_in_batch = 0;
+    };
+
+    bool failed = false;
+    while (consumed < issued) {
+        const int st = (int)(consumed % KS);
+        if (!wait_stage(bars_s + 8 * st, (unsigned)((consumed / KS) & 1))) { failed = true; break; }
+        const RowRef ref = refs[st];
+        if (ref.tile != c_tile) open_consumer(ref.tile);
+        const long long i = ref.row;
+        const long long di = i - c_i0;
+        const unsigned char* stage = wbase + st * KSTAGE;
+        float c[4], x[4], xb[4], xa[4];
+        if (on) {
+            if (i != c_last_ragged) {
+                if (sizeof(TC) == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(stage + lane * 16);
+                    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+                } else {
+                    const uint2 v = *reinterpret_cast<const uint2*>(stage + lane * 8);
+                    c[0] = bf16_bits_to_f32(v.x & 0xffffu);
+                    c[1] = bf16_bits_to_f32(v.x >> 16);
+                    c[2] = bf16_bits_to_f32(v.y & 0xffffu);
+                    c[3] = bf16_bits_to_f32(v.y >> 16);
+                }
+            } else {
+                ldc4_tail<float>(c_C + i * c_ldc, c_n - j0, c);
+            }
+            const float4 vx = *reinterpret_cast<const float4*>(stage + STRIP * 4 + lane * 16);
+            x[0] = vx.x; x[1] = vx.y; x[2] = vx.z; x[3] = vx.w;
+            if (c_avg) {
+                const float4 vb = *reinterpret_cast<const float4*>(stage + 2 * STRIP * 4 + lane * 16);
+                xb[0] = vb.x; xb[1] = vb.y; xb[2] = vb.z; xb[3] = vb.w;
+            } else {
+                xb[0] = xb[1] = xb[2] = xb[3] = 0.f;
+            }
+            if (!init) {
+                const float4 va = *reinterpret_cast<const float4*>(stage + 3 * STRIP * 4 + lane * 16);
+                xa[0] = va.x; xa[1] = va.y; xa[2] = va.z; xa[3] = va.w;
+            } else {
+                xa[0] = xa[1] = xa[2] = xa[3] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { c[e] = 0.f; x[e] = 0.f; xb[e] = 0.f; xa[e] = 0.f; }
+        }
+        // Row duals (current and average) staged per window of PWIN rows.
+        const long long win = di / PWIN;
+        if (win != c_win) {
+            const long long r0 = c_i0 + win * PWIN;
+            const long long r1 = min(r0 + (long long)PWIN, c_i1);
+            __syncwarp();
+            for (long long r = r0 + lane; r < r1; r += 32)
+                pbuf[r - r0] = make_float2((float)c_p[r], c_avg ? (float)c_pb[r] : 0.f);
+            __syncwarp();
+            c_win = win;
+        }
+        const float2 pp = pbuf[di - win * PWIN];
+        // The stage has been read: release it to the producer.
+        __syncwarp();
+        ++consumed;
+        if (p_tile < T) issue();
+
+        float rs = 0.f, rs2 = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (!valid[e]) continue;
+            const float Rc = (c[e] - pp.x) - qv[e];
+            t[0] += c[e] * x[e];
+            t[1] += Rc < 0.f ? Rc * Rc : 0.f;                  // [p + q - C]^+ squared
+            const float da = x[e] - xa[e];
+            t[4] += da * da;
+            if (init) t[2] += c[e] * c[e];                      // ||C||_F^2 (once per solve)
+            if (c_avg) {
+                const float Rb = (c[e] - pp.y) - qbv[e];
+                t[2] += c[e] * xb[e];
+                t[3] += Rb < 0.f ? Rb * Rb : 0.f;
+                const float db = xb[e] - xa[e];
+                t[5] += db * db;
+            }
+            const float sv = init ? x[e] : xb[e];
+            rs += sv;
+            csa[e] += sv;
+            rs2 += x[e];
+            csa2[e] += x[e];
+        }
+        if (init || c_avg) {
+            rs = warp_sum(rs);
+            if (lane == 0) c_rowpart[i] = (double)rs;
+        }
+        if (!init) {
+            rs2 = warp_sum(rs2);
+            if (lane == 0) c_rowpart2[i] = (double)rs2;
+        }
+        if (++rows_in_batch == 16) flush_acc();
+    }
+    pdl_release();
+    if (!failed) {
+        flush_tile();
+    } else if (lane == 0) {
+        const int tt = refs[(int)(consumed % KS)].tile;
+        atomicExch(&insts[tmap[tt].inst].ctrl->status, ST_DEVICE);
+    }
+    while (consumed < issued) {   // drain: wait (bounded) for every copy still in flight
+        const int st = (int)(consumed % KS);
+        wait_stage(bars_s + 8 * st, (unsigned)((consumed / KS) & 1));
+        ++consumed;
     }
 }
 
@@ -1802,6 +2079,7 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         S->barn = picks[2];
     }
     S->k = 0;
+    S->wavg = 1.0;
     S->kkt0 = kk.kkt;
     S->kkt_prev = kk.kkt;
     S->restarts += 1;
@@ -1809,7 +2087,45 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
     S->sigma = S->eta * S->omega;
 }
 
-__device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double* red, double* sgrp, int* s_last) {
+// Fixed-order sums of entry `idx` over two partial sets at once (A: the
+// average's, or the plan's at the initial check; B: the current plan's):
+// group g (warp g) adds partials g, g + VG, ... of each set, then warp 0
+// combines the VG group sums in order.  One block barrier; the results are
+// valid in warp 0.
+__device__ __forceinline__ void group_sum2(const double* pa, const double* pb, long long stride, int count,
+                                           long long idx, bool active, bool use_a, bool use_b, double* sgrp,
+                                           double& sa, double& sb) {
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    double a = 0.0, b = 0.0;
+    if (active) {
+#pragma unroll 4
+        for (int k = grp; k < count; k += VG) {
+            if (use_a) a += pa[(long long)k * stride + idx];
+            if (use_b) b += pb[(long long)k * stride + idx];
+        }
+    }
+    sgrp[grp * 32 + lane] = a;
+    sgrp[(VG + grp) * 32 + lane] = b;
+    __syncthreads();
+    sa = 0.0;
+    sb = 0.0;
+    if (grp == 0) {
+#pragma unroll
+        for (int g2 = 0; g2 < VG; ++g2) {
+            sa += sgrp[g2 * 32 + lane];
+            sb += sgrp[(VG + g2) * 32 + lane];
+        }
+    }
+}
+
+// One vector tile of the check: the exact row / column sums (both partial
+// sets in one phase), then warp 0 alone forms the residual, dual-objective and
+// distance terms, adds the tile partials of the plan pass, reduces the twelve
+// scalars with shuffles and takes the instance's ticket; the last tile runs
+// the restart / termination logic.  FP64 stays on one warp (a narrow pipe on
+// this part) and only one block barrier is on the path.  sgrp: 2 VG x 32
+// doubles.
+__device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double* sgrp) {
     const long long m = I.m, n = I.n;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const long long e = (long long)lvt * VE + lane;
@@ -1818,88 +2134,87 @@ __device__ void checkvec_tile(const Inst& I, Ctrl* S, int lvt, int mode, double*
     const bool row = e < m, col = !row && e < m + n;
     const long long idx = row ? e : e - m;          // i or j
     double s = 0.0, s2 = 0.0;
-    if (init || avg) {   // uniform across the block
-        s = group_sum(row ? I.rowpart : I.colpart, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx, row || col,
-                      sgrp);
-    }
-    if (!init) {   // the current plan's exact sums (the passes carry them forward by sums of changes)
-        s2 = group_sum(row ? I.rowpart2 : I.colpart2, row ? m : I.ldx, row ? I.nstrips : I.nchunks, idx,
-                       row || col, sgrp);
-    }
-    double* Vc = slot_v(I, S->cur);
-    double* Vb = slot_v(I, S->bar);
-    const double* Va = slot_v(I, S->anc);
-    double a[VP];
+    // A: the plan's sums at the initial check, the average's at a check;
+    // B: the current plan's exact sums (the passes carry them forward by sums
+    // of changes between checks).
+    group_sum2(row ? I.rowpart : I.colpart, row ? I.rowpart2 : I.colpart2, row ? m : I.ldx,
+               row ? I.nstrips : I.nchunks, idx, row || col, init || avg, !init, sgrp, s, s2);
+    if (grp == 0) {
+        double* Vc = slot_v(I, S->cur);
+        double* Vb = slot_v(I, S->bar);
+        const double* Va = slot_v(I, S->anc);
+        double a[VP];
 #pragma unroll
-    for (int k = 0; k < VP; ++k) a[k] = 0.0;
-    if (grp == 0 && (row || col)) {
-        const long long yo = row ? idx : m + idx;               // offset of p_i / q_j in a vector set
-        const long long so = row ? m + n + idx : 2 * m + n + idx;   // offset of r_i / c_j
-        const double b = row ? I.f[idx] : I.g[idx];
-        const double y = Vc[yo];
-        if (init) {
-            Vc[so] = s;
-            a[0] = (s - b) * (s - b);
-            a[2] = b * y;
-            // marginal statistics: sum f, sum g, ||[f;g]||^2, invalid entries
-            if (row) a[1] = b; else a[3] = b;
-            a[4] = b * b;
-            a[5] = (b >= 0.0 && isfinite(b)) ? 0.0 : 1.0;
-        } else {
-            const double r = s2;
-            Vc[so] = s2;
-            a[0] = (r - b) * (r - b);
-            a[2] = b * y;
-            const double ya = Va[yo];
-            a[4] = (y - ya) * (y - ya);
-            if (avg) {
-                Vb[so] = s;
-                const double yb = Vb[yo];
-                a[1] = (s - b) * (s - b);
-                a[3] = b * yb;
-                a[5] = (yb - ya) * (yb - ya);
+        for (int k = 0; k < VP; ++k) a[k] = 0.0;
+        if (row || col) {
+            const long long yo = row ? idx : m + idx;                   // offset of p_i / q_j in a vector set
+            const long long so = row ? m + n + idx : 2 * m + n + idx;   // offset of r_i / c_j
+            const double b = row ? I.f[idx] : I.g[idx];
+            const double y = Vc[yo];
+            if (init) {
+                Vc[so] = s;
+                a[0] = (s - b) * (s - b);
+                a[2] = b * y;
+                // marginal statistics: sum f, sum g, ||[f;g]||^2, invalid entries
+                if (row) a[1] = b; else a[3] = b;
+                a[4] = b * b;
+                a[5] = (b >= 0.0 && isfinite(b)) ? 0.0 : 1.0;
+            } else {
+                Vc[so] = s2;
+                a[0] = (s2 - b) * (s2 - b);
+                a[2] = b * y;
+                const double ya = Va[yo];
+                a[4] = (y - ya) * (y - ya);
+                if (avg) {
+                    Vb[so] = s;
+                    const double yb = Vb[yo];
+                    a[1] = (s - b) * (s - b);
+                    a[3] = b * yb;
+                    a[5] = (yb - ya) * (yb - ya);
+                }
+            }
+        }
+        const long long T = I.ntiles;
+        const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+        for (long long t = t0 + lane; t < t1; t += 32) {
+#pragma unroll
+            for (int k = 0; k < TP; ++k) a[6 + k] += I.tpart[t * TP + k];
+        }
+#pragma unroll
+        for (int k = 0; k < VP; ++k) a[k] = warp_sum(a[k]);
+        unsigned old = 0;
+        if (lane == 0) {
+            double* vp = I.vpart + (long long)lvt * VP;
+#pragma unroll
+            for (int k = 0; k < VP; ++k) vp[k] = a[k];
+            old = ticket_arrive(I.ticket);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        __syncwarp();
+        if (old == (unsigned)(I.nvt - 1)) {
+            double b[VP];
+#pragma unroll
+            for (int k = 0; k < VP; ++k) b[k] = 0.0;
+            for (int v = lane; v < I.nvt; v += 32) {
+                const double* vp = I.vpart + (long long)v * VP;
+#pragma unroll
+                for (int k = 0; k < VP; ++k) b[k] += __ldcg(vp + k);
+            }
+#pragma unroll
+            for (int k = 0; k < VP; ++k) b[k] = warp_sum(b[k]);
+            if (lane == 0) {
+                *I.ticket = 0u;
+                finalize_check(S, b, mode);
             }
         }
     }
-    const long long T = I.ntiles;
-    const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
-    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < TP; ++k) a[6 + k] += I.tpart[t * TP + k];
-    }
-    block_sum<VP>(a, red);
-    if (threadIdx.x == 0) {
-        double* vp = I.vpart + (long long)lvt * VP;
-#pragma unroll
-        for (int k = 0; k < VP; ++k) vp[k] = a[k];
-        const unsigned old = ticket_arrive(I.ticket);
-        *s_last = (old == (unsigned)(I.nvt - 1));
-    }
-    __syncthreads();
-    if (*s_last) {
-        double b[VP];
-#pragma unroll
-        for (int k = 0; k < VP; ++k) b[k] = 0.0;
-        for (int v = threadIdx.x; v < I.nvt; v += blockDim.x) {
-            const double* vp = I.vpart + (long long)v * VP;
-#pragma unroll
-            for (int k = 0; k < VP; ++k) b[k] += __ldcg(vp + k);
-        }
-        block_sum<VP>(b, red);
-        if (threadIdx.x == 0) {
-            *I.ticket = 0u;
-            finalize_check(S, b, mode);
-        }
-    }
-    __syncthreads();
+    __syncthreads();   // sgrp is reused by the caller's next tile
 }
 
 __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts, const TileRef* __restrict__ vmap,
                                                  const int* __restrict__ NVp, unsigned* wctr, int mode) {
     // One CTA per vector tile (no work queue): the grid covers the tile count.
-    __shared__ double red[(VT / 32) * VP];
-    __shared__ double sgrp[VG * 32];
-    __shared__ int s_last;
+    __shared__ double sgrp[2 * VG * 32];
     pdl_enter();
     // No work counter of its own, but it still resets the others for the
     // kernels that follow (block 0, before any early exit).
@@ -1910,7 +2225,7 @@ __global__ void __launch_bounds__(VT) k_checkvec(const Inst* __restrict__ insts,
     const Inst& I = insts[tr.inst];
     Ctrl* S = I.ctrl;
     if (S->status != ST_RUNNING) return;
-    checkvec_tile(I, S, tr.local, mode, red, sgrp, &s_last);
+    checkvec_tile(I, S, tr.local, mode, sgrp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1960,9 +2275,8 @@ __global__ void __launch_bounds__(TWARPS * 32, 2)
 k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp,
              const TileRef* __restrict__ vmap, const int* __restrict__ NVp, unsigned* wctr, GridBar* gb, int npass,
              int wc_a, int wc_b, int wc_kkt) {
-    __shared__ double red[(VT / 32) * VP];
-    __shared__ double sgrp[VG * 32];
-    __shared__ int s_last, s_ok;
+    __shared__ double sgrp[2 * VG * 32];
+    __shared__ int s_ok;
     extern __shared__ __align__(128) unsigned char dsm[];
     const int T = *Tp, NV = *NVp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2004,7 +2318,7 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
                 const Inst& I = insts[tr.inst];
                 Ctrl* S = I.ctrl;
                 if (S->status != ST_RUNNING) continue;
-                checkvec_tile(I, S, tr.local, MODE_CHECK, red, sgrp, &s_last);
+                checkvec_tile(I, S, tr.local, MODE_CHECK, sgrp);
             }
         }
     }
@@ -2146,12 +2460,19 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
     if (ttype == TT_F64)
         return launch_k(pdl, k_kkt<double, double>, (unsigned)cfg.tile_blocks_f64, th, 0, st, d_insts, d_tmap, T, wctr,
                         wc, mode);
-    if (ttype == TT_BF16)
-        return launch_k(pdl, k_kkt<unsigned short, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T,
-                        wctr, wc, mode);
     if (ttype == TT_GEN)
         return launch_k(pdl, k_kkt<GenC8, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T, wctr, wc,
                         mode);
+    if (cfg.kkt_blocks > 0) {   // bulk-copy pipeline for stored FP32 / BF16 costs
+        if (ttype == TT_BF16)
+            return launch_k(pdl, k_kkt_bulk<unsigned short>, (unsigned)cfg.kkt_blocks, th, kkt_smem(), st, d_insts,
+                            d_tmap, T, wctr, wc, mode);
+        return launch_k(pdl, k_kkt_bulk<float>, (unsigned)cfg.kkt_blocks, th, kkt_smem(), st, d_insts, d_tmap, T, wctr,
+                        wc, mode);
+    }
+    if (ttype == TT_BF16)
+        return launch_k(pdl, k_kkt<unsigned short, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T,
+                        wctr, wc, mode);
     return launch_k(pdl, k_kkt<float, float>, (unsigned)cfg.tile_blocks, th, 0, st, d_insts, d_tmap, T, wctr, wc,
                     mode);
 }
@@ -2255,6 +2576,11 @@ int setup_group_pass() {
                          (const void*)k_pass_group<unsigned short, GROUP_S, false>,
                          (const void*)k_pass_group<GenC4, GROUP_S, true>, (const void*)k_pass_group<GenC4, GROUP_S, false>};
     return setup_dyn(fns, 6, group_smem());
+}
+
+int setup_kkt_bulk() {
+    const void* fns[] = {(const void*)k_kkt_bulk<float>, (const void*)k_kkt_bulk<unsigned short>};
+    return setup_dyn(fns, 2, kkt_smem());
 }
 
 int setup_bulk_pass() {

@@ -112,3 +112,19 @@ def test_state_bytes_needs_no_gpu(lib):
         assert pdot.pdot_state_bytes(m, n, xt) == 1024 + 3 * al(m * ldx * xs) + 3 * al(16 * (m + n))
     assert pdot.pdot_state_bytes(0, 5, pdot.F32) == 0
     assert pdot.pdot_state_bytes(5, 5, pdot.BF16) == 0
+
+
+def test_option_ranges_are_checked_before_any_cuda_call(lib):
+    """pdot_create rejects a pass_kernel outside 0..3 and a compensated_cost
+    outside 0..2 (PDOT_ERR_ARG) before it touches a device; the defaults are
+    the autotuner's kernel and the size-dependent compensation."""
+    import ctypes
+    from paper_2407_19689_gb300 import pdot
+    o = pdot.pdot_default_options()
+    assert o.pass_kernel == 0 and o.compensated_cost == 2
+    for field, bad in (("pass_kernel", 4), ("pass_kernel", -1), ("compensated_cost", 3)):
+        o = pdot.pdot_default_options()
+        setattr(o, field, bad)
+        h = ctypes.c_void_p()
+        assert lib.pdot_create(ctypes.byref(o), 0, None, ctypes.byref(h)) == pdot.ERR_ARG
+        assert not h.value
