@@ -35,6 +35,12 @@
 namespace pdot {
 
 constexpr int KU = 2;
+// Rows a plan pass (KKT pass) accumulates in FP32 per lane before adding into
+// its FP64 partial sums: FP64 is a narrow pipe on this part, and the FP32
+// partial over 32 (64) rows of one column carries a relative error of order
+// 1e-7, far below what the FP64 sums it feeds are compared against.
+constexpr int FLUSH_ROWS = 32;
+constexpr int KKT_FLUSH_ROWS = 64;
 constexpr int BULK_ROW_S = 8;   // row stages per warp in the per-row bulk pass   // rows per load batch in the KKT pass
 
 // ---------------------------------------------------------------------------
@@ -829,7 +835,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
         }
         rs = warp_sum(rs);
         if (lane == 0) c_rowpart[i] = (double)rs;
-        if (++rows_in_batch == 8) {
+        if (++rows_in_batch == FLUSH_ROWS) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
             dx2 += (double)dxa;
@@ -1253,7 +1259,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
         const float tot = rows4_sum(rsv, lane);
         if ((lane & 7) == 0 && (lane >> 3) < ref.count) c_rowpart[ref.row0 + (lane >> 3)] = (double)tot;
         rows_in_batch += ref.count;
-        if (rows_in_batch >= 8) {
+        if (rows_in_batch >= FLUSH_ROWS) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
             dx2 += (double)dxa;
@@ -1528,10 +1534,11 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
     double* rowpart = I.rowpart + (long long)strip * m;
     double* rowpart2 = I.rowpart2 + (long long)strip * m;
 
-    // FP32 plans accumulate in FP32 over KFLUSH row batches before adding
+    // FP32 plans accumulate in FP32 over KKT_FLUSH_ROWS rows before adding
     // into the FP64 partials (an FP64 add per batch of two rows would make
-    // this pass bound by the narrow FP64 pipe).
-    constexpr int KFLUSH = sizeof(A) == 4 ? 8 : 1;
+    // this pass bound by the narrow FP64 pipe) -- the same grouping as
+    // k_kkt_bulk, so both give the same bits.
+    constexpr int KFLUSH = sizeof(A) == 4 ? KKT_FLUSH_ROWS / KU : 1;
     A t[TP] = {A(0), A(0), A(0), A(0), A(0), A(0)};
     A csa[4] = {A(0), A(0), A(0), A(0)}, csa2[4] = {A(0), A(0), A(0), A(0)};
     int nbatch = 0;
@@ -1932,7 +1939,7 @@ k_kkt_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, con
             rs2 = warp_sum(rs2);
             if (lane == 0) c_rowpart2[i] = (double)rs2;
         }
-        if (++rows_in_batch == 16) flush_acc();
+        if (++rows_in_batch == KKT_FLUSH_ROWS) flush_acc();
     }
     pdl_release();
     if (!failed) {
