@@ -56,6 +56,8 @@ def parse():
                          "instances through the batch engine vs one instance per launch; serve: Poisson "
                          "request stream through the continuous-batching engine vs a plain FIFO server")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-detail", action="store_true",
+                    help="batch workload: add each instance's size, passes and times, batched and alone")
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: the --serve-loads sweep)")
     ap.add_argument("--active-mb", type=float, default=400.0,
@@ -428,7 +430,7 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched and served workloads (manual runs; one JSON line each)
 # ---------------------------------------------------------------------------
-def batch_record(tol: float = 1e-6, count: int = 256) -> dict:
+def batch_record(tol: float = 1e-6, count: int = 256, detail: bool = False) -> dict:
     """The batched workload: `count` instances, m and n log-uniform in
     [64, 2048] (seeded), U[0,1]^2 points, squared-Euclidean FP32 cost,
     Dirichlet(1) marginals, each solved to `tol`; once through the batch
@@ -491,7 +493,14 @@ def batch_record(tol: float = 1e-6, count: int = 256) -> dict:
     objs_b = sorted((tid, v.result["primal_obj"]) for tid, v in rb.items())
     maxdiff = max(abs(a[1] - b.result["primal_obj"]) / abs(b.result["primal_obj"])
                   for a, b in zip(objs_b, rp))
-    return {"workload": f"batch{count}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems, "tol": tol,
+    extra = {}
+    if detail:
+        # tickets are issued in submission order, so sorted ids follow the instances
+        bres = [rb[tid] for tid in sorted(rb)]
+        extra["instances"] = [{"m": m, "n": n, "batched_passes": b.result["passes"],
+                               "batched_completion_s": b.result["seconds"], "plain_passes": p.result["passes"],
+                               "plain_s": p.result["seconds"]} for (m, n), b, p in zip(sizes, bres, rp)]
+    return {**extra, "workload": f"batch{count}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems, "tol": tol,
             "batched": {"seconds": tb, "solves_per_s": count / tb, "ok": okb, "gpu_launches": launches,
                         "passes": sum(v.result["passes"] for v in rb.values()),
                         "sgm10_completion_s": sgm10([v.result["seconds"] for v in rb.values()]),
@@ -508,7 +517,7 @@ def run_batch(args):
     from paper_2407_19689_gb300 import _build, pdot
     _build.build()
     pdot.load()
-    rec = batch_record(args.tol, args.batch_count)
+    rec = batch_record(args.tol, args.batch_count, args.batch_detail)
     tb = rec["batched"]["seconds"]
     line = {"metric": METRIC, "value": args.batch_count / tb, "unit": f"solves/s ({args.batch_count} uneven "
             f"instances to {args.tol:g} rel. KKT)", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tb * 1e3,
@@ -601,6 +610,17 @@ def run_pass_sweep(args):
                        "us": ms * 1e3, "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
                 out.append(row)
                 print(json.dumps(row), flush=True)
+        # the default kernel and tiles with the compensated reduced cost
+        os.environ.pop("PDOT_PASS_BULK", None)
+        s = pdot.Solver(device=0, compensated_cost=1)
+        st, ms, b, var = pdot.pdot_time_pass(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
+                                             30 if G == 64 else 10)
+        s.close()
+        row = {"m": m, "kernel": "compensated cost, " + {0: "register", 1: "bulk-row", 2: "bulk-group"}.get(var, "?"),
+               "tile_rows": "auto", "us": ms * 1e3,
+               "GBps": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / peak}
+        out.append(row)
+        print(json.dumps(row), flush=True)
         del C
         torch.cuda.empty_cache()
         # the same pass with the cost generated from the pixel coordinates
