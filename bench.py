@@ -499,7 +499,12 @@ def batch_record(tol: float = 1e-6, count: int = 256, detail: bool = False) -> d
         bres = [rb[tid] for tid in sorted(rb)]
         extra["instances"] = [{"m": m, "n": n, "batched_passes": b.result["passes"],
                                "batched_completion_s": b.result["seconds"], "plain_passes": p.result["passes"],
-                               "plain_s": p.result["seconds"]} for (m, n), b, p in zip(sizes, bres, rp)]
+                               "plain_s": p.result["seconds"], "batched_obj": b.result["primal_obj"],
+                               "plain_obj": p.result["primal_obj"], "batched_rel_kkt": b.result["rel_kkt"],
+                               "plain_rel_kkt": p.result["rel_kkt"],
+                               "batched_avg": b.result.get("returned_average"),
+                               "plain_avg": p.result.get("returned_average")}
+                              for (m, n), b, p in zip(sizes, bres, rp)]
     return {**extra, "workload": f"batch{count}_loguniform64-2048_dirichlet1_sqeuclid", "elements": elems, "tol": tol,
             "batched": {"seconds": tb, "solves_per_s": count / tb, "ok": okb, "gpu_launches": launches,
                         "passes": sum(v.result["passes"] for v in rb.values()),

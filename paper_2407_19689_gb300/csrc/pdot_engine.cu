@@ -425,7 +425,7 @@ void init_ctrl(pdot_handle* h, Ctrl* S, long long m, long long n, double tol, do
     S->sched_len = h->sched_len;
     S->cur = 0; S->anc = 0; S->bar = 1; S->nxt = 2; S->barn = 3;
     S->status = ST_RUNNING;
-    S->res_slot = 0;
+    S->res_slot = S->res_xslot = 0;
 }
 
 void launch_count(pdot_handle* h, int k) { h->launches += k; }
@@ -461,9 +461,16 @@ void run_step(pdot_handle* h, int ttype) {
     launch_count(h, 2);
 }
 
+// After a check: form the average plan it picked, if it picked one.
+void run_avgfix(pdot_handle* h, int ttype) {
+    CKL(launch_avgfix(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->cfg, h->stream));
+    launch_count(h, 1);
+}
+
 void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
     for (int s = 0; s < K; ++s) run_step(h, ttype);
     run_check(h, ttype, MODE_CHECK);
+    run_avgfix(h, ttype);
 }
 
 bool use_coop(pdot_handle* h, int ttype) {
@@ -478,6 +485,7 @@ void launch_chunk(pdot_handle* h, int ttype, int K) {
         CKL(launch_chunk_coop(ttype, h->d_inst, h->d_tmap, h->d_cnt, h->d_vmap, h->d_cnt + 1, h->wctr, h->d_gb, K,
                               h->cfg, h->stream));
         launch_count(h, 1);
+        run_avgfix(h, ttype);
         return;
     }
     const long long key[8] = {(long long)(uintptr_t)w.base,
@@ -709,7 +717,7 @@ void autotune_pass(pdot_handle* h, long long m, long long n, const void* C, int 
 // the controller, then the plans of the current, average and anchor slots
 // (m x ldx each) and their vector sets ([p | q | r | c]).
 // ---------------------------------------------------------------------------
-constexpr uint64_t STATE_MAGIC = 0x3130455441545350ull;   // "PSTATE01"
+constexpr uint64_t STATE_MAGIC = 0x3230455441545350ull;   // "PSTATE02" (average stored as its deviation)
 constexpr size_t STATE_HEAD = 1024;
 struct StateHead {
     uint64_t magic;
@@ -789,7 +797,7 @@ bool import_state(pdot_handle* h, const void* in, Ctrl* S) {
     S->r_kkt = B.r_kkt; S->r_rel_p = B.r_rel_p; S->r_rel_d = B.r_rel_d; S->r_rel_gap = B.r_rel_gap; S->r_rel = B.r_rel;
     S->cur = 0; S->bar = 1; S->anc = 2; S->nxt = 3; S->barn = 4;
     S->status = ST_RUNNING;
-    S->res_slot = 0;
+    S->res_slot = S->res_xslot = 0;
     S->res_avg = 0;
     return hd.replay != 0;
 }
@@ -836,7 +844,10 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
         // solve stopped at runs again with its restart logic.
         const bool replay = import_state(h, start->state_in, S);
         CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-        if (replay) run_check(h, ttype, MODE_CHECK);
+        if (replay) {
+            run_check(h, ttype, MODE_CHECK);
+            run_avgfix(h, ttype);
+        }
     } else {
         CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
         upload_start(h, start);   // X = 0, p = q = 0 (C1) unless a starting point is given
@@ -889,7 +900,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
         CK(cudaStreamSynchronize(h->stream));
         if (S->status == ST_RUNNING) {
             S->status = ST_TIMEOUT;
-            S->res_slot = S->cur;
+            S->res_slot = S->res_xslot = S->cur;
             S->res_avg = 0;
         }
     }
@@ -899,13 +910,13 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     const double bc = (double)csize_of(ctype), bx = (double)xsize_of(w.xtype);
     res->hbm_bytes = (double)S->passes * mn * (bc + 4.0 * bx) + (double)S->checks * mn * (bc + 3.0 * bx);
     res->rounded_obj = std::numeric_limits<double>::quiet_NaN();
-    const int slot = S->res_slot;
-    const char* Xslot = (const char*)w.X + (size_t)slot * (size_t)(w.m * w.ldx) * xsize_of(w.xtype);
+    const int slot = S->res_slot, xslot = S->res_xslot;   // vector set / plan of the reported point
+    const char* Xslot = (const char*)w.X + (size_t)xslot * (size_t)(w.m * w.ldx) * xsize_of(w.xtype);
     if (h->opt.round_plan) {
         res->rounded_obj =
             round_plan_dev(h, w.m, w.n, w.xtype, Xslot, w.ldx, f, g, X_out, I.C, ctype, ldc_used, &I.gen);
     } else if (X_out) {
-        copy_plan_out(h, slot, X_out, cudaMemcpyDeviceToDevice);
+        copy_plan_out(h, xslot, X_out, cudaMemcpyDeviceToDevice);
     }
     copy_duals_out(h, slot, p_out, q_out, cudaMemcpyDeviceToDevice);
     CK(cudaStreamSynchronize(h->stream));
@@ -1286,6 +1297,11 @@ void batch_issue_chunk(pdot_handle* h, int types) {
         CKL(launch_checkvec(B->insts.d, B->vmap.d, B->cnt.d + CNT_VEC, B->nv_grid, h->wctr, MODE_CHECK, h->cfg,
                             st));
         launch_count(h, 1);
+        for (int t = 0; t < NTT; ++t) {
+            if (!(types & (1 << t))) continue;
+            CKL(launch_avgfix(t, B->insts.d, B->tmap[t].d, B->cnt.d + t, h->cfg, st));
+            launch_count(h, 1);
+        }
     }
     (void)nvh;
 }
@@ -1395,7 +1411,7 @@ bool batch_retire(pdot_handle* h, const BatchEngine::Flight& f) {
             const size_t xs = xsize_of(s->w.xtype);
             const int slot = s->last.res_slot;
             if (s->req.X_out) {
-                const char* src = (const char*)s->w.X + (size_t)slot * (size_t)(s->w.m * s->w.ldx) * xs;
+                const char* src = (const char*)s->w.X + (size_t)s->last.res_xslot * (size_t)(s->w.m * s->w.ldx) * xs;
                 CK(cudaMemcpy2DAsync(s->req.X_out, (size_t)s->w.n * xs, src, (size_t)s->w.ldx * xs,
                                      (size_t)s->w.n * xs, (size_t)s->w.m, cudaMemcpyDeviceToDevice, h->stream));
             }
@@ -1905,7 +1921,20 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
         const int cur = S->cur, bar = k > 0 ? S->bar : S->cur;
         copy_plan_out(h, cur, X, cudaMemcpyDeviceToDevice);
         copy_duals_out(h, cur, p, q, cudaMemcpyDeviceToDevice);
-        if (Xbar_out) copy_plan_out(h, bar, Xbar_out, cudaMemcpyDeviceToDevice);
+        if (Xbar_out) {
+            // The average slot holds its deviation from the current plan:
+            // form X + D in the free next slot, then copy it out.
+            int src = cur;
+            if (k > 0) {
+                const size_t pe = (size_t)w.m * (size_t)w.ldx, xs = xsize_of(w.xtype);
+                const char* base = (const char*)w.X;
+                CKL(launch_combine(w.xtype, base + (size_t)cur * pe * xs, base + (size_t)bar * pe * xs,
+                                   (char*)w.X + (size_t)S->nxt * pe * xs, (long long)pe, h->stream));
+                launch_count(h, 1);
+                src = S->nxt;
+            }
+            copy_plan_out(h, src, Xbar_out, cudaMemcpyDeviceToDevice);
+        }
         copy_duals_out(h, bar, pbar_out, qbar_out, cudaMemcpyDeviceToDevice);
         CK(cudaStreamSynchronize(h->stream));
         return PDOT_OK;

@@ -5,7 +5,8 @@
 //   X    : NSLOT plan buffers of m * ldx elements (FP32 or FP64).  Roles
 //          (current, next, average, next average, restart anchor) are slot
 //          indices kept in Ctrl, so accepting a step, rejecting it or
-//          restarting swaps indices instead of copying m*n data.
+//          restarting swaps indices instead of copying m*n data.  The
+//          average's slots hold its deviation from the current plan.
 //   V    : NSLOT vector sets of 2(m+n) doubles, one per plan slot:
 //          [p (m) | q (n) | r = X1 (m) | c = X^T1 (n)].
 //   rowpart[nstrips][m], colpart[nchunks][ldx]: FP64 partial row/column sums
@@ -47,8 +48,14 @@ struct Ctrl {
     int cur, nxt, bar, barn, anc;
     int status;          // ST_RUNNING or a final status
     int res_slot, res_avg;
+    int res_xslot;       // plan slot of the reported point (res_slot: its vector set)
     int stop_req;        // host-written: 1 = stop at the next check with the current iterate (time limit)
-    int pad_;
+    // The average plan slot holds D = Xbar - X (X: the current plan), so the
+    // average itself is X + D.  A check that picks the average (a restart to
+    // it, or the reported point) sets fix: the next k_avgfix writes
+    // X[fix_dst] = X[fix_x] + X[fix_d] (in place for a restart); the next
+    // pass clears it.
+    int fix, fix_x, fix_d, fix_dst;
     // options
     double tol, beta, beta_suff, beta_nec, beta_art, theta, R, eps_zero;
     long long max_passes;
@@ -195,6 +202,12 @@ int launch_kkt(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int*
 int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, int nv_hint, unsigned* wctr, int mode,
                     const LaunchCfg& cfg, void* stream);
 int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* out, void* stream);
+// After a check: form the average plan the check picked (Ctrl::fix) for the
+// instances of one tile type.
+int launch_avgfix(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const LaunchCfg& cfg,
+                  void* stream);
+// out = a + d elementwise (count a multiple of 4; xtype 0 FP32, 2 FP64).
+int launch_combine(int xtype, const void* a, const void* d, void* out, long long count, void* stream);
 // One warp's bounded wait on a transfer that never comes; *d_status <- ST_DEVICE.
 int launch_watchdog_selftest(long long limit, int* d_status, void* stream);
 int occupancy_tile_blocks_per_sm(int ttype);

@@ -266,6 +266,22 @@ __device__ __forceinline__ bool pass_reversed(const Ctrl& S, int dir_xor) {
     return ((S.passes ^ (long long)dir_xor) & 1) != 0;
 }
 
+// Uniform running average of Algorithm 2, kept as its deviation from the
+// current plan, D = Xbar - X: Xbar+ = Xbar + w (X+ - Xbar) becomes
+// D+ = (1 - w)(D - d) with d = X+ - X, and D+ = 0 for the first iterate of an
+// epoch (Xbar+ = X+).  Stored this way, the rounding of each update is
+// relative to |D| (the spread of the iterates around their mean, which
+// shrinks as the solve converges), not to |Xbar|: an FP32 average updated in
+// place loses the late iterates' weight w = 1/(k+1) below its last bit.
+__device__ __forceinline__ float avg_dev_next(float dbar, float d, float w, bool first) {
+    const float s = dbar - d;
+    return first ? 0.f : fmaf(-w, s, s);
+}
+__device__ __forceinline__ double avg_dev_next(double dbar, double d, double w, bool first) {
+    const double s = dbar - d;
+    return first ? 0.0 : fma(-w, s, s);
+}
+
 // CP: compensated reduced cost (a kernel template parameter, so the plain
 // path is compiled without the compensated one and costs nothing extra).
 template <typename TC, typename TX, int U, bool CP>
@@ -345,7 +361,7 @@ __device__ __forceinline__ void pass_tile(const Inst& I, const Ctrl& S, int lt, 
                 rs += d;                                          // row / column sums of X+ - X
                 csa[e] += d;
                 xn[e] = v;
-                xbn[e] = first ? v : xb[u][e] + w * (v - xb[u][e]);
+                xbn[e] = avg_dev_next(xb[u][e], d, w, first);
             }
             if (rv && on) {
                 st4(Xnr + u * ldx, xn);
@@ -822,7 +838,7 @@ __device__ bool pass_row_run(const Inst* __restrict__ insts, const TileRef* __re
             rs += d;                                              // row / column sums of X+ - X
             csa[e] += d;
             xn[e] = v;
-            xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
+            xbn[e] = avg_dev_next(xb[e], d, w, first);
         }
         if (on) {
             if (c_hint) {
@@ -1244,7 +1260,7 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
                 rs += d;                                          // row / column sums of X+ - X
                 csa[e] += d;
                 xn[e] = v;
-                xbn[e] = first ? v : xb[e] + w * (v - xb[e]);
+                xbn[e] = avg_dev_next(xb[e], d, w, first);
             }
             if (on) {
                 st4(c_xn + di * c_ldx, xn);
@@ -1340,10 +1356,11 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, Sch
     }
     if (!isfinite(dX2) || !isfinite(dy2) || !isfinite(eta) || !(eta > 0.0)) {
         S->status = ST_NUMERIC;
-        S->res_slot = S->cur;
+        S->res_slot = S->res_xslot = S->cur;
         S->res_avg = 0;
         return;
     }
+    S->fix = 0;   // the plan a restart picked has been formed before this pass
     if (accept) {
         S->cur = S->nxt;
         S->bar = S->barn;
@@ -1558,6 +1575,8 @@ __device__ __forceinline__ void kkt_tile(const Inst& I, const Ctrl& S, int lt, i
                 if (avg) {
                     ld4(Xb + i * ldx + j0, xb[u]);
                     ld4(Xa + i * ldx + j0, xa[u]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) xb[u][e] = x[u][e] + xb[u][e];   // the average: X + D
                 } else if (!init) {
                     ld4(Xa + i * ldx + j0, xa[u]);
                 }
@@ -1877,7 +1896,7 @@ k_kkt_bulk(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, con
             x[0] = vx.x; x[1] = vx.y; x[2] = vx.z; x[3] = vx.w;
             if (c_avg) {
                 const float4 vb = *reinterpret_cast<const float4*>(stage + 2 * STRIP * 4 + lane * 16);
-                xb[0] = vb.x; xb[1] = vb.y; xb[2] = vb.z; xb[3] = vb.w;
+                xb[0] = x[0] + vb.x; xb[1] = x[1] + vb.y; xb[2] = x[2] + vb.z; xb[3] = x[3] + vb.w;   // X + D
             } else {
                 xb[0] = xb[1] = xb[2] = xb[3] = 0.f;
             }
@@ -1999,7 +2018,7 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         const double sf = A[1], sg = A[3];
         if (A[5] > 0.0 || !(fabs(sf - sg) <= 1e-9 * fmax(sf, 1.0))) {
             S->status = ST_ARG;
-            S->res_slot = S->cur;
+            S->res_slot = S->res_xslot = S->cur;
             return;
         }
     }
@@ -2011,7 +2030,7 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         // measures this check has just computed for it.
         report(S, c);
         S->status = ST_TIMEOUT;
-        S->res_slot = S->cur;
+        S->res_slot = S->res_xslot = S->cur;
         S->res_avg = 0;
         return;
     }
@@ -2019,8 +2038,8 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         report(S, c);
         S->kkt0 = c.kkt;
         S->kkt_prev = c.kkt;
-        if (!isfinite(c.kkt)) { S->status = ST_NUMERIC; S->res_slot = S->cur; S->res_avg = 0; }
-        else if (c.rel <= S->tol) { S->status = ST_OK; S->res_slot = S->cur; S->res_avg = 0; }
+        if (!isfinite(c.kkt)) { S->status = ST_NUMERIC; S->res_slot = S->res_xslot = S->cur; S->res_avg = 0; }
+        else if (c.rel <= S->tol) { S->status = ST_OK; S->res_slot = S->res_xslot = S->cur; S->res_avg = 0; }
         return;
     }
     if (S->k == 0) {
@@ -2028,7 +2047,7 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         if (S->passes >= S->max_passes) {
             report(S, c);
             S->status = ST_MAX_ITER;
-            S->res_slot = S->cur;
+            S->res_slot = S->res_xslot = S->cur;
             S->res_avg = 0;
         }
         return;
@@ -2038,7 +2057,7 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
     if (!isfinite(c.kkt) || !isfinite(b.kkt)) {
         report(S, c);
         S->status = ST_NUMERIC;
-        S->res_slot = S->cur;
+        S->res_slot = S->res_xslot = S->cur;
         S->res_avg = 0;
         return;
     }
@@ -2050,7 +2069,18 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
     if (kk.rel <= S->tol || S->passes >= S->max_passes) {
         S->status = kk.rel <= S->tol ? ST_OK : ST_MAX_ITER;
         S->res_slot = cand;
+        S->res_xslot = cand;
         S->res_avg = use_avg ? 1 : 0;
+        if (use_avg) {
+            // The reported plan X + D is formed into the free next slot, so
+            // the current plan, D and the anchor stay as they are (a solve
+            // stopped by its pass budget can be resumed from them).
+            S->fix = 1;
+            S->fix_x = S->cur;
+            S->fix_d = S->bar;
+            S->fix_dst = S->nxt;
+            S->res_xslot = S->nxt;
+        }
         return;
     }
     bool restart;
@@ -2071,6 +2101,15 @@ __device__ void finalize_check(Ctrl* S, const double* A, int mode) {
         const double dy = sqrt(use_avg ? A[5] : A[4]);
         if (dX > S->eps_zero && dy > S->eps_zero)
             S->omega = exp(S->theta * log(dy / dX) + (1.0 - S->theta) * log(S->omega));
+    }
+    if (use_avg) {
+        // Restart to the average: its slot becomes X + D in place before the
+        // next pass (the vector set of that slot already holds the averaged
+        // duals and the exact sums of X + D).
+        S->fix = 1;
+        S->fix_x = S->cur;
+        S->fix_d = cand;
+        S->fix_dst = cand;
     }
     S->cur = cand;
     S->anc = cand;
@@ -2335,6 +2374,59 @@ k_chunk_coop(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
 // ---------------------------------------------------------------------------
 // Snapshot of every resident instance's controller (one D2H copy per chunk)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Average plan forming (after every check): where the check picked the
+// running average (a restart to it, or the reported point), write
+// X[fix_dst] = X[fix_x] + X[fix_d] -- the current plan plus the stored
+// deviation, with the rounding the checks used for the same value.  One warp
+// per plan tile; instances without a request cost one controller read.
+// ---------------------------------------------------------------------------
+template <typename TX>
+__global__ void __launch_bounds__(TWARPS * 32)
+k_avgfix(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, const int* __restrict__ Tp) {
+    pdl_enter();
+    const int T = *Tp;
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)gridDim.x * TWARPS;
+    for (int t = (int)blockIdx.x * TWARPS + (int)(threadIdx.x >> 5); t < T; t += nw) {
+        const TileRef tr = tmap[t];
+        const Inst& I = insts[tr.inst];
+        const Ctrl& S = *I.ctrl;
+        if (!S.fix) continue;
+        const int strip = tr.local % I.nstrips, chunk = tr.local / I.nstrips;
+        const long long j0 = (long long)strip * STRIP + lane * 4;
+        if (j0 >= I.n) continue;
+        const long long i0 = (long long)chunk * I.tile_rows;
+        const long long i1 = min(i0 + (long long)I.tile_rows, I.m);
+        const TX* Xa = slot_x<TX>(I, S.fix_x);
+        const TX* Xd = slot_x<TX>(I, S.fix_d);
+        TX* Xo = slot_x<TX>(I, S.fix_dst);
+        for (long long i = i0; i < i1; ++i) {
+            TX a[4], d[4];
+            ld4(Xa + i * I.ldx + j0, a);
+            ld4(Xd + i * I.ldx + j0, d);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[e] = a[e] + d[e];
+            st4(Xo + i * I.ldx + j0, a);
+        }
+    }
+}
+
+// out = a + d over `count` elements (a multiple of 4): a plan formed from
+// the current plan and the average's deviation, for the host's copies.
+template <typename TX>
+__global__ void k_combine(const TX* __restrict__ a, const TX* __restrict__ d, TX* out, long long count) {
+    const long long stride = (long long)gridDim.x * blockDim.x * 4;
+    for (long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e < count; e += stride) {
+        TX x[4], y[4];
+        ld4(a + e, x);
+        ld4(d + e, y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = x[k] + y[k];
+        st4(out + e, x);
+    }
+}
+
 __global__ void k_snapshot(const Inst* __restrict__ insts, const int* __restrict__ count, Ctrl* out) {
     pdl_enter();
     const int n = *count;
@@ -2489,6 +2581,26 @@ int launch_checkvec(const Inst* d_insts, const TileRef* d_vmap, const int* NV, i
     if (blocks < 1) blocks = 1;
     return launch_k(cfg.pdl != 0, k_checkvec, (unsigned)blocks, VT, 0, (cudaStream_t)stream, d_insts, d_vmap, NV,
                     wctr, mode);
+}
+int launch_avgfix(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const LaunchCfg& cfg,
+                  void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (ttype == TT_F64)
+        return launch_k(cfg.pdl != 0, k_avgfix<double>, (unsigned)cfg.tile_blocks_f64, TWARPS * 32, 0, st, d_insts,
+                        d_tmap, T);
+    return launch_k(cfg.pdl != 0, k_avgfix<float>, (unsigned)cfg.tile_blocks, TWARPS * 32, 0, st, d_insts, d_tmap, T);
+}
+int launch_combine(int xtype, const void* a, const void* d, void* out, long long count, void* stream) {
+    if (count <= 0) return 0;
+    long long blocks = (count / 4 + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (xtype == 2)
+        k_combine<double><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+            static_cast<const double*>(a), static_cast<const double*>(d), static_cast<double*>(out), count);
+    else
+        k_combine<float><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+            static_cast<const float*>(a), static_cast<const float*>(d), static_cast<float*>(out), count);
+    return err(cudaGetLastError());
 }
 int launch_watchdog_selftest(long long limit, int* d_status, void* stream) {
     k_watchdog_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(limit, d_status);
