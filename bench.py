@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: the --serve-loads sweep)")
     ap.add_argument("--active-mb", type=float, default=400.0,
-                    help="serving: per-pass plan megabytes the active-budget engine advances together")
+                    help="serving: per-pass plan megabytes the active-budget engine advances together (0: skip that server)")
     ap.add_argument("--serve-loads", default="0.5,0.8,1.1",
                     help="offered loads as fractions of the one-at-a-time server's measured capacity")
     ap.add_argument("--serve-max", type=int, default=8192, help="largest m, n of served requests")
@@ -554,8 +554,10 @@ def run_serve(args):
         sb = serve.summary(rb, reqs)
         # the same engine with an active-bytes budget: the oldest solve keeps
         # the bandwidth, small ones fill in beside it
-        ra = serve.serve_batched(reqs, batch_active_bytes=int(args.active_mb * 1e6), **lim)
-        sa = serve.summary(ra, reqs)
+        sa = None
+        if args.active_mb > 0:
+            ra = serve.serve_batched(reqs, batch_active_bytes=int(args.active_mb * 1e6), **lim)
+            sa = serve.summary(ra, reqs)
         rp = serve.serve_plain(reqs, **lim)
         sp = serve.summary(rp, reqs)
         diffs = [abs(rb["obj"][k] - rp["obj"][k]) / max(abs(rp["obj"][k]), 1e-30) for k in rb["obj"]]
@@ -563,7 +565,7 @@ def run_serve(args):
                        "continuous_batching_active_budget": sa, "plain_fifo": sp,
                        "p50_ratio_plain_over_batched": sp["p50_s"] / sb["p50_s"],
                        "p99_ratio_plain_over_batched": sp["p99_s"] / sb["p99_s"],
-                       "p99_ratio_plain_over_active_budget": sp["p99_s"] / sa["p99_s"],
+                       "p99_ratio_plain_over_active_budget": sp["p99_s"] / sa["p99_s"] if sa else None,
                        "max_rel_obj_diff_vs_plain": float(np.max(diffs)) if diffs else None})
         print(json.dumps({"progress": points[-1]}), file=sys.stderr, flush=True)
     top = points[-1]

@@ -153,6 +153,9 @@ typedef struct {
     double hbm_bytes;       /* algorithmic plan-pass bytes moved */
     double rounded_obj;     /* <C, X_feas> of Algorithm 3 when round_plan = 1, else NaN */
     int32_t returned_average; /* 1 if the returned iterate is the running average */
+    int32_t tile_rows;      /* rows per plan tile the solve ran with (it fixes the FP32 summation
+                               order: a solve with the same tile_rows option and pass kernel takes
+                               the same passes and returns the same bits) */
 } pdot_result;
 
 typedef struct {

@@ -219,6 +219,7 @@ struct pdot_handle {
     long long chunk_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::map<long long, std::pair<int, int>> tune_cache;   // (m, n, ttype) -> (pass kernel, tile_rows)
     int autotune = 1;            // time pass-kernel candidates on a shape's first solve
+    int batch_min_rows = 16;     // smallest tile height of a batched instance (even)
     // host staging for pdot_solve_host
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -325,8 +326,19 @@ void validate_marginals(pdot_handle* h, long long m, long long n, const double* 
 int tile_rows_for(pdot_handle* h, long long m, long long n, int ttype, int kernel, bool batch, bool split = false) {
     if (h->opt.tile_rows > 0) return h->opt.tile_rows;
     const long long nstrips = (n + STRIP - 1) / STRIP;
-    if (batch) return 64;   // many instances share the tile queue: moderate tiles keep it balanced
     if (ttype == TT_F64) kernel = 0;
+    if (batch) {
+        // A batched instance's tiles depend on its own shape only, so its
+        // result is the same alone or in any mix: the split a single solve
+        // takes (one tile per resident warp, for a large instance running
+        // nearly alone at the end of a batch or in a sparse stream), but no
+        // fewer than batch_min_rows rows (in a crowded batch, per-tile costs
+        // stay small) and no more than 64.
+        long long tr = tile_rows_for(h, m, n, ttype, ttype == TT_F64 ? 0 : h->cfg_base.pass_bulk, false, true);
+        tr = std::max<long long>(tr, h->batch_min_rows);
+        tr = std::min<long long>(tr, 64);
+        return (int)tr;
+    }
     if (kernel == 2 && !split) return 32;   // grouped kernel: short tiles through the dynamic queue
     // Otherwise split the instance evenly over the resident warps, one tile
     // each (the last wave of a dynamic queue would leave a tail), as tall as
@@ -541,6 +553,7 @@ void fill_result(const Ctrl& S, pdot_result* r, pdot_status st) {
     r->eta = S.eta;
     r->omega = S.omega;
     r->returned_average = S.res_avg;
+    r->tile_rows = 0;   // set by the caller, which knows the workspace
 }
 
 pdot_status map_status(int st) {
@@ -906,6 +919,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     }
     const pdot_status st = map_status(S->status);
     fill_result(*S, res, st);
+    res->tile_rows = w.tile_rows;
     const double mn = (double)m * (double)n;
     const double bc = (double)csize_of(ctype), bx = (double)xsize_of(w.xtype);
     res->hbm_bytes = (double)S->passes * mn * (bc + 4.0 * bx) + (double)S->checks * mn * (bc + 3.0 * bx);
@@ -1311,6 +1325,7 @@ void batch_launch_chunk(pdot_handle* h) {
     const int types = B->types;
     h->cfg.gen_dims = B->gen_dims;
     h->cfg.comp = h->opt.compensated_cost != 0 ? 1 : 0;
+    h->cfg.pass_bulk = h->cfg_base.pass_bulk;   // the batch engine's pass kernel (its tiles were sized for it)
     long long tmaps = 0;
     for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
     const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->cnt.d,
@@ -1364,6 +1379,7 @@ pdot_result batch_result(pdot_handle* h, const BSlot* s, int status) {
     pdot_result r;
     memset(&r, 0, sizeof(r));
     fill_result(s->last, &r, map_status(status));
+    r.tile_rows = s->w.tile_rows;
     const double mn = (double)s->req.m * (double)s->req.n;
     const double bc = (double)csize_of(s->req.c_dtype), bx = (double)xsize_of(h->opt.x_dtype);
     r.hbm_bytes = (double)s->last.passes * mn * (bc + 4.0 * bx) + (double)s->last.checks * mn * (bc + 3.0 * bx);
@@ -1727,6 +1743,8 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
                 h->autotune = 0;   // an explicit kernel choice disables the tuner
             }
         }
+        const char* bm = getenv("PDOT_BATCH_MIN_ROWS");   // comparison runs only
+        if (bm && atoi(bm) >= 2 && atoi(bm) <= 64 && atoi(bm) % 2 == 0) h->batch_min_rows = atoi(bm);
         const char* at = getenv("PDOT_AUTOTUNE");
         if (at && atoi(at) == 0) h->autotune = 0;
         int l2 = 0;

@@ -81,6 +81,7 @@ class Result(ctypes.Structure):
         ("hbm_bytes", ctypes.c_double),
         ("rounded_obj", ctypes.c_double),
         ("returned_average", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -184,7 +184,9 @@ def test_solve_fp32_plan(s32, m, n, seed, marg):
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
     Co = _np(C)
     opt, *_ = oracle.exact_transport(Co, ins.f, ins.g)
-    for tol, bound in [(1e-4, 2e-3), (1e-6, 2e-5)]:
+    # Reading C19: a relative KKT of 1e-6 puts the objective within a few
+    # 1e-6 of the optimum (the FP64 oracle too); 1e-7 puts it within 1e-6.
+    for tol, bound in [(1e-4, 2e-3), (1e-6, 5e-6), (1e-7, 1e-6)]:
         sol = s32.solve(C, ins.f, ins.g, tol=tol)
         r = sol.result
         assert sol.status == pdot.OK, r

@@ -134,9 +134,12 @@ def test_points_solve_reaches_exact_optimum(s32, m, n, d, dist, div):
     opt, *_ = oracle.exact_transport(Co, f, g)
     sol = s32.solve(pdot.Points(xs, ys, dist, div), f, g, tol=1e-6)
     assert sol.status == pdot.OK, sol.result
-    assert abs(sol.result["primal_obj"] - opt) / opt < 2e-5
+    assert abs(sol.result["primal_obj"] - opt) / opt < 5e-6
     k = oracle.kkt(Co, f, g, _np(sol.X), _np(sol.p), _np(sol.q))
     assert k.rel_kkt <= 1.05e-6
+    # reading C19: at relative KKT 1e-7 the objective is within 1e-6
+    sol = s32.solve(pdot.Points(xs, ys, dist, div), f, g, tol=1e-7)
+    assert sol.status == pdot.OK and abs(sol.result["primal_obj"] - opt) / opt < 1e-6, sol.result
 
 
 def test_points_rounding_objective():
@@ -151,13 +154,12 @@ def test_points_rounding_objective():
 
 def test_points_batch_equals_single_solves():
     cases = [(150, 97, 3, "l1", 3.0), (64, 256, 2, "sqeuclid", 2.0), (200, 130, 8, "sqeuclid", 8.0)]
-    single = pdot.Solver(device=0, tile_rows=64, time_limit_s=120.0)
     bs = pdot.BatchSolver(device=0, time_limit_s=120.0)
-    want, tickets = {}, {}
+    costs, tickets = {}, {}
     for i, (m, n, d, dist, div) in enumerate(cases):
         xs, ys, f, g = _points(m, n, d, 300 + i)
         cost = pdot.Points(xs, ys, dist, div)
-        want[i] = single.solve(cost, f, g, tol=1e-6)
+        costs[i] = (cost, f, g)
         tickets[bs.submit(cost, f, g, tol=1e-6)] = i
         # a stored-cost request in the same batch
         ins = I.batch_instance(m, n, 400 + i)
@@ -167,7 +169,11 @@ def test_points_batch_equals_single_solves():
         assert res[tid].status == pdot.OK
         if i < 0:
             continue
-        a, b = res[tid], want[i]
+        # the single solve with the tile height and pass kernel the batch ran
+        single = pdot.Solver(device=0, tile_rows=res[tid].result["tile_rows"], pass_kernel=2, time_limit_s=120.0)
+        cost, f, g = costs[i]
+        a, b = res[tid], single.solve(cost, f, g, tol=1e-6)
+        single.close()
         assert a.result["passes"] == b.result["passes"] and a.result["primal_obj"] == b.result["primal_obj"]
         assert torch.equal(a.X, b.X) and torch.equal(a.p, b.p)
     bs.close()
