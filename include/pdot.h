@@ -134,6 +134,14 @@ typedef struct {
                                       0 = (C - (float)p) - (float)q; 2 (default) = 1 for instances of
                                       fewer than 4M plan entries and in the batch engine, 0 above.
                                       No effect on FP64 plans.  Other values: PDOT_ERR_ARG */
+    int32_t resident;              /* 1 (default) = an instance with an FP32 plan and a stored FP32 / BF16
+                                      cost whose plan and average fit the shared memory of one thread-block
+                                      cluster (8 CTAs; about 190k plan entries) runs in the resident kernel
+                                      where pass_kernel and tile_rows are 0 (in the batch engine: where
+                                      tile_rows is 0): the cluster keeps X and the average's
+                                      deviation on chip and runs whole check periods of Algorithm 2 in one
+                                      launch (pdot_solve, pdot_pdhg_steps and the batch engine); 0 = the
+                                      tile kernels for every instance.  Other values: PDOT_ERR_ARG */
 } pdot_options;
 
 typedef struct {
@@ -155,7 +163,8 @@ typedef struct {
     int32_t returned_average; /* 1 if the returned iterate is the running average */
     int32_t tile_rows;      /* rows per plan tile the solve ran with (it fixes the FP32 summation
                                order: a solve with the same tile_rows option and pass kernel takes
-                               the same passes and returns the same bits) */
+                               the same passes and returns the same bits); 0 when it ran in the
+                               resident kernel (whose order depends on the instance's shape only) */
 } pdot_result;
 
 typedef struct {
@@ -247,6 +256,14 @@ typedef struct {
 /* Bytes of a solver-state blob for an m x n solve with plans in x_dtype
  * (F32 or F64); 0 for invalid arguments.  Needs no GPU. */
 int64_t pdot_state_bytes(int64_t m, int64_t n, pdot_dtype x_dtype);
+
+/* 1 if an m x n instance's FP32 plan and the average's deviation fit the
+ * shared memory of one thread-block cluster of the resident kernel (8 CTAs,
+ * rows split evenly; each CTA holds its rows of both at 4 B per entry plus
+ * FP64 partial sums), else 0.  Whether such an instance runs resident also
+ * depends on the options (pdot_options.resident) and its cost type.  Needs
+ * no GPU. */
+int32_t pdot_resident_fits(int64_t m, int64_t n);
 
 /* pdot_solve from a starting point or a saved state (see pdot_start); start
  * may be NULL (then the same as pdot_solve). */

@@ -220,6 +220,9 @@ struct pdot_handle {
     std::map<long long, std::pair<int, int>> tune_cache;   // (m, n, ttype) -> (pass kernel, tile_rows)
     int autotune = 1;            // time pass-kernel candidates on a shape's first solve
     int batch_min_rows = 16;     // smallest tile height of a batched instance (even)
+    int res_clusters = 0;        // resident-kernel clusters the device holds at once (0: not available)
+    int* d_res1 = nullptr;       // {0, 1}: the list and count of a single-instance resident launch
+    bool res_on = false;         // the current single-instance call runs in the resident kernel
     // host staging for pdot_solve_host
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -485,12 +488,26 @@ void issue_chunk_kernels(pdot_handle* h, int ttype, int K) {
     run_avgfix(h, ttype);
 }
 
+// An instance runs in the resident kernel when the option allows it, the
+// device can hold its clusters, it has an FP32 plan and a stored FP32 / BF16
+// cost, and its plan and average fit a cluster's shared memory.
+bool resident_for(pdot_handle* h, long long m, long long n, int ttype) {
+    return h->opt.resident == 1 && h->opt.tile_rows == 0 && h->res_clusters > 0 && h->opt.x_dtype == PDOT_F32 &&
+           (ttype == TT_F32 || ttype == TT_BF16) && resident_fits(m, n);
+}
+
 bool use_coop(pdot_handle* h, int ttype) {
     return h->coop && h->cfg.coop_blocks > 0 && ttype != TT_F64 && ttype != TT_GEN && h->cfg.pass_bulk == 1;
 }
 
 void launch_chunk(pdot_handle* h, int ttype, int K) {
     const Work& w = h->ws;
+    if (h->res_on) {
+        // the whole check period (K passes and the check) in one resident launch
+        CKL(launch_resident(ttype, h->d_inst, h->d_res1, h->d_res1 + 1, 1, K, K, 0, h->cfg, h->stream));
+        launch_count(h, 1);
+        return;
+    }
     if (use_coop(h, ttype)) {
         CK(cudaMemsetAsync(h->wctr, 0, sizeof(unsigned) * WC_N, h->stream));
         CK(cudaMemsetAsync(h->d_gb, 0, sizeof(GridBar), h->stream));
@@ -840,6 +857,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     validate_marginals(h, m, n, f, g, false, &norm_b);
     const int ttype = ttype_of(ctype);
     autotune_pass(h, m, n, C, ctype, ldc, f, g);
+    h->res_on = h->opt.pass_kernel == 0 && resident_for(h, m, n, ttype);
     const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, ctype));
     ensure_work(h, m, n, h->opt.x_dtype, tr);
     ensure_maps(h);
@@ -857,7 +875,12 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
         // solve stopped at runs again with its restart logic.
         const bool replay = import_state(h, start->state_in, S);
         CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-        if (replay) {
+        if (replay && h->res_on) {
+            // the stopped check again, in the kernel that will run the solve
+            CKL(launch_resident(ttype, h->d_inst, h->d_res1, h->d_res1 + 1, 1, 0,
+                                std::max(1, h->opt.restart_check_every), 1, h->cfg, h->stream));
+            launch_count(h, 1);
+        } else if (replay) {
             run_check(h, ttype, MODE_CHECK);
             run_avgfix(h, ttype);
         }
@@ -919,7 +942,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     }
     const pdot_status st = map_status(S->status);
     fill_result(*S, res, st);
-    res->tile_rows = w.tile_rows;
+    res->tile_rows = h->res_on ? 0 : w.tile_rows;
     const double mn = (double)m * (double)n;
     const double bc = (double)csize_of(ctype), bx = (double)xsize_of(w.xtype);
     res->hbm_bytes = (double)S->passes * mn * (bc + 4.0 * bx) + (double)S->checks * mn * (bc + 3.0 * bx);
@@ -1067,6 +1090,7 @@ struct BSlot {
     bool timed_out = false;   // past its time limit: a stop request goes out before the next chunk
     bool stop_sent = false;   // that request has been issued
     bool fresh = true;        // admitted, init check not run yet
+    bool resident = false;    // runs in the resident kernel (its init check in the tile kernels)
     Ctrl last{};              // last snapshot of its controller
 };
 
@@ -1102,8 +1126,8 @@ struct DevArr {
 // Device count words of the batch engine: plan tiles per type, vector tiles,
 // instances, init-check plan tiles per type, init-check vector tiles, and two
 // pinned source words for status writes (cancel, time limit).
-constexpr int CNT_VEC = NTT, CNT_INST = NTT + 1, CNT_INIT = NTT + 2, CNT_INIT_VEC = 2 * NTT + 2, CNT_WORDS = 2 * NTT + 3,
-              CNT_TIMEOUT = 14, CNT_CANCEL = 15;
+constexpr int CNT_VEC = NTT, CNT_INST = NTT + 1, CNT_INIT = NTT + 2, CNT_INIT_VEC = 2 * NTT + 2,
+              CNT_RES = 2 * NTT + 3, CNT_WORDS = 2 * NTT + 5, CNT_TIMEOUT = 14, CNT_CANCEL = 15;
 static_assert(CNT_WORDS <= CNT_TIMEOUT, "count words overlap");
 
 struct BatchEngine {
@@ -1117,6 +1141,8 @@ struct BatchEngine {
     DevArr<TileRef> vmap;
     DevArr<TileRef> tmap_init[NTT];
     DevArr<TileRef> vmap_init;
+    DevArr<int> rlist[2];     // resident instances with FP32 / BF16 costs (indices into insts)
+    int res_grid[2] = {0, 0}; // cluster-count bound of each resident launch (bucketed)
     DevArr<Ctrl> snap[2];     // controller snapshots of the two chunks that can be in flight
     DevArr<Ctrl> ctrl_stage;
     DevArr<int> cnt;          // counts, laid out as the CNT_* indices below
@@ -1204,12 +1230,14 @@ void batch_compose(pdot_handle* h) {
             if (active[(size_t)i]) used += b;
         }
     }
-    size_t nt[NTT] = {}, nti[NTT] = {}, nv = 0, nvi = 0;
+    size_t nt[NTT] = {}, nti[NTT] = {}, nv = 0, nvi = 0, nr[2] = {0, 0};
     int gd = 0;
     B->types = 0;
     for (int i = 0; i < L; ++i) {
         BSlot* s = B->live[(size_t)i];
-        if (active[(size_t)i]) {
+        if (active[(size_t)i] && s->resident) {
+            nr[s->ttype == TT_BF16 ? 1 : 0] += 1;
+        } else if (active[(size_t)i]) {
             B->types |= 1 << s->ttype;
             if (s->req.c_dtype == PDOT_POINTS) gd = std::max(gd, (int)s->pts.d);
             nt[s->ttype] += (size_t)s->w.ntiles;
@@ -1226,6 +1254,8 @@ void batch_compose(pdot_handle* h) {
     }
     B->vmap.ensure(std::max<size_t>(nv, 1));
     B->vmap_init.ensure(std::max<size_t>(nvi, 1));
+    for (int r = 0; r < 2; ++r) B->rlist[r].ensure(std::max<size_t>(nr[r], 1));
+    size_t orr[2] = {0, 0};
     B->gen_dims = gd;
     size_t ot[NTT] = {}, oti[NTT] = {}, ov = 0, ovi = 0;
     for (int i = 0; i < L; ++i) {
@@ -1238,7 +1268,8 @@ void batch_compose(pdot_handle* h) {
         }
         B->insts.h[i] = make_inst(s->w, Cd, s->req.c_dtype, ldc, s->req.f, s->req.g);
         const int tt = s->ttype;
-        const bool act = active[(size_t)i] != 0;
+        const bool act = active[(size_t)i] != 0 && !s->resident;
+        if (active[(size_t)i] && s->resident) B->rlist[tt == TT_BF16 ? 1 : 0].h[orr[tt == TT_BF16 ? 1 : 0]++] = i;
         for (int t = 0; t < s->w.ntiles; ++t) {
             if (act) B->tmap[tt].h[ot[tt]++] = TileRef{i, t};
             if (s->fresh) B->tmap_init[tt].h[oti[tt]++] = TileRef{i, t};
@@ -1259,6 +1290,17 @@ void batch_compose(pdot_handle* h) {
     }
     if (ov) CK(cudaMemcpyAsync(B->vmap.d, B->vmap.h, sizeof(TileRef) * ov, cudaMemcpyHostToDevice, st));
     if (ovi) CK(cudaMemcpyAsync(B->vmap_init.d, B->vmap_init.h, sizeof(TileRef) * ovi, cudaMemcpyHostToDevice, st));
+    for (int r = 0; r < 2; ++r) {
+        if (orr[r]) CK(cudaMemcpyAsync(B->rlist[r].d, B->rlist[r].h, sizeof(int) * orr[r], cudaMemcpyHostToDevice, st));
+        B->cnt.h[CNT_RES + r] = (int)orr[r];
+        // grid bound, bucketed so the chunk graph is re-captured only when the bucket changes
+        int gb = 0;
+        if (orr[r]) {
+            gb = 4;
+            while (gb < (int)orr[r]) gb *= 2;
+        }
+        B->res_grid[r] = gb;
+    }
     B->cnt.h[CNT_VEC] = (int)ov;
     B->cnt.h[CNT_INST] = L;
     B->cnt.h[CNT_INIT_VEC] = (int)ovi;
@@ -1293,6 +1335,13 @@ void batch_issue_chunk(pdot_handle* h, int types) {
     const int checks = std::max(1, h->opt.chunk_checks);
     const cudaStream_t st = h->stream;
     const int nvh = std::max(1, B->nv_live);
+    for (int r = 0; r < 2; ++r) {
+        if (!B->res_grid[r]) continue;
+        // the resident instances' whole chunk (its check periods) in one launch
+        CKL(launch_resident(r ? TT_BF16 : TT_F32, B->insts.d, B->rlist[r].d, B->cnt.d + CNT_RES + r, B->res_grid[r],
+                            K * checks, K, 0, h->cfg, st));
+        launch_count(h, 1);
+    }
     for (int c = 0; c < checks; ++c) {
         for (int s = 0; s < K; ++s) {
             for (int t = 0; t < NTT; ++t) {
@@ -1330,8 +1379,10 @@ void batch_launch_chunk(pdot_handle* h) {
     for (int t = 0; t < NTT; ++t) tmaps ^= (long long)(uintptr_t)B->tmap[t].d << t;
     const long long key[8] = {(long long)(uintptr_t)B->insts.d, (long long)(uintptr_t)B->cnt.d,
                               (long long)(uintptr_t)B->vmap.d, tmaps,
-                              types | ((long long)B->nv_grid << 8) | ((long long)B->gen_dims << 48),
-                              h->opt.restart_check_every, h->opt.chunk_checks, h->cfg.comp};
+                              types | ((long long)B->gen_dims << 8) | ((long long)B->res_grid[0] << 16) |
+                                  ((long long)B->res_grid[1] << 40),
+                              h->opt.restart_check_every, h->opt.chunk_checks,
+                              h->cfg.comp | ((long long)B->nv_grid << 8)};
     if (!h->opt.use_graph) {
         batch_issue_chunk(h, types);
     } else {
@@ -1379,7 +1430,7 @@ pdot_result batch_result(pdot_handle* h, const BSlot* s, int status) {
     pdot_result r;
     memset(&r, 0, sizeof(r));
     fill_result(s->last, &r, map_status(status));
-    r.tile_rows = s->w.tile_rows;
+    r.tile_rows = s->resident ? 0 : s->w.tile_rows;
     const double mn = (double)s->req.m * (double)s->req.n;
     const double bc = (double)csize_of(s->req.c_dtype), bx = (double)xsize_of(h->opt.x_dtype);
     r.hbm_bytes = (double)s->last.passes * mn * (bc + 4.0 * bx) + (double)s->last.checks * mn * (bc + 3.0 * bx);
@@ -1615,6 +1666,8 @@ void batch_destroy(pdot_handle* h) {
     }
     B->vmap.release();
     B->vmap_init.release();
+    B->rlist[0].release();
+    B->rlist[1].release();
     B->snap[0].release();
     B->snap[1].release();
     B->ctrl_stage.release();
@@ -1663,6 +1716,7 @@ void pdot_default_options(pdot_options* o) {
     o->batch_active_bytes = 0;
     o->pass_kernel = 0;
     o->compensated_cost = 2;
+    o->resident = 1;
 }
 
 const char* pdot_status_str(pdot_status s) {
@@ -1697,6 +1751,7 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         }
         if (h->opt.pass_kernel < 0 || h->opt.pass_kernel > 3) throw ArgError{"pass_kernel must be in 0..3"};
         if (h->opt.compensated_cost < 0 || h->opt.compensated_cost > 2) throw ArgError{"compensated_cost must be in 0..2"};
+        if (h->opt.resident < 0 || h->opt.resident > 1) throw ArgError{"resident must be 0 or 1"};
         int ndev = 0;
         CK(cudaGetDeviceCount(&ndev));
         if (device < 0 || device >= ndev) throw ArgError{"no such CUDA device"};
@@ -1722,6 +1777,14 @@ pdot_status pdot_create(const pdot_options* opt, int device, void* cuda_stream, 
         const int grp = setup_group_pass();
         if (grp > 0) throw CudaError{(cudaError_t)grp};
         h->cfg.group_blocks = h->sm_count * (-grp);
+        const int rc = setup_resident();
+        if (rc > 0) throw CudaError{(cudaError_t)rc};
+        h->res_clusters = -rc;
+        {
+            const int one[2] = {0, 1};   // instance list [0] and count 1 of a single-instance resident launch
+            CK(cudaMalloc(&h->d_res1, sizeof(one)));
+            CK(cudaMemcpy(h->d_res1, one, sizeof(one), cudaMemcpyHostToDevice));
+        }
         const int kb = setup_kkt_bulk();
         if (kb > 0) throw CudaError{(cudaError_t)kb};
         h->cfg.kkt_blocks = h->sm_count * (-kb);
@@ -1810,6 +1873,7 @@ pdot_status pdot_destroy(pdot_handle* h) {
     if (h->d_cnt) cudaFree(h->d_cnt);
     if (h->d_gb) cudaFree(h->d_gb);
     if (h->d_tp) cudaFree(h->d_tp);
+    if (h->d_res1) cudaFree(h->d_res1);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1830,6 +1894,11 @@ int64_t pdot_state_bytes(int64_t m, int64_t n, pdot_dtype x_dtype) {
     if (m < 1 || n < 1 || m > (1LL << 31) / 2 || n > (1LL << 31) / 2) return 0;
     if (x_dtype != PDOT_F32 && x_dtype != PDOT_F64) return 0;
     return (int64_t)state_layout(m, n, x_dtype).total;
+}
+
+int32_t pdot_resident_fits(int64_t m, int64_t n) {
+    if (m < 1 || n < 1 || m > (1LL << 31) / 2 || n > (1LL << 31) / 2) return 0;
+    return resident_fits(m, n) ? 1 : 0;
 }
 
 pdot_status pdot_solve_from(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
@@ -1931,7 +2000,14 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
         CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
         upload_state(h, X, p, q);
         run_check(h, ttype, MODE_INIT);   // row/column sums of the starting plan
-        for (int64_t s = 0; s < k; ++s) run_step(h, ttype);
+        if (h->opt.pass_kernel == 0 && resident_for(h, m, n, ttype)) {
+            if (k > 0) {   // k steps in one resident launch, no check
+                CKL(launch_resident(ttype, h->d_inst, h->d_res1, h->d_res1 + 1, 1, (int)k, 0, 0, h->cfg, h->stream));
+                launch_count(h, 1);
+            }
+        } else {
+            for (int64_t s = 0; s < k; ++s) run_step(h, ttype);
+        }
         CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         if (S->status == ST_ARG) throw ArgError{"invalid marginals"};
@@ -2029,6 +2105,7 @@ pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int coun
                     s->req.ldc = 0;
                 }
                 s->ttype = ttype_of(r.c_dtype);
+                s->resident = resident_for(h, r.m, r.n, s->ttype);
                 s->bytes = slot_bytes(h, r, pick_tile_rows(h, r.m, r.n, s->ttype, true));
                 if (s->bytes > B->budget) {
                     for (BSlot* x : slots) delete x;

@@ -206,6 +206,18 @@ int launch_snapshot(const Inst* d_insts, const int* count, int max_count, Ctrl* 
 // instances of one tile type.
 int launch_avgfix(int ttype, const Inst* d_insts, const TileRef* d_tmap, const int* T, const LaunchCfg& cfg,
                   void* stream);
+// Resident solve (one thread-block cluster per instance, the plan held in
+// shared memory): instances list[0 .. *count) of FP32 plans with stored
+// FP32 / BF16 costs, each for up to `passes` passes with a check every K
+// (K <= 0: none), after a first check when `replay` is set; max_count bounds
+// *count (it sizes the grid).
+int launch_resident(int ttype, const Inst* d_insts, const int* list, const int* count, int max_count, int passes,
+                    int K, int replay, const LaunchCfg& cfg, void* stream);
+// Whether an m x n instance's plan fits a cluster's shared memory.
+bool resident_fits(long long m, long long n);
+// Shared-memory attribute of the resident kernel; -(clusters held at once),
+// 0 when it cannot run on this device, > 0 a CUDA error.
+int setup_resident();
 // out = a + d elementwise (count a multiple of 4; xtype 0 FP32, 2 FP64).
 int launch_combine(int xtype, const void* a, const void* d, void* out, long long count, void* stream);
 // One warp's bounded wait on a transfer that never comes; *d_status <- ST_DEVICE.

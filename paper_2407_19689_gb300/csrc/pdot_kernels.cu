@@ -2459,6 +2459,12 @@ __global__ void k_watchdog_selftest(long long limit, int* status) {
     if (lane == 0) *status = done ? ST_OK : ST_DEVICE;
 }
 
+}  // namespace pdot
+
+#include "pdot_resident.cuh"
+
+namespace pdot {
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -2695,6 +2701,51 @@ int setup_group_pass() {
                          (const void*)k_pass_group<unsigned short, GROUP_S, false>,
                          (const void*)k_pass_group<GenC4, GROUP_S, true>, (const void*)k_pass_group<GenC4, GROUP_S, false>};
     return setup_dyn(fns, 6, group_smem());
+}
+
+// Resident kernel: its shared-memory size, and how many of its clusters the
+// device holds at once (-count; 0: cannot run, a positive value: an error).
+int setup_resident() {
+    const void* fns[] = {(const void*)k_resident<float, false>, (const void*)k_resident<float, true>,
+                         (const void*)k_resident<unsigned short, false>, (const void*)k_resident<unsigned short, true>};
+    int r = 1 << 20;
+    for (const void* fn : fns) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, res::RSMEM);
+        if (e != cudaSuccess) return (int)e;
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3(res::RCS);
+        c.blockDim = dim3(res::RT);
+        c.dynamicSmemBytes = res::RSMEM;
+        int nc = 0;
+        e = cudaOccupancyMaxActiveClusters(&nc, fn, &c);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        if (nc < r) r = nc;
+    }
+    return -r;
+}
+bool resident_fits(long long m, long long n) { return res::fits(m, n); }
+int launch_resident(int ttype, const Inst* d_insts, const int* list, const int* count, int max_count, int passes,
+                    int K, int replay, const LaunchCfg& cfg, void* stream) {
+    if (max_count < 1) return 0;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const dim3 grid((unsigned)(res::RCS * max_count)), block(res::RT);
+    if (ttype == TT_BF16) {
+        if (cfg.comp)
+            k_resident<unsigned short, true><<<grid, block, res::RSMEM, st>>>(d_insts, list, count, passes, K, replay);
+        else
+            k_resident<unsigned short, false><<<grid, block, res::RSMEM, st>>>(d_insts, list, count, passes, K, replay);
+    } else if (ttype == TT_F32) {
+        if (cfg.comp)
+            k_resident<float, true><<<grid, block, res::RSMEM, st>>>(d_insts, list, count, passes, K, replay);
+        else
+            k_resident<float, false><<<grid, block, res::RSMEM, st>>>(d_insts, list, count, passes, K, replay);
+    } else {
+        return (int)cudaErrorInvalidValue;   // FP32 plans with stored FP32 / BF16 costs only
+    }
+    return err(cudaGetLastError());
 }
 
 int setup_kkt_bulk() {

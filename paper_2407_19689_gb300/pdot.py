@@ -57,6 +57,7 @@ class Options(ctypes.Structure):
         ("batch_active_bytes", ctypes.c_uint64),
         ("pass_kernel", ctypes.c_int32),
         ("compensated_cost", ctypes.c_int32),
+        ("resident", ctypes.c_int32),
     ]
 
 
@@ -138,7 +139,7 @@ class Start(ctypes.Structure):
 # Every symbol include/pdot.h declares (checked by the CPU tests).
 DECLARED = [
     "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
-    "pdot_solve_host", "pdot_solve_from", "pdot_state_bytes", "pdot_pdhg_steps", "pdot_kkt", "pdot_round",
+    "pdot_solve_host", "pdot_solve_from", "pdot_state_bytes", "pdot_resident_fits", "pdot_pdhg_steps", "pdot_kkt", "pdot_round",
     "pdot_batch_submit", "pdot_poll", "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass",
     "pdot_round_noalloc", "pdot_watchdog_selftest",
 ]
@@ -170,6 +171,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_solve_from": (i32, [H, i64, i64, vp, i32, i64, vp, vp, dbl, ctypes.POINTER(Start), vp, vp, vp,
                                   ctypes.POINTER(Result)]),
         "pdot_state_bytes": (i64, [i64, i64, i32]),
+        "pdot_resident_fits": (i32, [i64, i64]),
         "pdot_pdhg_steps": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i64, dbl, dbl, vp, vp, vp, vp, vp, vp]),
         "pdot_kkt": (i32, [H, i64, i64, vp, i32, i64, vp, vp, vp, vp, vp, ctypes.POINTER(KktParts)]),
         "pdot_round": (i32, [H, i64, i64, vp, vp, vp, vp]),
@@ -248,6 +250,10 @@ def pdot_solve_from(h, m, n, C, c_dtype, ldc, f, g, tol, start: Start | None, X_
 
 def pdot_state_bytes(m, n, x_dtype) -> int:
     return load().pdot_state_bytes(m, n, x_dtype)
+
+
+def pdot_resident_fits(m, n) -> int:
+    return load().pdot_resident_fits(m, n)
 
 
 def pdot_pdhg_steps(h, m, n, C, c_dtype, ldc, f, g, k, eta, omega, X, p, q, Xbar=0, pbar=0, qbar=0) -> int:

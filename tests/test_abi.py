@@ -115,16 +115,33 @@ def test_state_bytes_needs_no_gpu(lib):
 
 
 def test_option_ranges_are_checked_before_any_cuda_call(lib):
-    """pdot_create rejects a pass_kernel outside 0..3 and a compensated_cost
-    outside 0..2 (PDOT_ERR_ARG) before it touches a device; the defaults are
-    the autotuner's kernel and the size-dependent compensation."""
+    """pdot_create rejects a pass_kernel outside 0..3, a compensated_cost
+    outside 0..2 and a resident flag outside 0..1 (PDOT_ERR_ARG) before it
+    touches a device; the defaults are the autotuner's kernel, the
+    size-dependent compensation and the resident kernel where it fits."""
     import ctypes
     from paper_2407_19689_gb300 import pdot
     o = pdot.pdot_default_options()
-    assert o.pass_kernel == 0 and o.compensated_cost == 2
-    for field, bad in (("pass_kernel", 4), ("pass_kernel", -1), ("compensated_cost", 3)):
+    assert o.pass_kernel == 0 and o.compensated_cost == 2 and o.resident == 1
+    for field, bad in (("pass_kernel", 4), ("pass_kernel", -1), ("compensated_cost", 3), ("resident", 2)):
         o = pdot.pdot_default_options()
         setattr(o, field, bad)
         h = ctypes.c_void_p()
         assert lib.pdot_create(ctypes.byref(o), 0, None, ctypes.byref(h)) == pdot.ERR_ARG
         assert not h.value
+
+
+def test_resident_fit_rule_needs_no_gpu(lib):
+    """pdot_resident_fits: a plan and its average's deviation at 4 B each per
+    entry, split over the 8 CTAs of a cluster, must fit one CTA's shared
+    memory (with the FP64 partial sums): about 190k entries for square plans."""
+    from paper_2407_19689_gb300 import pdot
+    assert pdot.pdot_resident_fits(1, 1) == 1
+    assert pdot.pdot_resident_fits(430, 430) == 1
+    assert pdot.pdot_resident_fits(700, 700) == 0
+    assert pdot.pdot_resident_fits(60, 2100) == 1
+    assert pdot.pdot_resident_fits(0, 5) == 0 and pdot.pdot_resident_fits(5, -1) == 0
+    # monotone in each dimension
+    for n in (1, 100, 1000, 5000):
+        fits = [pdot.pdot_resident_fits(m, n) for m in range(1, 3000, 37)]
+        assert fits == sorted(fits, reverse=True)

@@ -36,20 +36,26 @@ def _same(a, b):
     assert torch.equal(a.X, b.X) and torch.equal(a.p, b.p) and torch.equal(a.q, b.q)
 
 
-def test_batch_equals_single_solves():
-    # The batch engine sizes each instance's tiles from its own shape (16 to
-    # 64 rows) and runs the per-row bulk pass kernel; a single solve with the
-    # same tile height and kernel reduces its partial sums in the same order
-    # and must match bit for bit.
-    batch = pdot.BatchSolver(device=0, time_limit_s=120.0)
+@pytest.mark.parametrize("resident", [1, 0])
+def test_batch_equals_single_solves(resident):
+    # Resident instances (a thread-block cluster each) compute in an order
+    # fixed by their shape; the others run in tiles the batch engine sizes
+    # from their shape (16 to 64 rows) with the per-row bulk pass kernel.  A
+    # single solve in the same kernel with the same tiles reduces in the same
+    # order and must match bit for bit.
+    batch = pdot.BatchSolver(device=0, time_limit_s=120.0, resident=resident)
     insts = [_inst(k) for k in range(12)]
     ids = [batch.submit(C, f, g, tol=1e-6) for C, f, g in insts]
     res = batch.run()
     assert sorted(res) == sorted(ids)
     for tid, (C, f, g) in zip(ids, insts):
         tr = res[tid].result["tile_rows"]
-        assert 16 <= tr <= 64 and tr % 2 == 0
-        single = pdot.Solver(device=0, time_limit_s=120.0, tile_rows=tr, pass_kernel=2)
+        if resident:
+            assert tr == 0   # every instance here fits a cluster
+            single = pdot.Solver(device=0, time_limit_s=120.0)
+        else:
+            assert 16 <= tr <= 64 and tr % 2 == 0
+            single = pdot.Solver(device=0, time_limit_s=120.0, tile_rows=tr, pass_kernel=2, resident=0)
         _same(res[tid], single.solve(C, f, g, tol=1e-6))
         single.close()
         opt, *_ = oracle.exact_transport(C.double().cpu().numpy(), f, g)

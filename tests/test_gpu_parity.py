@@ -85,7 +85,7 @@ def test_pdhg_steps_register_path(m, n, monkeypatch):
     """The register-pipelined pass kernel (selected with PDOT_PASS_BULK=0 when a
     handle is created) against the oracle, FP32 and BF16 costs."""
     monkeypatch.setenv("PDOT_PASS_BULK", "0")
-    s = pdot.Solver(device=0)
+    s = pdot.Solver(device=0, resident=0)
     ins = I.points_instance(m, n, 1500 + m)
     eta = 0.5 / math.sqrt(m + n)
     z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
@@ -195,6 +195,23 @@ def test_solve_fp32_plan(s32, m, n, seed, marg):
         assert k.rel_kkt <= 1.05 * tol, (k.rel_kkt, r["rel_kkt"])
 
 
+def test_fp32_running_average_keeps_the_fp64_pass_count(s32, s64):
+    """The running average of Algorithm 2 is held as its deviation from the
+    current plan, so an FP32 plan keeps the late iterates' weight 1/(k+1):
+    on a served request where an FP32 average updated in place needed about
+    four times the FP64 passes (158 x 3159, L1-type spread, tol 1e-6), the
+    FP32 solve stays within 1.5x of the FP64 one and reaches the same
+    objective to 5e-6 (both stop at relative KKT 1e-6, reading C19)."""
+    reqs = I.serve_requests(60, 1e9, I.seed_for(4), hi=4096)
+    r = [r for r in reqs if (r.m, r.n) == (158, 3159)][0]
+    ins = I.request_instance(r)
+    a = s32.solve(torch.tensor(ins.C, dtype=torch.float32, device=DEV), ins.f, ins.g, tol=r.tol)
+    b = s64.solve(torch.tensor(ins.C.astype(np.float32).astype(np.float64), device=DEV), ins.f, ins.g, tol=r.tol)
+    assert a.status == pdot.OK and b.status == pdot.OK
+    assert a.result["passes"] <= 1.5 * b.result["passes"], (a.result["passes"], b.result["passes"])
+    assert abs(a.result["primal_obj"] - b.result["primal_obj"]) <= 5e-6 * b.result["primal_obj"]
+
+
 def test_solve_is_deterministic(s32):
     ins = I.points_instance(150, 170, 21)
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
@@ -212,9 +229,9 @@ def test_cooperative_chunk_equals_graph_path(monkeypatch):
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
     monkeypatch.setenv("PDOT_PASS_BULK", "1")
     monkeypatch.setenv("PDOT_COOP", "1")
-    a = pdot.Solver(device=0, time_limit_s=120.0)
+    a = pdot.Solver(device=0, time_limit_s=120.0, resident=0)
     monkeypatch.setenv("PDOT_COOP", "0")
-    b = pdot.Solver(device=0, time_limit_s=120.0)
+    b = pdot.Solver(device=0, time_limit_s=120.0, resident=0)
     ra = a.solve(C, ins.f, ins.g, tol=1e-6)
     rb = b.solve(C, ins.f, ins.g, tol=1e-6)
     assert ra.status == rb.status == pdot.OK

@@ -108,12 +108,13 @@ def test_points_kkt_matches_oracle(s32, m, n, d, dist, div):
 def test_points_grid_solve_is_bit_identical_to_stored_cost(G):
     """Integer pixel coordinates: the generated squared distance divided by
     its maximum equals the stored FP32 cost entry exactly, so the two solves
-    take the same steps."""
+    take the same steps (both in the tile kernels: generated costs do not run
+    resident)."""
     ins = I.grid_blob_instance(G, I.seed_for(1, G))
     P = _grid(G)
     div = float(2 * (G - 1) ** 2)
     Cs = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
-    a = pdot.Solver(device=0, time_limit_s=120.0)
+    a = pdot.Solver(device=0, time_limit_s=120.0, resident=0)
     b = pdot.Solver(device=0, time_limit_s=120.0)
     ra = a.solve(Cs, ins.f, ins.g, tol=1e-6)
     rb = b.solve(pdot.Points(P, P, "sqeuclid", div), ins.f, ins.g, tol=1e-6)
