@@ -134,14 +134,16 @@ typedef struct {
                                       0 = (C - (float)p) - (float)q; 2 (default) = 1 for instances of
                                       fewer than 4M plan entries and in the batch engine, 0 above.
                                       No effect on FP64 plans.  Other values: PDOT_ERR_ARG */
-    int32_t resident;              /* 1 (default) = an instance with an FP32 plan and a stored FP32 / BF16
-                                      cost whose plan and average fit the shared memory of one thread-block
-                                      cluster (8 CTAs; about 190k plan entries) runs in the resident kernel
-                                      where pass_kernel and tile_rows are 0 (in the batch engine: where
-                                      tile_rows is 0): the cluster keeps X and the average's
-                                      deviation on chip and runs whole check periods of Algorithm 2 in one
-                                      launch (pdot_solve, pdot_pdhg_steps and the batch engine); 0 = the
-                                      tile kernels for every instance.  Other values: PDOT_ERR_ARG */
+    int32_t resident;              /* 1 = an instance with an FP32 plan and a stored FP32 / BF16 cost whose
+                                      plan and average fit the shared memory of one thread-block cluster
+                                      (8 CTAs; about 190k plan entries) runs in the resident kernel where
+                                      pass_kernel and tile_rows are 0 (in the batch engine: where tile_rows
+                                      is 0): the cluster keeps X and the average's deviation on chip and
+                                      runs whole check periods of Algorithm 2 in one launch (pdot_solve,
+                                      pdot_pdhg_steps and the batch engine); 0 (default) = the tile kernels
+                                      for every instance (measured faster on one GB300 for single solves
+                                      and for batches: the resident kernel computes an instance on 8 SMs
+                                      and sweeps the plan twice per pass).  Other values: PDOT_ERR_ARG */
 } pdot_options;
 
 typedef struct {

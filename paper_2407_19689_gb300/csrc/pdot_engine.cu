@@ -1716,7 +1716,7 @@ void pdot_default_options(pdot_options* o) {
     o->batch_active_bytes = 0;
     o->pass_kernel = 0;
     o->compensated_cost = 2;
-    o->resident = 1;
+    o->resident = 0;
 }
 
 const char* pdot_status_str(pdot_status s) {

@@ -52,7 +52,7 @@ struct Layout {
     long long rows;       // rows per CTA (rows_cta)
     long long ldx;
     int nstrips, nseg;
-    long long off_x, off_d, off_colseg, off_cols, off_rows, off_rowt, off_scal, off_ctrl, off_red, total;
+    long long off_x, off_d, off_colseg, off_cols, off_rows, off_rowt, off_scal, off_ctrl, off_red, off_prow, total;
 };
 
 __host__ __device__ inline long long al16(long long b) { return (b + 15) / 16 * 16; }
@@ -73,6 +73,7 @@ __host__ __device__ inline Layout layout(long long m, long long n) {
     L.off_scal = o;   o = al16(o + RSCAL * 8);                       // scalars read by the cluster
     L.off_ctrl = o;   o = al16(o + (long long)sizeof(Ctrl));         // this CTA's copy of the controller
     L.off_red = o;    o = al16(o + RW * RSCAL * 8);                  // per-warp scalar partials
+    L.off_prow = o;   o = al16(o + L.rows * 8);                      // the rows' duals, staged per sweep
     L.total = o;
     return L;
 }
@@ -100,13 +101,20 @@ __device__ __forceinline__ void block_sums(double* red, const double* v, int nv,
 }
 
 // The scalars every CTA published (scal[0..nv)), added in rank order; the
-// same values in every CTA.
-__device__ __forceinline__ void cluster_scalars(cg::cluster_group& cl, double* scal, int nv, double* out) {
-    for (int k = 0; k < nv; ++k) out[k] = 0.0;
-    for (unsigned r = 0; r < (unsigned)RCS; ++r) {
-        const double* rs = cl.map_shared_rank(scal, r);
-        for (int k = 0; k < nv; ++k) out[k] += rs[k];
+// same values in every CTA.  Called by all threads: RCS * nv of them fetch
+// one remote value each into buf (one round trip), then every thread adds
+// them in order into out.  Block barriers on both sides of the fetch.
+__device__ __forceinline__ void cluster_scalars(cg::cluster_group& cl, double* scal, int nv, double* buf,
+                                                double* out) {
+    const int t = threadIdx.x;
+    if (t < RCS * nv) buf[t] = cl.map_shared_rank(scal, (unsigned)(t / nv))[t % nv];
+    __syncthreads();
+    for (int k = 0; k < nv; ++k) {
+        double a = 0.0;
+        for (int r = 0; r < RCS; ++r) a += buf[r * nv + k];
+        out[k] = a;
     }
+    __syncthreads();
 }
 
 // Pointers and sizes of one CTA's part of an instance.
@@ -123,7 +131,46 @@ struct Part {
     double* rowt;
     double* scal;
     double* red;
+    float2* prow;                  // per row: (p_hi, p_lo) in a pass, (p, pbar) in a check
 };
+
+constexpr int RU = 4;   // rows whose loads a warp issues together
+
+// The duals of the CTA's rows, staged in shared memory for a sweep: (p_hi,
+// p_lo) of vector set vs (PAIR), or (p of vs, p of vb).  Block barriers on
+// both sides.
+__device__ __forceinline__ void stage_rows(const Part& P, const double* vs, const double* vb, bool pair, bool use_b) {
+    __syncthreads();
+    for (long long li = threadIdx.x; li < P.nr; li += RT) {
+        const double y = __ldcg(vs + P.r0 + li);
+        float2 v;
+        if (pair) {
+            split_dual(y, v.x, v.y);
+        } else {
+            v.x = (float)y;
+            v.y = use_b ? (float)__ldcg(vb + P.r0 + li) : 0.f;
+        }
+        P.prow[li] = v;
+    }
+    __syncthreads();
+}
+
+// The rows [a0, a1) of strip s that warp `unit` sweeps (see sweep_step).
+struct Unit {
+    int s, g;
+    long long a0, a1, j0;
+};
+__device__ __forceinline__ Unit unit_of(const Part& P, int unit, int lane) {
+    const int ns = P.L.nstrips, nseg = P.L.nseg;
+    Unit u;
+    u.s = unit % ns;
+    u.g = ns <= RW ? unit / ns : 0;
+    const long long seg_rows = (P.nr + nseg - 1) / nseg;
+    u.a0 = ns <= RW ? (long long)u.g * seg_rows : 0;
+    u.a1 = ns <= RW ? min(u.a0 + seg_rows, P.nr) : P.nr;
+    u.j0 = (long long)u.s * STRIP + lane * 4;
+    return u;
+}
 
 // One sweep over the CTA's rows with the plan step of Algorithm 2 at the
 // duals of vector set `vs` (p_i, q_j as FP32 hi/lo pairs, reading C9):
@@ -131,21 +178,18 @@ struct Part {
 //          ||d||^2 into *dx2 (per thread; added by the caller);
 //   WRITE: X <- X+, D <- (1 - w)(D - d) (D <- 0 on the first iterate).
 // Warp w takes strip w % nstrips and row segment w / nstrips (or, with more
-// strips than warps, strips w, w + RW, ... over all rows).
+// strips than warps, strips w, w + RW, ... over all rows), RU rows at a time.
 template <typename TC, bool CP, bool WRITE>
 __device__ __forceinline__ void sweep_step(const Part& P, const double* vs, float tau, float w, bool first,
                                            double* dx2) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int ns = P.L.nstrips, nseg = P.L.nseg;
-    const double* p = vs;
     const double* q = vs + P.m;
+    stage_rows(P, vs, nullptr, true, false);
     const int nunits = ns <= RW ? ns * nseg : ns;
     for (int unit = wp; unit < nunits; unit += RW) {
-        const int s = unit % ns, g = ns <= RW ? unit / ns : 0;
-        const long long seg_rows = (P.nr + nseg - 1) / nseg;
-        const long long a0 = ns <= RW ? (long long)g * seg_rows : 0;
-        const long long a1 = ns <= RW ? min(a0 + seg_rows, P.nr) : P.nr;
-        const long long j0 = (long long)s * STRIP + lane * 4;
+        const Unit U = unit_of(P, unit, lane);
+        const long long j0 = U.j0;
         const bool on = j0 < P.n;
         float qh[4], ql[4];
         bool valid[4];
@@ -159,52 +203,61 @@ __device__ __forceinline__ void sweep_step(const Part& P, const double* vs, floa
         double cs[4] = {0.0, 0.0, 0.0, 0.0};
         float dxa = 0.f;
         int nb = 0;
-        for (long long li = a0; li < a1; ++li) {
-            const long long i = P.r0 + li;
-            float ph, pl;
-            split_dual(__ldcg(p + i), ph, pl);
-            float c[4] = {0.f, 0.f, 0.f, 0.f}, x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (on) {
-                cr.get(i, c);
-                const float4 t = *reinterpret_cast<const float4*>(P.Xs + li * P.ldx + j0);
-                x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
-            }
-            float v[4], d[4], rs = 0.f;
+        for (long long lb = U.a0; lb < U.a1; lb += RU) {
+            float c[RU][4], x[RU][4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float R = reduced_cost(c[e], ph, pl, qh[e], ql[e], CP);
-                // one explicit FMA, so the accepting sweep recomputes the same bits
-                float vv = __fmaf_rn(-tau, R, x[e]);
-                vv = vv > 0.f ? vv : 0.f;
-                v[e] = valid[e] ? vv : 0.f;
-                d[e] = v[e] - x[e];
-                rs += d[e];
-            }
-            if (WRITE) {
-                if (on) {
-                    float4* dp = reinterpret_cast<float4*>(P.Ds + li * P.ldx + j0);
-                    const float4 od = *dp;
-                    const float o[4] = {od.x, od.y, od.z, od.w};
-                    float nd[4];
+            for (int u = 0; u < RU; ++u) {
+                const long long li = lb + u;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) nd[e] = avg_dev_next(first ? 0.f : o[e], d[e], w, first);
-                    *dp = make_float4(nd[0], nd[1], nd[2], nd[3]);
-                    *reinterpret_cast<float4*>(P.Xs + li * P.ldx + j0) = make_float4(v[0], v[1], v[2], v[3]);
+                for (int e = 0; e < 4; ++e) { c[u][e] = 0.f; x[u][e] = 0.f; }
+                if (on && li < U.a1) {
+                    cr.get(P.r0 + li, c[u]);
+                    const float4 t = *reinterpret_cast<const float4*>(P.Xs + li * P.ldx + j0);
+                    x[u][0] = t.x; x[u][1] = t.y; x[u][2] = t.z; x[u][3] = t.w;
                 }
-            } else {
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const long long li = lb + u;
+                if (li >= U.a1) break;
+                const float2 pp = P.prow[li];
+                float v[4], d[4], rs = 0.f;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    csa[e] += d[e];
-                    dxa += d[e] * d[e];
+                    const float R = reduced_cost(c[u][e], pp.x, pp.y, qh[e], ql[e], CP);
+                    // one explicit FMA, so the accepting sweep recomputes the same bits
+                    float vv = __fmaf_rn(-tau, R, x[u][e]);
+                    vv = vv > 0.f ? vv : 0.f;
+                    v[e] = valid[e] ? vv : 0.f;
+                    d[e] = v[e] - x[u][e];
+                    rs += d[e];
                 }
-                rs = warp_sum(rs);
-                if (lane == 0) P.rowp[(long long)s * P.L.rows + li] = (double)rs;
-                if (++nb == RFLUSH) {
+                if (WRITE) {
+                    if (on) {
+                        float4* dp = reinterpret_cast<float4*>(P.Ds + li * P.ldx + j0);
+                        const float4 od = *dp;
+                        const float o[4] = {od.x, od.y, od.z, od.w};
+                        float nd[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
-                    *dx2 += (double)dxa;
-                    dxa = 0.f;
-                    nb = 0;
+                        for (int e = 0; e < 4; ++e) nd[e] = avg_dev_next(first ? 0.f : o[e], d[e], w, first);
+                        *dp = make_float4(nd[0], nd[1], nd[2], nd[3]);
+                        *reinterpret_cast<float4*>(P.Xs + li * P.ldx + j0) = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        csa[e] += d[e];
+                        dxa += d[e] * d[e];
+                    }
+                    rs = warp_sum(rs);
+                    if (lane == 0) P.rowp[(long long)U.s * P.L.rows + li] = (double)rs;
+                    if (++nb == RFLUSH) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
+                        *dx2 += (double)dxa;
+                        dxa = 0.f;
+                        nb = 0;
+                    }
                 }
             }
         }
@@ -214,7 +267,7 @@ __device__ __forceinline__ void sweep_step(const Part& P, const double* vs, floa
             *dx2 += (double)dxa;
             if (on) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) P.colseg[(long long)g * P.ldx + j0 + e] = cs[e];
+                for (int e = 0; e < 4; ++e) P.colseg[(long long)U.g * P.ldx + j0 + e] = cs[e];
             }
         }
     }
@@ -226,86 +279,95 @@ __device__ __forceinline__ void sweep_step(const Part& P, const double* vs, floa
 // X + D with its duals (into e6[0..6), per thread), and the row sums / column
 // partials of X; with AVG = true only the row sums / column partials of
 // X + D.
+constexpr int RUC = 2;   // rows per load batch of a check sweep (more registers per row)
+
 template <typename TC, bool AVG>
 __device__ __forceinline__ void sweep_check(const Part& P, const double* Vc, const double* Vb, const float* Xa,
                                             bool avg, double* e6) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int ns = P.L.nstrips, nseg = P.L.nseg;
+    if (!AVG) stage_rows(P, Vc, Vb, false, avg);
     const int nunits = ns <= RW ? ns * nseg : ns;
     for (int unit = wp; unit < nunits; unit += RW) {
-        const int s = unit % ns, g = ns <= RW ? unit / ns : 0;
-        const long long seg_rows = (P.nr + nseg - 1) / nseg;
-        const long long a0 = ns <= RW ? (long long)g * seg_rows : 0;
-        const long long a1 = ns <= RW ? min(a0 + seg_rows, P.nr) : P.nr;
-        const long long j0 = (long long)s * STRIP + lane * 4;
+        const Unit U = unit_of(P, unit, lane);
+        const long long j0 = U.j0;
         const bool on = j0 < P.n;
         float qv[4], qbv[4];
         bool valid[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             valid[e] = j0 + e < P.n;
-            qv[e] = valid[e] ? (float)__ldcg(Vc + P.m + j0 + e) : 0.f;
-            qbv[e] = (valid[e] && avg) ? (float)__ldcg(Vb + P.m + j0 + e) : 0.f;
+            qv[e] = (!AVG && valid[e]) ? (float)__ldcg(Vc + P.m + j0 + e) : 0.f;
+            qbv[e] = (!AVG && valid[e] && avg) ? (float)__ldcg(Vb + P.m + j0 + e) : 0.f;
         }
         const CostRow<TC, float> cr(*P.I, j0);
         float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float csa[4] = {0.f, 0.f, 0.f, 0.f};
         double cs[4] = {0.0, 0.0, 0.0, 0.0};
         int nb = 0;
-        for (long long li = a0; li < a1; ++li) {
-            const long long i = P.r0 + li;
-            float c[4] = {0.f, 0.f, 0.f, 0.f}, x[4] = {0.f, 0.f, 0.f, 0.f}, dd[4] = {0.f, 0.f, 0.f, 0.f},
-                  xa[4] = {0.f, 0.f, 0.f, 0.f};
-            if (on) {
-                if (!AVG) cr.get(i, c);
-                const float4 tx = *reinterpret_cast<const float4*>(P.Xs + li * P.ldx + j0);
-                x[0] = tx.x; x[1] = tx.y; x[2] = tx.z; x[3] = tx.w;
-                if (AVG || avg) {
-                    const float4 td = *reinterpret_cast<const float4*>(P.Ds + li * P.ldx + j0);
-                    dd[0] = td.x; dd[1] = td.y; dd[2] = td.z; dd[3] = td.w;
-                }
-                if (!AVG) {
-                    const float4 ta = __ldcg(reinterpret_cast<const float4*>(Xa + i * P.ldx + j0));
-                    xa[0] = ta.x; xa[1] = ta.y; xa[2] = ta.z; xa[3] = ta.w;
-                }
-            }
-            const float pv = AVG ? 0.f : (float)__ldcg(Vc + i);
-            const float pbv = (!AVG && avg) ? (float)__ldcg(Vb + i) : 0.f;
-            float rs = 0.f;
+        for (long long lb = U.a0; lb < U.a1; lb += RUC) {
+            float c[RUC][4], x[RUC][4], dd[RUC][4], xa[RUC][4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (!valid[e]) continue;
-                const float xb = x[e] + dd[e];   // the average: X + D
-                if (AVG) {
-                    rs += xb;
-                    csa[e] += xb;
-                } else {
-                    const float Rc = (c[e] - pv) - qv[e];
-                    t[0] += c[e] * x[e];
-                    t[1] += Rc < 0.f ? Rc * Rc : 0.f;            // [p + q - C]^+ squared
-                    const float da = x[e] - xa[e];
-                    t[4] += da * da;
-                    if (avg) {
-                        const float Rb = (c[e] - pbv) - qbv[e];
-                        t[2] += c[e] * xb;
-                        t[3] += Rb < 0.f ? Rb * Rb : 0.f;
-                        const float db = xb - xa[e];
-                        t[5] += db * db;
+            for (int u = 0; u < RUC; ++u) {
+                const long long li = lb + u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { c[u][e] = 0.f; x[u][e] = 0.f; dd[u][e] = 0.f; xa[u][e] = 0.f; }
+                if (on && li < U.a1) {
+                    const long long i = P.r0 + li;
+                    if (!AVG) cr.get(i, c[u]);
+                    const float4 tx = *reinterpret_cast<const float4*>(P.Xs + li * P.ldx + j0);
+                    x[u][0] = tx.x; x[u][1] = tx.y; x[u][2] = tx.z; x[u][3] = tx.w;
+                    if (AVG || avg) {
+                        const float4 td = *reinterpret_cast<const float4*>(P.Ds + li * P.ldx + j0);
+                        dd[u][0] = td.x; dd[u][1] = td.y; dd[u][2] = td.z; dd[u][3] = td.w;
                     }
-                    rs += x[e];
-                    csa[e] += x[e];
+                    if (!AVG) {
+                        const float4 ta = __ldcg(reinterpret_cast<const float4*>(Xa + i * P.ldx + j0));
+                        xa[u][0] = ta.x; xa[u][1] = ta.y; xa[u][2] = ta.z; xa[u][3] = ta.w;
+                    }
                 }
             }
-            rs = warp_sum(rs);
-            if (lane == 0) P.rowp[(long long)s * P.L.rows + li] = (double)rs;
-            if (++nb == RFLUSH) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
-                if (!AVG) {
+            for (int u = 0; u < RUC; ++u) {
+                const long long li = lb + u;
+                if (li >= U.a1) break;
+                const float2 pp = AVG ? make_float2(0.f, 0.f) : P.prow[li];   // (p, pbar) of the row
+                float rs = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) { e6[k] += (double)t[k]; t[k] = 0.f; }
+                for (int e = 0; e < 4; ++e) {
+                    if (!valid[e]) continue;
+                    const float xb = x[u][e] + dd[u][e];   // the average: X + D
+                    if (AVG) {
+                        rs += xb;
+                        csa[e] += xb;
+                    } else {
+                        const float Rc = (c[u][e] - pp.x) - qv[e];
+                        t[0] += c[u][e] * x[u][e];
+                        t[1] += Rc < 0.f ? Rc * Rc : 0.f;            // [p + q - C]^+ squared
+                        const float da = x[u][e] - xa[u][e];
+                        t[4] += da * da;
+                        if (avg) {
+                            const float Rb = (c[u][e] - pp.y) - qbv[e];
+                            t[2] += c[u][e] * xb;
+                            t[3] += Rb < 0.f ? Rb * Rb : 0.f;
+                            const float db = xb - xa[u][e];
+                            t[5] += db * db;
+                        }
+                        rs += x[u][e];
+                        csa[e] += x[u][e];
+                    }
                 }
-                nb = 0;
+                rs = warp_sum(rs);
+                if (lane == 0) P.rowp[(long long)U.s * P.L.rows + li] = (double)rs;
+                if (++nb == RFLUSH) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) { cs[e] += (double)csa[e]; csa[e] = 0.f; }
+                    if (!AVG) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) { e6[k] += (double)t[k]; t[k] = 0.f; }
+                    }
+                    nb = 0;
+                }
             }
         }
 #pragma unroll
@@ -316,7 +378,7 @@ __device__ __forceinline__ void sweep_check(const Part& P, const double* Vc, con
         }
         if (on) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) P.colseg[(long long)g * P.ldx + j0 + e] = cs[e];
+            for (int e = 0; e < 4; ++e) P.colseg[(long long)U.g * P.ldx + j0 + e] = cs[e];
         }
     }
 }
@@ -413,10 +475,10 @@ __device__ __forceinline__ void resident_check(cg::cluster_group& cl, const Part
     block_sums(P.red, A, 12, P.scal);
     cl.sync();   // every CTA's check scalars
     const long long restarts0 = S->restarts;
-    if (tid == 0) {
+    {
         double B[12];
-        cluster_scalars(cl, P.scal, 12, B);
-        finalize_check(S, B, MODE_CHECK);
+        cluster_scalars(cl, P.scal, 12, P.red, B);
+        if (tid == 0) finalize_check(S, B, MODE_CHECK);
     }
     __syncthreads();
     const bool fix = S->fix != 0, in_place = S->fix_dst == S->fix_d;
@@ -477,6 +539,7 @@ k_resident(const Inst* __restrict__ insts, const int* __restrict__ list, const i
     P.rowt = reinterpret_cast<double*>(smem + P.L.off_rowt);
     P.scal = reinterpret_cast<double*>(smem + P.L.off_scal);
     P.red = reinterpret_cast<double*>(smem + P.L.off_red);
+    P.prow = reinterpret_cast<float2*>(smem + P.L.off_prow);
     Ctrl* S = reinterpret_cast<Ctrl*>(smem + P.L.off_ctrl);
     const int tid = threadIdx.x;
 
@@ -511,6 +574,9 @@ k_resident(const Inst* __restrict__ insts, const int* __restrict__ list, const i
         const double sigma = S->sigma, wavg = S->wavg;
         const long long k0 = S->k;
         const bool first = k0 == 0;
+        // the step-size schedule factors, requested now (used after the sweeps)
+        SchedFactors fac = {0.0, 0.0};
+        if (tid == 0 && S->adaptive_step) fac = sched_factors(S, S->total);
         double dx2 = 0.0;
         sweep_step<TC, CP, false>(P, Vc, tau, wf, first, &dx2);
         combine_sums(P);
@@ -534,12 +600,10 @@ k_resident(const Inst* __restrict__ insts, const int* __restrict__ list, const i
             block_sums(P.red, v3, 3, P.scal);
         }
         cl.sync();   // every CTA's step scalars (and its p+, q+) are written
-        if (tid == 0) {
+        {
             double tot[3];
-            cluster_scalars(cl, P.scal, 3, tot);
-            SchedFactors fac = {0.0, 0.0};
-            if (S->adaptive_step) fac = sched_factors(S, S->total);
-            finalize_step(S, tot[2], tot[0], tot[1], fac, 1.0 / (double)(k0 + 2));
+            cluster_scalars(cl, P.scal, 3, P.red, tot);
+            if (tid == 0) finalize_step(S, tot[2], tot[0], tot[1], fac, 1.0 / (double)(k0 + 2));
         }
         __syncthreads();
         if (S->status != ST_RUNNING) break;

@@ -118,11 +118,11 @@ def test_option_ranges_are_checked_before_any_cuda_call(lib):
     """pdot_create rejects a pass_kernel outside 0..3, a compensated_cost
     outside 0..2 and a resident flag outside 0..1 (PDOT_ERR_ARG) before it
     touches a device; the defaults are the autotuner's kernel, the
-    size-dependent compensation and the resident kernel where it fits."""
+    size-dependent compensation and the tile kernels."""
     import ctypes
     from paper_2407_19689_gb300 import pdot
     o = pdot.pdot_default_options()
-    assert o.pass_kernel == 0 and o.compensated_cost == 2 and o.resident == 1
+    assert o.pass_kernel == 0 and o.compensated_cost == 2 and o.resident == 0
     for field, bad in (("pass_kernel", 4), ("pass_kernel", -1), ("compensated_cost", 3), ("resident", 2)):
         o = pdot.pdot_default_options()
         setattr(o, field, bad)

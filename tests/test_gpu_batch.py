@@ -52,7 +52,7 @@ def test_batch_equals_single_solves(resident):
         tr = res[tid].result["tile_rows"]
         if resident:
             assert tr == 0   # every instance here fits a cluster
-            single = pdot.Solver(device=0, time_limit_s=120.0)
+            single = pdot.Solver(device=0, time_limit_s=120.0, resident=1)
         else:
             assert 16 <= tr <= 64 and tr % 2 == 0
             single = pdot.Solver(device=0, time_limit_s=120.0, tile_rows=tr, pass_kernel=2, resident=0)

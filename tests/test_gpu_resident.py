@@ -1,6 +1,6 @@
-"""The resident kernel (one thread-block cluster per instance, the plan and
-the average's deviation in shared memory, whole check periods of
-Algorithm 2 per launch), on the GPU:
+"""The resident kernel (pdot_options.resident = 1: one thread-block cluster
+per instance, the plan and the average's deviation in shared memory, whole
+check periods of Algorithm 2 per launch), on the GPU:
 
 - k steps of Algorithm 2 against the FP64 oracle, element by element, on
   shapes with fewer rows than CTAs, one column, ragged column strips and the
@@ -53,7 +53,6 @@ SHAPES = [(5, 300), (700, 1), (130, 517), (60, 2100), (430, 430)]
 @pytest.mark.parametrize("k", [1, 37])
 def test_resident_steps_match_oracle(m, n, k):
     ins = I.points_instance(m, n, 3100 + m + n)
-    s = pdot.Solver(device=0)
     res = pdot.Solver(device=0, resident=1)
     assert pdot.pdot_resident_fits(m, n) == 1
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
@@ -68,14 +67,13 @@ def test_resident_steps_match_oracle(m, n, k):
             a = _np(a)
             scale = max(float(np.max(np.abs(b))), 1e-300)
             assert float(np.max(np.abs(a - b))) <= 1e-5 * scale, (name, start)
-    s.close()
     res.close()
 
 
 def test_resident_steps_bf16_cost():
     m, n = 200, 333
     ins = I.points_instance(m, n, 3300)
-    s = pdot.Solver(device=0)
+    s = pdot.Solver(device=0, resident=1)
     C = torch.tensor(ins.C, dtype=torch.bfloat16, device=DEV)
     z = (np.zeros((m, n)), np.zeros(m), np.zeros(n))
     eta = 0.5 / math.sqrt(m + n)
@@ -93,8 +91,8 @@ def test_resident_solve_reaches_exact_optimum(m, n, seed):
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
     Co = _np(C)
     opt, *_ = oracle.exact_transport(Co, ins.f, ins.g)
-    r1 = pdot.Solver(device=0, time_limit_s=120.0)
-    r0 = pdot.Solver(device=0, time_limit_s=120.0, resident=0)
+    r1 = pdot.Solver(device=0, time_limit_s=120.0, resident=1)
+    r0 = pdot.Solver(device=0, time_limit_s=120.0)
     for tol, bound in [(1e-6, 5e-6), (1e-7, 1e-6)]:
         a = r1.solve(C, ins.f, ins.g, tol=tol)
         b = r0.solve(C, ins.f, ins.g, tol=tol)
@@ -117,7 +115,7 @@ def test_resident_solve_reaches_exact_optimum(m, n, seed):
 def test_resident_fit_rule():
     """A plan that fits a cluster runs resident (tile_rows 0); one that does
     not runs in tiles."""
-    s = pdot.Solver(device=0, time_limit_s=60.0, max_iter=64)
+    s = pdot.Solver(device=0, time_limit_s=60.0, max_iter=64, resident=1)
     big = (700, 700)
     assert pdot.pdot_resident_fits(*big) == 0
     for (m, n), resident in [((200, 200), True), (big, False)]:
@@ -131,12 +129,12 @@ def test_resident_fit_rule():
 def test_resident_solve_is_deterministic_and_resumable():
     ins = I.points_instance(150, 170, 3600)
     C = torch.tensor(ins.C, dtype=torch.float32, device=DEV)
-    s = pdot.Solver(device=0, time_limit_s=120.0)
+    s = pdot.Solver(device=0, time_limit_s=120.0, resident=1)
     a = s.solve(C, ins.f, ins.g, tol=1e-6)
     b = s.solve(C, ins.f, ins.g, tol=1e-6)
     assert a.result["passes"] == b.result["passes"] and torch.equal(a.X, b.X) and torch.equal(a.p, b.p)
     budget = max(64, (a.result["passes"] // 128) * 64)
-    s1 = pdot.Solver(device=0, max_iter=budget)
+    s1 = pdot.Solver(device=0, max_iter=budget, resident=1)
     blob = torch.empty(s1.state_bytes(150, 170), dtype=torch.uint8, device=DEV)
     part = s1.solve(C, ins.f, ins.g, tol=1e-6, state_out=blob)
     assert part.status == pdot.MAX_ITER
@@ -154,14 +152,14 @@ def test_resident_and_tile_instances_mixed_in_a_batch():
         ins = I.points_instance(m, n, 3700 + k, marginals="dirichlet")
         dt = torch.bfloat16 if k == 4 else torch.float32
         reqs.append((torch.tensor(ins.C, dtype=dt, device=DEV), ins.f, ins.g))
-    mix = pdot.BatchSolver(device=0, time_limit_s=120.0)
+    mix = pdot.BatchSolver(device=0, time_limit_s=120.0, resident=1)
     ids = [mix.submit(C, f, g, tol=1e-6) for C, f, g in reqs]
     rm = mix.run()
     mix.close()
     heights = [rm[t].result["tile_rows"] for t in ids]
     assert heights[2] > 0 and heights[0] == 0 and heights[4] == 0
     for tid, (C, f, g) in zip(ids, reqs):
-        alone = pdot.BatchSolver(device=0, time_limit_s=120.0)
+        alone = pdot.BatchSolver(device=0, time_limit_s=120.0, resident=1)
         t2 = alone.submit(C, f, g, tol=1e-6)
         ra = alone.run()[t2]
         alone.close()
