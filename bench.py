@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--pass-kernel", type=int, default=0,
                     help="plan-pass kernel (pdot_options.pass_kernel; 0: the autotuner's choice) -- for profiling")
     ap.add_argument("--tile-rows", type=int, default=0, help="rows per plan tile (0: by shape) -- for profiling")
+    ap.add_argument("--resident", type=int, default=0, choices=[0, 1],
+                    help="grid workload: solve in the resident kernel where the plan fits (pdot_options.resident) "
+                         "-- for profiling")
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched-vs-plain record (256 uneven instances) out of the default line")
     ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
@@ -314,7 +317,7 @@ def run_ours(args):
     X = torch.empty((m, n), dtype=torch.float32, device=dev)
     p = torch.empty(m, dtype=torch.float64, device=dev)
     q = torch.empty(n, dtype=torch.float64, device=dev)
-    solver = pdot.Solver(device=local, pass_kernel=args.pass_kernel, tile_rows=args.tile_rows)
+    solver = pdot.Solver(device=local, pass_kernel=args.pass_kernel, tile_rows=args.tile_rows, resident=args.resident)
     h = solver.h
 
     def solve_once():
