@@ -338,9 +338,8 @@ pdot_status pdot_batch_pending(pdot_handle *h, int *queued, int *running);
  *   synchronises.
  *   Limits: 1 <= m, n <= 32768 and x_dtype F32 or F64, else PDOT_ERR_ARG.
  *   The first call on a device looks up the array's device address (once per
- *   device); make that first call before any stream capture.  The address is
- *   kept for the life of the process, so calls on a device after a
- *   cudaDeviceReset of it are not supported.
+ *   device).  The address is kept for the life of the process, so calls on a
+ *   device after a cudaDeviceReset of it are not supported.
  *   All calls share the one array: the library runs one call per device at
  *   a time (a lock held until the call's stream synchronises, on error paths
  *   too), so calls from several host threads or on several streams wait for
