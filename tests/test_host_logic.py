@@ -204,6 +204,20 @@ def test_oracle_sample_times_whole_check_periods():
     assert 0.0 < t < 1.0
 
 
+def test_cpu_baseline_runs_one_oracle_copy_per_core():
+    """The CPU baseline of the default line runs the unchanged oracle as
+    independent copies, one per host core, in spawned processes (no GPU code
+    in them), and adds their solves/s; the one-core figure is reported
+    beside it."""
+    import bench
+    rec = bench.cpu_record(4, 1e-4, 500, "solves/s", 2)
+    assert rec["kind"] == "oracle" and rec["cores"] == 2
+    assert rec["value"] > 0 and rec["one_core_value"] > 0   # (a 16 x 16 sample is too short to compare)
+    assert "2 concurrent copies" in rec["sample"]
+    one = bench.cpu_record(4, 1e-4, 500, "solves/s", 1)
+    assert one["cores"] == 1 and one["value"] == one["one_core_value"]
+
+
 def test_reference_arm_prints_the_contract_line():
     """`bench.py --impl reference` (the FP64 oracle on the host) prints one
     JSON line with the keys the harness reads; a 16 x 16 grid keeps it short."""
