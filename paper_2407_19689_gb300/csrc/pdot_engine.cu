@@ -21,6 +21,14 @@
 #include "../../include/pdot.h"
 #include "pdot_internal.h"
 
+// NVTX ranges (header-only NVTX v3) name the phases of a solve and of the
+// batch engine for profilers (Nsight Systems, ncu --nvtx).  With no tool
+// attached a push or pop is one call through a no-op function pointer.
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define PDOT_HAVE_NVTX 1
+#endif
+
 using namespace pdot;
 
 namespace pdot {
@@ -55,6 +63,24 @@ struct CudaError {
 
 struct ArgError {
     const char* what;
+};
+
+// A host-thread NVTX range for the lifetime of the object.
+struct Range {
+    explicit Range(const char* name) {
+#ifdef PDOT_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~Range() {
+#ifdef PDOT_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -856,7 +882,10 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     double norm_b = 0.0;
     validate_marginals(h, m, n, f, g, false, &norm_b);
     const int ttype = ttype_of(ctype);
-    autotune_pass(h, m, n, C, ctype, ldc, f, g);
+    {
+        const Range r_("autotune");
+        autotune_pass(h, m, n, C, ctype, ldc, f, g);
+    }
     h->res_on = h->opt.pass_kernel == 0 && resident_for(h, m, n, ttype);
     const int tr = pick_tile_rows(h, m, n, ttype, false, gen_dims_of(C, ctype));
     ensure_work(h, m, n, h->opt.x_dtype, tr);
@@ -870,24 +899,27 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     Ctrl* S = h->h_ctrl;
     init_ctrl(h, S, m, n, tol, norm_b, 0.0, false, 0.0, 0.0);   // norms: computed by the init check
     CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), h->stream));
-    if (start && start->state_in) {
-        // Resume: the saved state, the handle's options; the check the saved
-        // solve stopped at runs again with its restart logic.
-        const bool replay = import_state(h, start->state_in, S);
-        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-        if (replay && h->res_on) {
-            // the stopped check again, in the kernel that will run the solve
-            CKL(launch_resident(ttype, h->d_inst, h->d_res1, h->d_res1 + 1, 1, 0,
-                                std::max(1, h->opt.restart_check_every), 1, h->cfg, h->stream));
-            launch_count(h, 1);
-        } else if (replay) {
-            run_check(h, ttype, MODE_CHECK);
-            run_avgfix(h, ttype);
+    {
+        const Range r_("start");   // the init check, or the replayed check of a resumed solve
+        if (start && start->state_in) {
+            // Resume: the saved state, the handle's options; the check the saved
+            // solve stopped at runs again with its restart logic.
+            const bool replay = import_state(h, start->state_in, S);
+            CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+            if (replay && h->res_on) {
+                // the stopped check again, in the kernel that will run the solve
+                CKL(launch_resident(ttype, h->d_inst, h->d_res1, h->d_res1 + 1, 1, 0,
+                                    std::max(1, h->opt.restart_check_every), 1, h->cfg, h->stream));
+                launch_count(h, 1);
+            } else if (replay) {
+                run_check(h, ttype, MODE_CHECK);
+                run_avgfix(h, ttype);
+            }
+        } else {
+            CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+            upload_start(h, start);   // X = 0, p = q = 0 (C1) unless a starting point is given
+            run_check(h, ttype, MODE_INIT);
         }
-    } else {
-        CK(cudaMemcpyAsync(w.ctrl, S, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-        upload_start(h, start);   // X = 0, p = q = 0 (C1) unless a starting point is given
-        run_check(h, ttype, MODE_INIT);
     }
 
     const int K = std::max(1, h->opt.restart_check_every);
@@ -898,6 +930,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     try {
+        const Range r_("chunks");
         // Keep two chunks in flight: the host reads chunk i's status while
         // chunk i+1 runs (a chunk issued after termination is a no-op).
         long long i = 0;
@@ -928,6 +961,7 @@ pdot_status solve_impl(pdot_handle* h, long long m, long long n, const void* C, 
     cudaEventDestroy(ev[1]);
     CK(cudaMemcpyAsync(S, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    const Range r_result("result");
     if (start && start->state_out) export_state(h, *S, start->state_out);
     if (timed_out && S->status == ST_RUNNING) {
         // Evaluate the current iterate and report it.
@@ -1610,12 +1644,15 @@ void batch_collect(pdot_handle* h, bool wait) {
 pdot_status batch_poll(pdot_handle* h, uint64_t* ids, pdot_result* results, int cap, int* n_done) {
     BatchEngine* B = batch_of(h);
     bool changed = false;
-    if (B->flights.size() >= 2) batch_retire_front(h, changed);
-    while (!B->flights.empty()) {
-        const cudaError_t q = cudaEventQuery(B->ev_chunk[B->flights.front().buf]);
-        if (q == cudaErrorNotReady) break;
-        if (q != cudaSuccess) throw CudaError{q};
-        batch_retire_front(h, changed);
+    {
+        const Range r_("retire");
+        if (B->flights.size() >= 2) batch_retire_front(h, changed);
+        while (!B->flights.empty()) {
+            const cudaError_t q = cudaEventQuery(B->ev_chunk[B->flights.front().buf]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) throw CudaError{q};
+            batch_retire_front(h, changed);
+        }
     }
     // The pinned staging buffers are rewritten below: the copies that read
     // them for the previous chunk must have run.
@@ -1624,12 +1661,16 @@ pdot_status batch_poll(pdot_handle* h, uint64_t* ids, pdot_result* results, int 
         B->staged_pending = false;
     }
     batch_apply_cancels(h);
-    changed |= batch_admit(h);
-    // With an active-bytes budget the advancing set can change every chunk.
-    if (changed || B->chunks == 0 || h->opt.batch_active_bytes > 0) batch_compose(h);
+    {
+        const Range r_("admit");
+        changed |= batch_admit(h);
+        // With an active-bytes budget the advancing set can change every chunk.
+        if (changed || B->chunks == 0 || h->opt.batch_active_bytes > 0) batch_compose(h);
+    }
     CK(cudaEventRecord(B->ev_staged, h->stream));
     B->staged_pending = true;
     if (!B->live.empty()) {
+        const Range r_("launch chunk");
         batch_launch_chunk(h);
     } else {
         while (!B->flights.empty()) batch_retire_front(h, changed);
@@ -1884,6 +1925,7 @@ pdot_status pdot_solve(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot
                        const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
                        pdot_result* res) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_solve");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         return solve_impl(h, m, n, C, c_dtype, ldc, f, g, tol, X_out, p_out, q_out, res);
@@ -1905,6 +1947,7 @@ pdot_status pdot_solve_from(pdot_handle* h, int64_t m, int64_t n, const void* C,
                             const double* f, const double* g, double tol, const pdot_start* start, void* X_out,
                             double* p_out, double* q_out, pdot_result* res) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_solve_from");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         return solve_impl(h, m, n, C, c_dtype, ldc, f, g, tol, X_out, p_out, q_out, res, start);
@@ -1915,6 +1958,7 @@ pdot_status pdot_solve_host(pdot_handle* h, int64_t m, int64_t n, const void* C,
                             const double* f, const double* g, double tol, void* X_out, double* p_out, double* q_out,
                             pdot_result* res) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_solve_host");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         const bool pts = c_dtype == PDOT_POINTS;
@@ -1979,6 +2023,7 @@ pdot_status pdot_pdhg_steps(pdot_handle* h, int64_t m, int64_t n, const void* C,
                             const double* f, const double* g, int64_t k, double eta, double omega, void* X, double* p,
                             double* q, void* Xbar_out, double* pbar_out, double* qbar_out) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_pdhg_steps");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
@@ -2039,6 +2084,7 @@ pdot_status pdot_kkt(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_d
                      const double* f, const double* g, const void* X, const double* p, const double* q,
                      pdot_kkt_parts* out) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_kkt");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
@@ -2072,6 +2118,7 @@ pdot_status pdot_kkt(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_d
 pdot_status pdot_round(pdot_handle* h, int64_t m, int64_t n, const void* X, const double* f, const double* g,
                        void* X_out) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_round");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         if (m < 1 || n < 1 || !X || !f || !g || !X_out) throw ArgError{"bad arguments"};
@@ -2087,6 +2134,7 @@ int64_t pdot_launch_count(pdot_handle* h) { return h ? h->launches : 0; }
 
 pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int count, uint64_t* ticket_ids) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_batch_submit");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         if (count < 0 || (count > 0 && (!reqs || !ticket_ids))) throw ArgError{"bad request array"};
@@ -2130,6 +2178,7 @@ pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int coun
 
 pdot_status pdot_poll(pdot_handle* h, uint64_t* done_ids, pdot_result* done_results, int cap, int* n_done) {
     if (!h || !n_done || cap < 0) return PDOT_ERR_ARG;
+    const Range r_("pdot_poll");
     *n_done = 0;
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
@@ -2139,6 +2188,7 @@ pdot_status pdot_poll(pdot_handle* h, uint64_t* done_ids, pdot_result* done_resu
 
 pdot_status pdot_cancel(pdot_handle* h, uint64_t ticket) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_cancel");
     BatchEngine* B = h->batch;
     if (!B) return PDOT_ERR_ARG;
     for (BSlot* s : B->queue)
@@ -2179,6 +2229,7 @@ pdot_status pdot_time_pass(pdot_handle* h, int64_t m, int64_t n, const void* C, 
                            const double* f, const double* g, int reps, double* ms_per_pass, double* bytes_per_pass,
                            int32_t* kernel_variant) {
     if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_time_pass");
     return guarded(h, [&]() -> pdot_status {
         CK(cudaSetDevice(h->device));
         check_common_args(h, m, n, C, c_dtype, ldc, f, g);
