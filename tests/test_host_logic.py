@@ -150,6 +150,121 @@ def test_row_sharded_step_equals_unsharded_gloo():
         np.testing.assert_allclose(o[3], qo, rtol=1e-13, atol=1e-15)
 
 
+def _fixed_order_allreduce(vec, world, dist):
+    """Sum of every rank's vector, added in rank order (the same bits on
+    every rank)."""
+    import torch
+    part = torch.tensor(np.asarray(vec, dtype=np.float64))
+    parts = [torch.zeros_like(part) for _ in range(world)]
+    dist.all_gather(parts, part)
+    total = parts[0].clone()
+    for t in parts[1:]:
+        total += t
+    return total.numpy()
+
+
+SHARD_PASSES = 5
+
+
+def _shard_period_main(rank, world, port, q):
+    """One rank of a row-sharded solve over several passes and a check.
+
+    Rows [r0, r1) of C, X, f and p live on the rank; q and the column sums c
+    of the current plan are replicated.  Per pass one all-reduce of
+    [column sums of X+ - X (n) | ||X+ - X||^2 | dp . (row sums of X+ - X) |
+    ||dp||^2] gives every rank the q update (2c+ - c = c + 2 dc) and the
+    step-size ratio of the Sec. 5 rule; per check one all-reduce of
+    [column sums of X (n) | ||r - f||^2 | dual-infeasibility^2 | <C, X> |
+    f.p | ||f||^2 | ||C||_F^2] gives the KKT error of Sec. 3.1 and its
+    relative measures."""
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ins = I.points_instance(37, 23, 4321)
+    m, n = ins.C.shape
+    rng = np.random.default_rng(9)
+    X0 = rng.random((m, n)) / (m * n)
+    p0, q0 = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
+    eta, omega = 0.05, 1.3
+    tau, sigma = eta / omega, eta * omega
+    r0, r1 = m * rank // world, m * (rank + 1) // world
+    Cb, fb, Xb, pb, qv = ins.C[r0:r1], ins.f[r0:r1], X0[r0:r1].copy(), p0[r0:r1].copy(), q0.copy()
+    g = ins.g
+    c = _fixed_order_allreduce(Xb.sum(axis=0), world, dist)
+    eta_bar = None
+    for _ in range(SHARD_PASSES):
+        Xn, pn, _ = oracle.pdhg_step(Cb, fb, g, Xb, pb, qv, tau, sigma)   # row-local X+ and p+
+        dX = Xn - Xb
+        dp = pn - pb
+        buf = _fixed_order_allreduce(
+            np.concatenate([dX.sum(axis=0), [np.sum(dX * dX), dp @ dX.sum(axis=1), dp @ dp]]), world, dist)
+        dc, dx2, dpdr, dp2 = buf[:n], buf[n], buf[n + 1], buf[n + 2]
+        qn = qv + sigma * (g - (c + 2.0 * dc))
+        dq = qn - qv
+        eta_bar = (omega * dx2 + (dp2 + dq @ dq) / omega) / (2.0 * abs(dpdr + dq @ dc))
+        Xb, pb, qv, c = Xn, pn, qn, c + dc
+    V = pb[:, None] + qv[None, :] - Cb
+    kb = _fixed_order_allreduce(
+        np.concatenate([Xb.sum(axis=0), [np.sum((Xb.sum(axis=1) - fb) ** 2), np.sum(np.where(V > 0, V * V, 0.0)),
+                                        np.sum(Cb * Xb), fb @ pb, fb @ fb, np.sum(Cb * Cb)]]), world, dist)
+    cx_exact = kb[:n]
+    rp2 = kb[n] + np.sum((cx_exact - g) ** 2)
+    rd2, cx, dual = kb[n + 1], kb[n + 2], kb[n + 3] + g @ qv
+    gap = cx - dual
+    rel_p = np.sqrt(rp2) / np.sqrt(kb[n + 4] + g @ g)
+    rel_d = np.sqrt(rd2) / np.sqrt(kb[n + 5])
+    rel_gap = abs(gap) / (abs(cx) + abs(dual))
+    kkt = dict(rp2=rp2, rd2=rd2, gap=gap, kkt=np.sqrt(rp2 + rd2 + gap * gap),
+               rel_kkt=max(rel_p, rel_d, rel_gap))
+    q.put((rank, Xb, pb, qv, eta_bar, kkt, np.abs(c - cx_exact).max()))
+    dist.destroy_process_group()
+
+
+def test_row_sharded_passes_and_check_equal_unsharded_gloo():
+    """Design check of a row-sharded single instance over several passes and
+    a restart check (two gloo ranks, 37 rows split 18 / 19): the plan, the
+    duals, the step-size ratio of the last pass and the KKT measures equal
+    the unsharded oracle's up to the summation order of the exchanged sums,
+    and the running column sums equal the exact column sums at the check."""
+    pytest.importorskip("torch.distributed")
+    import multiprocessing as mp
+
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_period_main, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    ins = I.points_instance(37, 23, 4321)
+    m, n = ins.C.shape
+    rng = np.random.default_rng(9)
+    X0 = rng.random((m, n)) / (m * n)
+    p0, q0 = rng.standard_normal(m) * 0.1, rng.standard_normal(n) * 0.1
+    eta, omega = 0.05, 1.3
+    X, p, qv, *_ = oracle.pdhg_steps(ins.C, ins.f, ins.g, X0, p0, q0, SHARD_PASSES - 1, eta, omega)
+    Xn, pn, qn = oracle.pdhg_step(ins.C, ins.f, ins.g, X, p, qv, eta / omega, eta * omega)
+    dX, dp, dq = Xn - X, pn - p, qn - qv
+    eta_bar = (omega * np.sum(dX * dX) + (dp @ dp + dq @ dq) / omega) / (
+        2.0 * abs(dp @ dX.sum(axis=1) + dq @ dX.sum(axis=0)))
+    np.testing.assert_allclose(np.vstack([o[1] for o in out]), Xn, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(np.concatenate([o[2] for o in out]), pn, rtol=1e-12, atol=1e-15)
+    k = oracle.kkt(ins.C, ins.f, ins.g, Xn, pn, qn)
+    for o in out:
+        np.testing.assert_allclose(o[3], qn, rtol=1e-12, atol=1e-15)
+        assert abs(o[4] - eta_bar) <= 1e-9 * eta_bar
+        assert o[6] <= 1e-15
+        for key in ("rp2", "rd2", "gap", "kkt", "rel_kkt"):
+            assert abs(o[5][key] - getattr(k, key)) <= 1e-10 * abs(getattr(k, key)), key
+    assert out[0][4] == out[1][4] and out[0][5] == out[1][5]   # replicated decisions see the same bits
+
+
 def test_recorded_traffic_is_null_once_the_kernel_source_changes(tmp_path, monkeypatch):
     """bench.py reports the ncu DRAM traffic of the pass kernel only while the
     kernel source still hashes to the value recorded with the capture."""
