@@ -1300,8 +1300,9 @@ k_pass_group(const Inst* __restrict__ insts, const TileRef* __restrict__ tmap, c
 // ---------------------------------------------------------------------------
 // Slot bookkeeping
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void assign_free(Ctrl* S) {
-    const int used = (1 << S->cur) | (1 << S->bar) | (1 << S->anc);
+// nxt and barn <- the two lowest slots not in use as cur, bar or anc.
+__device__ __forceinline__ void assign_free(Ctrl* S, int cur, int bar, int anc) {
+    const int used = (1 << cur) | (1 << bar) | (1 << anc);
     int picks[2] = {0, 0};
     int np = 0;
     for (int s = 0; s < NSLOT && np < 2; ++s)
@@ -1330,22 +1331,51 @@ __device__ __forceinline__ SchedFactors sched_factors(const Ctrl* S, long long t
     return r;
 }
 
+// The controller fields the step decision reads.  Only the decision itself
+// writes them during a dual update, so a copy taken when the update starts
+// is current when the instance's last tile decides; taking it early keeps
+// those reads off the serial path (after the ticket's acquire they would go
+// to L2 again).
+struct StepPre {
+    double eta, omega;
+    long long passes, k, total, rejected;
+    int cur, nxt, bar, barn, anc, adaptive_step;
+};
+__device__ __forceinline__ StepPre step_pre(const Ctrl* S) {
+    StepPre P;
+    P.eta = S->eta;
+    P.omega = S->omega;
+    P.passes = S->passes;
+    P.k = S->k;
+    P.total = S->total;
+    P.rejected = S->rejected;
+    P.cur = S->cur;
+    P.nxt = S->nxt;
+    P.bar = S->bar;
+    P.barn = S->barn;
+    P.anc = S->anc;
+    P.adaptive_step = S->adaptive_step;
+    return P;
+}
+
 // w_next: 1 / (k + 2), the averaging weight after an accepted step (computed
-// by the caller early, off this serial path).
-__device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, SchedFactors fac, double w_next) {
-    S->passes += 1;
+// by the caller early, off this serial path).  P: step_pre(S), taken at any
+// point after the previous decision.
+__device__ void finalize_step(Ctrl* S, const StepPre& P, double dX2, double dy2, double inter, SchedFactors fac,
+                              double w_next) {
+    S->passes = P.passes + 1;
     S->last_dX2 = dX2;
     S->last_dy2 = dy2;
     S->last_inter = inter;
     bool accept = true;
-    double eta = S->eta;
-    if (S->adaptive_step) {
+    double eta = P.eta;
+    if (P.adaptive_step) {
         // Sec. 5 step-size rule in the PDLP form (reading C6); the exponent base
         // is the 1-based index of the attempted iteration plus one.
         // The accept/reject decision is discrete: it is taken in FP64 with
         // the same expression as the FP64 reference of the rule, so that
         // both sides decide alike away from exact ties.
-        const double om = S->omega;
+        const double om = P.omega;
         const double etabar = inter != 0.0 ? (om * dX2 + dy2 / om) / (2.0 * fabs(inter)) : CUDART_INF;
         const double a = (1.0 - fac.f3) * etabar;
         const double b = (1.0 + fac.f6) * eta;
@@ -1356,24 +1386,29 @@ __device__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, Sch
     }
     if (!isfinite(dX2) || !isfinite(dy2) || !isfinite(eta) || !(eta > 0.0)) {
         S->status = ST_NUMERIC;
-        S->res_slot = S->res_xslot = S->cur;
+        S->res_slot = S->res_xslot = P.cur;
         S->res_avg = 0;
         return;
     }
     S->fix = 0;   // the plan a restart picked has been formed before this pass
     if (accept) {
-        S->cur = S->nxt;
-        S->bar = S->barn;
-        assign_free(S);
-        S->k += 1;
+        S->cur = P.nxt;
+        S->bar = P.barn;
+        assign_free(S, P.nxt, P.barn, P.anc);
+        S->k = P.k + 1;
         S->wavg = w_next;
-        S->total += 1;
+        S->total = P.total + 1;
     } else {
-        S->rejected += 1;
+        S->rejected = P.rejected + 1;
     }
     S->eta = eta;
-    S->tau = eta / S->omega;
-    S->sigma = eta * S->omega;
+    S->tau = eta / P.omega;
+    S->sigma = eta * P.omega;
+}
+
+__device__ __forceinline__ void finalize_step(Ctrl* S, double dX2, double dy2, double inter, SchedFactors fac,
+                                              double w_next) {
+    finalize_step(S, step_pre(S), dX2, dy2, inter, fac, w_next);
 }
 
 // One vector tile (VE = 32 entries of [p; q]) per CTA.  All warps add the
@@ -1398,8 +1433,12 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
     double* Vn = nullptr;
     double* Vbn = nullptr;
     SchedFactors fac = {0.0, 0.0};
+    // The step decision's controller fields, used only by the instance's last
+    // tile (lane 0 of warp 0 copies and later reads them: no barrier needed).
+    __shared__ StepPre s_pre;
     if (grp == 0) {
         status = S->status;
+        if (lane == 0) s_pre = step_pre(S);
         sigma = S->sigma;
         k = S->k;
         wavg = S->wavg;
@@ -1425,13 +1464,21 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
 #pragma unroll 8
         for (int kk = grp; kk < count; kk += VG) s += part[(long long)kk * stride + idx];
     }
+    // This tile's slice of the plan tiles' ||X+ - X||^2 partials, requested
+    // with the partial sums above (before the barrier, off the serial path).
+    double a2 = 0.0;
+    if (grp == 0) {
+        const long long T = I.ntiles;
+        const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
+        for (long long tt = t0 + lane; tt < t1; tt += 32) a2 += I.tpart[tt * TP + 0];
+    }
     sgrp[grp * 32 + lane] = s;
     __syncthreads();
     if (grp == 0 && status == ST_RUNNING) {
         double t = 0.0;
 #pragma unroll
         for (int g2 = 0; g2 < VG; ++g2) t += sgrp[g2 * 32 + lane];
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;   // ||dy||^2, dy^T A dx, ||dX||^2 (this tile's slice)
+        double a0 = 0.0, a1 = 0.0;   // ||dy||^2, dy^T A dx (this tile's slice; a2: ||dX||^2)
         if (row || col) {
             // t: this row's or column's sum of X+ - X (the pass sums the change
             // itself, so the step-size term dy^T A dX below is not a difference
@@ -1444,11 +1491,6 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
             const double dy = yn - y;
             a0 = dy * dy;
             a1 = dy * t;
-        }
-        {
-            const long long T = I.ntiles;
-            const long long t0 = T * lvt / I.nvt, t1 = T * (lvt + 1) / I.nvt;
-            for (long long tt = t0 + lane; tt < t1; tt += 32) a2 += I.tpart[tt * TP + 0];
         }
         a0 = warp_sum(a0);
         a1 = warp_sum(a1);
@@ -1474,7 +1516,7 @@ __device__ void dual_tile(const Inst& I, Ctrl* S, int lvt, double* sgrp) {
             b2 = warp_sum(b2);
             if (lane == 0) {
                 *I.ticket = 0u;
-                finalize_step(S, b2, b0, b1, fac, w_next);
+                finalize_step(S, s_pre, b2, b0, b1, fac, w_next);
             }
         }
     }
