@@ -14,6 +14,8 @@ Each wrapper names the passage of the paper its C function follows:
 - ``solve``: Algorithm 2 with the Sec. 5 enhancements (or the theory mode).
 - ``round_plan``: Algorithm 3.
 - ``exact_transport``: the exact optimum of Eq. (1) (successive shortest paths).
+- ``dual_bound``: the weak-duality lower bound of Eq. (1) from a row dual p
+  (q_j = min_i (C_ij - p_i)).
 
 Parity status: the operators, the PDHG step, the KKT error, the rounding and
 the exact solver are pinned by the ``-m "not gpu"`` tests (closed forms,
@@ -70,6 +72,7 @@ def _load():
         lib.ora_solve.restype = ctypes.c_int
         lib.ora_round.argtypes = [i64, i64, d, d, d, d]
         lib.ora_exact_transport.argtypes = [i64, i64, d, d, d, d, d, d, d]
+        lib.ora_dual_bound.argtypes = [i64, i64, d, d, d, d, d, d]
         lib.ora_points_cost.argtypes = [i64, i64, ctypes.c_int, d, d, ctypes.c_int, ctypes.c_double, d]
         lib.ora_points_cost.restype = ctypes.c_int
         lib.ora_exact_transport.restype = ctypes.c_int
@@ -268,6 +271,17 @@ def exact_transport(C, f, g):
     if rc != 0:
         raise RuntimeError(f"exact_transport failed (code {rc})")
     return obj.value, X, p, q
+
+
+def dual_bound(C, f, g, p):
+    """Weak duality of Eq. (1): q_j = min_i (C_ij - p_i) is the largest column
+    dual feasible with p, and f^T p + g^T q <= OPT.  Returns (lower, q)."""
+    C, f, g, p = map(_f64, (C, f, g, p))
+    m, n = C.shape
+    q = np.empty(n)
+    lower = np.empty(1)
+    _load().ora_dual_bound(m, n, _p(C), _p(f), _p(g), _p(p), _p(q), _p(lower))
+    return float(lower[0]), q
 
 
 POINT_DISTANCES = {"sqeuclid": 0, "l1": 1, "l2": 2, "linf": 3}

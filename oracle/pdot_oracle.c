@@ -31,6 +31,14 @@
  *   ora_exact_transport          exact optimum of Eq. (1) by successive shortest
  *                                paths with node potentials (not in the paper:
  *                                the plain definition of the LP optimum).
+ *   ora_dual_bound               a lower bound on the optimum of Eq. (1) from
+ *                                any row dual p: the dual of Eq. (1) asks
+ *                                p_i + q_j <= C_ij (the constraint whose
+ *                                violation the KKT error's dual term measures,
+ *                                Sec. 3.1), and the largest q it allows for a
+ *                                given p is q_j = min_i (C_ij - p_i); weak
+ *                                duality then gives f^T p + g^T q <= OPT (not
+ *                                in the paper: the plain definition).
  *   ora_points_cost              C_ij = dist(x_i, y_j) / divisor for the
  *                                distances the paper's grid costs use (Sec. 5.1:
  *                                l1, l2, l_inf; squared l2 for the squared grid
@@ -567,6 +575,28 @@ int ora_exact_transport(int64_t m, int64_t n, const double *C, const double *f, 
     *obj = o;
     free(pi); free(dist); free(prev); free(done); free(sup); free(dem);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lower bound on the optimum from a row dual (weak duality of Eq. (1)).       */
+/* ------------------------------------------------------------------------- */
+/* q_out[j] = min over i of (C_ij - p_i), the largest column dual that keeps
+ * p_i + q_j <= C_ij for every i; *lower = f^T p + g^T q_out.  Rows in order,
+ * then the two dot products in order. */
+void ora_dual_bound(int64_t m, int64_t n, const double *C, const double *f, const double *g,
+                    const double *p, double *q_out, double *lower)
+{
+    for (int64_t j = 0; j < n; ++j) q_out[j] = C[j] - p[0];
+    for (int64_t i = 1; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double v = C[i * n + j] - p[i];
+            if (v < q_out[j]) q_out[j] = v;
+        }
+    }
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += f[i] * p[i];
+    for (int64_t j = 0; j < n; ++j) s += g[j] * q_out[j];
+    *lower = s;
 }
 
 /* ------------------------------------------------------------------------- */

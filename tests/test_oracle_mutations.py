@@ -81,6 +81,12 @@ MUTANTS = [
      "restart_condition_alone"),
     ("primal_weight_inverted", "log(dy / dX)", "log(dX / dy)"),
     ("adaptive_eta0_doubled", "eta = opt->adaptive_step ? 1.0 / sqrt", "eta = opt->adaptive_step ? 2.0 / sqrt"),
+    ("dual_bound_max_not_min", "if (v < q_out[j]) q_out[j] = v;", "if (v > q_out[j]) q_out[j] = v;", "dual_bound"),
+    ("dual_bound_adds_p", "double v = C[i * n + j] - p[i];", "double v = C[i * n + j] + p[i];", "dual_bound"),
+    ("dual_bound_skips_row1", "for (int64_t i = 1; i < m; ++i) {\n        for (int64_t j = 0; j < n; ++j) {\n            double v = C[i * n + j] - p[i];",
+     "for (int64_t i = 2; i < m; ++i) {\n        for (int64_t j = 0; j < n; ++j) {\n            double v = C[i * n + j] - p[i];",
+     "dual_bound"),
+    ("dual_bound_drops_f_term", "for (int64_t i = 0; i < m; ++i) s += f[i] * p[i];", ";", "dual_bound"),
 ]
 
 

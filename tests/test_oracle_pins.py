@@ -597,3 +597,55 @@ def test_points_cost_grid_invariants(ora):
 def test_points_cost_rejects_bad_arguments(ora):
     with pytest.raises(ValueError):
         ora.points_cost(np.zeros((2, 2)), np.zeros((2, 2)), "l1", 0.0)
+
+
+# --------------------------------------------------------------------------
+# Weak-duality lower bound of Eq. (1) from a row dual
+# --------------------------------------------------------------------------
+
+def test_dual_bound_single_row_is_the_optimum_for_any_p(ora):
+    """One source: the only feasible plan is X = g^T, so OPT = C g, and for
+    any p the bound p f + sum_j g_j (C_j - p) = C g (Sigma g = f) is exact.
+    Hand case: C = [1, 3], f = 1, g = [1/2, 1/2], p = 1/4: q = [3/4, 11/4],
+    bound 1/4 + 3/8 + 11/8 = 2 = OPT."""
+    C = np.array([[1.0, 3.0]])
+    lower, q = ora.dual_bound(C, np.array([1.0]), np.array([0.5, 0.5]), np.array([0.25]))
+    np.testing.assert_array_equal(q, [0.75, 2.75])
+    assert lower == 2.0
+    rng = np.random.default_rng(7)
+    C = rng.random((1, 9))
+    g = rng.dirichlet(np.ones(9))
+    for p0 in (-3.0, 0.0, 0.4, 17.0):
+        lower, _ = ora.dual_bound(C, np.array([1.0]), g, np.array([p0]))
+        assert abs(lower - C[0] @ g) <= 1e-14 * (1.0 + abs(p0))
+
+
+@pytest.mark.parametrize("m,n,seed", [(12, 9, 141), (30, 41, 142), (64, 64, I.seed_for(0))])
+def test_dual_bound_is_tight_at_the_exact_duals(ora, m, n, seed):
+    """Strong duality: at the exact solver's optimal duals (p*, q*), q*_j <=
+    min_i (C_ij - p*_i), so the bound is >= f^T p* + g^T q* = OPT and, by weak
+    duality, equal to it; the column dual it forms is >= q*."""
+    ins = I.points_instance(m, n, seed)
+    opt, _, ps, qs = ora.exact_transport(ins.C, ins.f, ins.g)
+    lower, q = ora.dual_bound(ins.C, ins.f, ins.g, ps)
+    assert abs(lower - opt) <= 1e-12 * opt
+    assert np.all(q >= qs - 1e-14)
+    # feasible: p*_i + q_j <= C_ij, with equality somewhere in every column
+    slack = ins.C - ps[:, None] - q[None, :]
+    assert slack.min() >= 0.0 and np.all(slack.min(axis=0) == 0.0)
+
+
+def test_dual_bound_below_the_optimum_and_shift_invariant(ora):
+    """Weak duality for arbitrary p (the bound never exceeds OPT), and a
+    shift p + c moves q by -c and leaves the bound unchanged (Sigma f =
+    Sigma g)."""
+    ins = I.points_instance(23, 31, 143)
+    opt, *_ = ora.exact_transport(ins.C, ins.f, ins.g)
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        p = rng.standard_normal(23)
+        lower, q = ora.dual_bound(ins.C, ins.f, ins.g, p)
+        assert lower <= opt + 1e-15
+        l2, q2 = ora.dual_bound(ins.C, ins.f, ins.g, p + 0.375)
+        np.testing.assert_allclose(q2, q - 0.375, rtol=0, atol=1e-15)
+        assert abs(l2 - lower) <= 1e-14
