@@ -305,6 +305,28 @@ pdot_status pdot_round(pdot_handle *h, int64_t m, int64_t n, const void *X, cons
                        void *X_out);
 
 /*
+ * Certified lower bound on the optimum of Eq. (1) from a row dual p.  The
+ * dual of Eq. (1) asks p_i + q_j <= C_ij (the constraint whose violation the
+ * KKT error's dual term measures, Sec. 3.1); for a given p the largest such q
+ * is q_j = min_i (C_ij - p_i), and weak duality gives
+ *   lower = f^T p + g^T q <= OPT.
+ * With the returned p of a solve (single or batched), `lower` and the
+ * objective of the Algorithm 3 rounding of its plan (rounded_obj with
+ * round_plan = 1, a feasible plan, so >= OPT) bracket the optimum: the
+ * result's objective error is certified without an exact solver.  The paper
+ * has no counterpart (it reports the duality gap of the rounded plan).
+ *   C, c_dtype, ldc: as pdot_solve (a PDOT_POINTS descriptor included; the
+ *   handle's x_dtype decides which cost types it accepts, as in pdot_solve);
+ *   f (m), g (n), p (m): device FP64; q_out: nullable device output (n) of q;
+ *   lower: HOST output.  The minimum is exact, so q is the same bits as the
+ *   definition evaluated in FP64 on the same cost values; lower is an FP64
+ *   sum in a fixed order.  Errors: PDOT_ERR_ARG for bad arguments (as
+ *   pdot_solve, and a null p or lower), PDOT_ERR_OOM, PDOT_ERR_CUDA.
+ */
+pdot_status pdot_dual_bound(pdot_handle *h, int64_t m, int64_t n, const void *C, pdot_dtype c_dtype, int64_t ldc,
+                            const double *f, const double *g, const double *p, double *q_out, double *lower);
+
+/*
  * Batch engine (continuous batching).  pdot_batch_submit queues `count`
  * requests and writes one ticket id per request; it never blocks on the GPU.
  * PDOT_BUSY: a request alone would exceed the HBM budget.  Requests wait in

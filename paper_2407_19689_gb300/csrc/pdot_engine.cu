@@ -39,6 +39,9 @@ int launch_round_write(const void* X, int xtype, long long m, long long n, long 
                        long long ldo, const void* C, int ctype, long long ldc, const GenSpec* gen,
                        double* objpart, int parts, void* stream);
 int launch_colreduce(const double* colpart, int parts, long long n, double* out, void* stream);
+int launch_dual_bound(const void* C, int ctype, long long ldc, const GenSpec* gen, const double* p,
+                      const double* f, const double* g, long long m, long long n, double* colmin, int parts,
+                      double* q, double* out, void* stream);
 }  // namespace pdot
 
 namespace {
@@ -2131,6 +2134,37 @@ pdot_status pdot_round(pdot_handle* h, int64_t m, int64_t n, const void* X, cons
 }
 
 int64_t pdot_launch_count(pdot_handle* h) { return h ? h->launches : 0; }
+
+pdot_status pdot_dual_bound(pdot_handle* h, int64_t m, int64_t n, const void* C, pdot_dtype c_dtype, int64_t ldc,
+                            const double* f, const double* g, const double* p, double* q_out, double* lower) {
+    if (!h) return PDOT_ERR_ARG;
+    const Range r_("pdot_dual_bound");
+    return guarded(h, [&]() -> pdot_status {
+        CK(cudaSetDevice(h->device));
+        check_common_args(h, m, n, C, c_dtype, ldc, f, g);
+        if (!p || !lower) throw ArgError{"null p or lower"};
+        const int parts = (int)std::min<long long>(64, m);   // row groups of the column minima
+        const size_t need = sizeof(double) * ((size_t)parts * (size_t)n + (size_t)n + 8);
+        if (h->round_scratch_bytes < need) {
+            if (h->round_scratch) cudaFree(h->round_scratch);
+            h->round_scratch = nullptr;
+            h->round_scratch_bytes = 0;
+            CK(cudaMalloc(&h->round_scratch, need));
+            h->round_scratch_bytes = need;
+        }
+        double* colmin = h->round_scratch;
+        double* q = colmin + (size_t)parts * (size_t)n;
+        double* val = q + n;
+        GenSpec gs{};
+        if (c_dtype == PDOT_POINTS) gs = gen_spec_of(C);
+        CKL(launch_dual_bound(C, (int)c_dtype, ldc, &gs, p, f, g, m, n, colmin, parts, q, val, h->stream));
+        launch_count(h, 3);
+        if (q_out) CK(cudaMemcpyAsync(q_out, q, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(lower, val, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return PDOT_OK;
+    });
+}
 
 pdot_status pdot_batch_submit(pdot_handle* h, const pdot_request* reqs, int count, uint64_t* ticket_ids) {
     if (!h) return PDOT_ERR_ARG;

@@ -104,7 +104,80 @@ struct Bf16 {
     __device__ operator double() const { return (double)__uint_as_float(((unsigned)b) << 16); }
 };
 
+// Weak-duality bound of Eq. (1) from a row dual p (no counterpart in the
+// paper; it certifies a result): q_j = min_i (C_ij - p_i) is the largest
+// column dual with p_i + q_j <= C_ij for all i, and f^T p + g^T q <= OPT.
+// colmin[grp][j] = min over the rows of group grp (one thread per column, so
+// a warp reads 32 consecutive entries of a row).  The minimum is exact, so
+// the result does not depend on the grouping.
+template <typename CA>
+__global__ void k_cmin_cols(CA C, const double* p, long long m, long long n, double* colmin, int parts) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int grp = blockIdx.y;
+    if (j >= n) return;
+    const long long r0 = m * grp / parts, r1 = m * (grp + 1) / parts;
+    double v = __longlong_as_double(0x7ff0000000000000LL);   // +inf: an empty group
+    for (long long i = r0; i < r1; ++i) {
+        const double t = C(i, j) - p[i];
+        if (t < v) v = t;
+    }
+    colmin[(long long)grp * n + j] = v;
+}
+
+__global__ void k_cmin_reduce(const double* colmin, int parts, long long n, double* q) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double v = colmin[j];
+    for (int g = 1; g < parts; ++g) {
+        const double t = colmin[(long long)g * n + j];
+        if (t < v) v = t;
+    }
+    q[j] = v;
+}
+
+// out[0] = f^T p + g^T q: one block, fixed-order strided sums, then a tree.
+__global__ void k_dual_value(const double* f, const double* p, long long m, const double* g, const double* q,
+                             long long n, double* out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < m; i += blockDim.x) s += f[i] * p[i];
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) s += g[j] * q[j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+template <typename CA>
+void launch_cmin(CA C, const double* p, long long m, long long n, double* colmin, int parts, cudaStream_t st) {
+    const dim3 cb((unsigned)((n + 255) / 256), (unsigned)parts);
+    k_cmin_cols<CA><<<cb, 256, 0, st>>>(C, p, m, n, colmin, parts);
+}
+
 }  // namespace
+
+// The bound above: q (n) and out[0] = f^T p + g^T q.  colmin: parts x n
+// scratch, 1 <= parts <= m.  ctype: 0 FP32, 1 BF16, 2 FP64 (row-major with
+// leading dimension ldc), 3 generated (gen).
+int launch_dual_bound(const void* C, int ctype, long long ldc, const GenSpec* gen, const double* p,
+                      const double* f, const double* g, long long m, long long n, double* colmin, int parts,
+                      double* q, double* out, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (ctype == 3)
+        launch_cmin(PointsCost{*gen}, p, m, n, colmin, parts, st);
+    else if (ctype == 2)
+        launch_cmin(StoredCost<double>{(const double*)C, ldc}, p, m, n, colmin, parts, st);
+    else if (ctype == 1)
+        launch_cmin(StoredCost<Bf16>{(const Bf16*)C, ldc}, p, m, n, colmin, parts, st);
+    else
+        launch_cmin(StoredCost<float>{(const float*)C, ldc}, p, m, n, colmin, parts, st);
+    k_cmin_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(colmin, parts, n, q);
+    k_dual_value<<<1, 1024, 0, st>>>(f, p, m, g, q, n, out);
+    return (int)cudaGetLastError();
+}
 
 int launch_round_rowsum(const void* X, int xtype, long long m, long long n, long long ldx, const double* rs,
                         const double* cs, double* rowout, double* colpart, int parts, void* stream) {

@@ -139,7 +139,7 @@ class Start(ctypes.Structure):
 # Every symbol include/pdot.h declares (checked by the CPU tests).
 DECLARED = [
     "pdot_default_options", "pdot_status_str", "pdot_last_error", "pdot_create", "pdot_destroy", "pdot_solve",
-    "pdot_solve_host", "pdot_solve_from", "pdot_state_bytes", "pdot_resident_fits", "pdot_pdhg_steps", "pdot_kkt", "pdot_round",
+    "pdot_solve_host", "pdot_solve_from", "pdot_state_bytes", "pdot_resident_fits", "pdot_pdhg_steps", "pdot_kkt", "pdot_round", "pdot_dual_bound",
     "pdot_batch_submit", "pdot_poll", "pdot_cancel", "pdot_batch_pending", "pdot_launch_count", "pdot_time_pass",
     "pdot_round_noalloc", "pdot_watchdog_selftest",
 ]
@@ -175,6 +175,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "pdot_pdhg_steps": (i32, [H, i64, i64, vp, i32, i64, vp, vp, i64, dbl, dbl, vp, vp, vp, vp, vp, vp]),
         "pdot_kkt": (i32, [H, i64, i64, vp, i32, i64, vp, vp, vp, vp, vp, ctypes.POINTER(KktParts)]),
         "pdot_round": (i32, [H, i64, i64, vp, vp, vp, vp]),
+        "pdot_dual_bound": (i32, [H, i64, i64, vp, i32, i64, vp, vp, vp, vp, ctypes.POINTER(dbl)]),
         "pdot_batch_submit": (i32, [H, ctypes.POINTER(Request), i32, ctypes.POINTER(ctypes.c_uint64)]),
         "pdot_poll": (i32, [H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), i32,
                             ctypes.POINTER(i32)]),
@@ -269,6 +270,12 @@ def pdot_kkt(h, m, n, C, c_dtype, ldc, f, g, X, p, q):
 
 def pdot_round(h, m, n, X, f, g, X_out) -> int:
     return load().pdot_round(h, m, n, X, f, g, X_out)
+
+
+def pdot_dual_bound(h, m, n, C, c_dtype, ldc, f, g, p, q_out=0):
+    lower = ctypes.c_double()
+    st = load().pdot_dual_bound(h, m, n, C, c_dtype, ldc, f, g, p, q_out or None, ctypes.byref(lower))
+    return st, lower.value
 
 
 def pdot_batch_submit(h, reqs: list[Request]):
@@ -527,6 +534,18 @@ class Solver:
         out = torch.empty_like(X)
         _check(self.h, pdot_round(self.h, m, n, X.data_ptr(), f.data_ptr(), g.data_ptr(), out.data_ptr()))
         return out
+
+    def dual_bound(self, C, f, g, p):
+        """Weak-duality lower bound f^T p + g^T q on the optimum, with
+        q_j = min_i (C_ij - p_i); returns (lower, q)."""
+        torch = _torch()
+        c, f, g = self._prep(C, f, g)
+        p = self._cuda(p, torch.float64)
+        q = torch.empty(c.n, dtype=torch.float64, device=f.device)
+        st, lower = pdot_dual_bound(self.h, c.m, c.n, c.ptr, c.dtype, c.ldc, f.data_ptr(), g.data_ptr(),
+                                    p.data_ptr(), q.data_ptr())
+        _check(self.h, st)
+        return lower, q
 
     def launch_count(self) -> int:
         return pdot_launch_count(self.h)
