@@ -61,6 +61,8 @@ def parse():
                          "instances through the batch engine vs one instance per launch; serve: Poisson "
                          "request stream through the continuous-batching engine vs a plain FIFO server")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--certify", action="store_true",
+                    help="--workload batch: certify every batched result (weak-duality bound and rounded plan)")
     ap.add_argument("--batch-detail", action="store_true",
                     help="batch workload: add each instance's size, passes and times, batched and alone")
     ap.add_argument("--requests", type=int, default=60)
@@ -596,10 +598,68 @@ def batch_record(tol: float = 1e-6, count: int = 256, detail: bool = False) -> d
             "speedup_vs_plain": tp / tb, "max_rel_obj_diff_batched_vs_plain": maxdiff}
 
 
+def batch_certificates(tol: float = 1e-6, count: int = 256) -> dict:
+    """The batched workload solved once through the batch engine (plans
+    kept), then every result certified by the library: the optimum of its
+    instance lies between the weak-duality bound of its p (pdot_dual_bound)
+    and the objective of the Algorithm 3 rounding of its FP32 plan
+    (pdot_round, then <C, X> by pdot_kkt).  Reports the distribution of the
+    certified bounds on each result's objective error."""
+    import torch
+
+    from paper_2407_19689_gb300 import instances as I
+    from paper_2407_19689_gb300 import pdot
+    dev = "cuda:0"
+    sizes = I.batch_sizes(count, I.seed_for(3))
+    insts = []
+    for k, (m, n) in enumerate(sizes):
+        ins = I.batch_instance(m, n, I.seed_for(3, k + 1))
+        insts.append((torch.tensor(ins.C, dtype=torch.float32, device=dev),
+                      torch.tensor(ins.f, device=dev), torch.tensor(ins.g, device=dev)))
+    b = pdot.BatchSolver(device=0, chunk_checks=4)
+    tick = {b.submit(C, f, g, tol=tol): k for k, (C, f, g) in enumerate(insts)}
+    res = b.run()
+    s = pdot.Solver(device=0)
+    errs, widths, ok = [], [], 0
+    for tid, sol in res.items():
+        C, f, g = insts[tick[tid]]
+        m, n = C.shape
+        if sol.status != pdot.OK:
+            continue
+        ok += 1
+        Xr = torch.empty_like(sol.X)
+        st = pdot.pdot_round(s.h, m, n, sol.X.data_ptr(), f.data_ptr(), g.data_ptr(), Xr.data_ptr())
+        st2, kp = pdot.pdot_kkt(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(), Xr.data_ptr(),
+                                sol.p.data_ptr(), sol.q.data_ptr())
+        st3, lower = pdot.pdot_dual_bound(s.h, m, n, C.data_ptr(), pdot.F32, n, f.data_ptr(), g.data_ptr(),
+                                          sol.p.data_ptr())
+        if st != pdot.OK or st2 != pdot.OK or st3 != pdot.OK:
+            raise RuntimeError("certificate calls failed")
+        upper, obj = kp.cx, sol.result["primal_obj"]
+        widths.append((upper - lower) / abs(lower))
+        errs.append(max(obj - lower, upper - obj) / abs(lower))
+    s.close()
+    b.close()
+    errs.sort()
+    widths.sort()
+
+    def q(v, a):
+        return v[min(len(v) - 1, int(a * len(v)))]
+
+    return {"workload": f"batch{count}_loguniform64-2048_dirichlet1_sqeuclid", "tol": tol, "ok": ok,
+            "certified_rel_err_bound": {"median": q(errs, 0.5), "p90": q(errs, 0.9), "max": errs[-1],
+                                        "count_le_1e-6": sum(1 for e in errs if e <= 1e-6),
+                                        "count_le_1e-5": sum(1 for e in errs if e <= 1e-5)},
+            "interval_rel_width": {"median": q(widths, 0.5), "max": widths[-1]}}
+
+
 def run_batch(args):
     from paper_2407_19689_gb300 import _build, pdot
     _build.build()
     pdot.load()
+    if args.certify:
+        print(json.dumps(batch_certificates(args.tol, args.batch_count)), flush=True)
+        return
     rec = batch_record(args.tol, args.batch_count, args.batch_detail)
     tb = rec["batched"]["seconds"]
     line = {"metric": METRIC, "value": args.batch_count / tb, "unit": f"solves/s ({args.batch_count} uneven "
