@@ -17,9 +17,10 @@ Each wrapper names the passage of the paper its C function follows:
 - ``dual_bound``: the weak-duality lower bound of Eq. (1) from a row dual p
   (q_j = min_i (C_ij - p_i)).
 
-Parity status: the operators, the PDHG step, the KKT error, the rounding and
-the exact solver are pinned by the ``-m "not gpu"`` tests (closed forms,
-brute force, library LP/assignment solvers, invariants).  The adaptive
+Parity status: the operators, the PDHG step, the KKT error, the rounding,
+the exact solver and the weak-duality bound are pinned by the
+``-m "not gpu"`` tests (closed forms, brute force, library LP/assignment
+solvers, strong duality at the exact duals, invariants).  The adaptive
 heuristics inside ``solve`` are pinned by special cases whose outcome follows
 from pinned steps (the restart candidate rule, the artificial-restart
 schedule, restart conditions (i) and (ii) each alone, the primal weight at
