@@ -69,6 +69,8 @@ def test_null_handle_is_rejected_without_gpu(lib):
     from paper_2407_19689_gb300 import pdot
     st, _ = pdot.pdot_solve(None, 4, 4, 0, pdot.F32, 4, 0, 0, 1e-4)
     assert st == pdot.ERR_ARG
+    st, _ = pdot.pdot_dual_bound(None, 4, 4, 0, pdot.F32, 4, 0, 0, 0)
+    assert st == pdot.ERR_ARG
     assert pdot.pdot_destroy(None) == pdot.OK
 
 
